@@ -1,0 +1,154 @@
+/*
+ * ccl.h - C ABI of a GB300 (sm_103a) library for two-pass connected-component labelling
+ * of binary images, after "A New Parallel Algorithm for Two-Pass Connected Component
+ * Labeling" (PARemSP, arXiv 1606.05973).
+ *
+ * Problem (Section III of the paper): every object pixel of a binary image receives a
+ * label so that connected object pixels share one.  An object pixel is any non-zero
+ * byte; pixels outside the image are background.  Connectivity is 8 (Section III: the
+ * paper uses 8-connectedness only).
+ *
+ * Output numbering (the paper's flatten, Algorithm 3, yields consecutive labels starting
+ * at the smallest equivalent label; this library fixes the order): background 0, and
+ * components 1..K in raster order of their first pixel.  The labels are a unique function
+ * of the image, so results are bit-exact and independent of scheduling.
+ *
+ * Memory: all image and label pointers are DEVICE pointers unless a function says HOST.
+ * The caller owns them.  The library owns a per-(device, stream) workspace that it
+ * allocates on first use and grows as needed; ccl_release() frees it.
+ *
+ * Errors: every function returns a ccl_status code; nothing is thrown across the ABI.
+ * Threads: calls on distinct streams may run concurrently from distinct host threads.
+ */
+#ifndef CCL_H_
+#define CCL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *ccl_stream_t;
+
+typedef enum {
+    CCL_OK = 0,
+    CCL_ERR_INVALID_ARGUMENT = 1, /* NULL pointer, negative size, pitch < W, H*W >= 2^31 */
+    CCL_ERR_UNSUPPORTED = 2,      /* connectivity other than 8 */
+    CCL_ERR_OUT_OF_MEMORY = 3,    /* workspace allocation failed */
+    CCL_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+    CCL_ERR_TIMEOUT = 5,          /* a device loop hit its iteration cap (see status bits) */
+    CCL_ERR_BUSY = 6,             /* server: over its memory cap and told not to wait */
+    CCL_ERR_INTERNAL = 7          /* a device-side consistency check failed */
+} ccl_status;
+
+/* Device status word bits (ccl_device_status). */
+#define CCL_STATUS_LOOP_CAP 1  /* a union-find loop exceeded its iteration cap */
+#define CCL_STATUS_BOUNDS 2    /* checked builds: an index was out of range (access skipped) */
+#define CCL_STATUS_BAD_VALUE 4 /* checked builds: a value that cannot occur was read */
+
+/* Human-readable name of a status code (static string). */
+const char *ccl_status_string(int32_t status);
+
+/* Library ABI version: major*10000 + minor*100 + patch. */
+int32_t ccl_version(void);
+
+/*
+ * ccl_label - label one image.
+ *
+ * Computes what the paper's CCLRemSP / ARemSP / PARemSP compute (Algorithms 1, 5, 7):
+ * provisional labels per tile with union-find (Algorithm 2, Rem's union with splicing),
+ * a lock-free Rem union across tile boundaries (Algorithms 7-8), flatten (Algorithm 3)
+ * and the labelling pass.
+ *
+ *   img            device, H rows of pitch_bytes bytes (only the first W bytes of a row
+ *                  are read); 16-byte alignment of img and pitch enables vector loads
+ *   H, W           image size, H >= 0, W >= 0, H*W < 2^31
+ *   pitch_bytes    row stride of img in bytes, >= W
+ *   connectivity   8 (4 returns CCL_ERR_UNSUPPORTED)
+ *   labels         device, H*W int32, row stride W (dense); fully overwritten
+ *   num_components HOST int32 or NULL.  Non-NULL: the call waits for `stream` and
+ *                  stores K; it also checks the device status word and returns
+ *                  CCL_ERR_TIMEOUT / CCL_ERR_INTERNAL if a bit is set.  NULL: the call
+ *                  only enqueues work and returns.
+ *   stream         CUDA stream; all work is ordered on it
+ *
+ * H == 0 or W == 0 is valid: nothing is written and K = 0.
+ */
+int32_t ccl_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes,
+                  int32_t connectivity, int32_t *labels, int32_t *num_components,
+                  ccl_stream_t stream);
+
+/*
+ * ccl_label_async - as ccl_label, fully asynchronous: K is written to the DEVICE int32
+ * num_components_dev (may be NULL).  Safe to capture in a CUDA graph once the stream's
+ * workspace is large enough (make one uncaptured call of the same or larger size first).
+ */
+int32_t ccl_label_async(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes,
+                        int32_t connectivity, int32_t *labels, int32_t *num_components_dev,
+                        ccl_stream_t stream);
+
+/*
+ * ccl_label_host - label one image held in HOST memory (pinned memory gives full copy
+ * speed).  Copies the image to the device, labels it, copies the labels back and waits.
+ *   img_host     HOST, H rows of pitch_bytes bytes
+ *   labels_host  HOST, H*W int32, row stride W
+ *   num_components HOST int32 or NULL
+ * Device buffers for the image and labels come from the stream's workspace.
+ */
+int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch_bytes,
+                       int32_t connectivity, int32_t *labels_host, int32_t *num_components,
+                       ccl_stream_t stream);
+
+/* One image of a batch: device pointers, same conventions as ccl_label. */
+typedef struct {
+    const uint8_t *img;
+    int32_t H;
+    int32_t W;
+    int64_t pitch_bytes;
+    int32_t *labels;
+} ccl_image;
+
+/*
+ * ccl_label_batch - label n images (uneven sizes allowed) on one stream.
+ *   imgs               HOST array of n descriptors (device pointers inside)
+ *   num_components_dev DEVICE int32[n] or NULL; entry i receives K of image i
+ * Asynchronous; results are identical to labelling each image alone.
+ */
+int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity,
+                        int32_t *num_components_dev, ccl_stream_t stream);
+
+/* Bytes of workspace one image of H x W needs (for capacity planning). */
+int32_t ccl_workspace_bytes(int32_t H, int32_t W, int64_t *bytes);
+
+/* Read and clear the device status word of `stream`'s workspace (waits for the stream).
+ * *flags receives CCL_STATUS_* bits (0 when everything ran within its limits). */
+int32_t ccl_device_status(ccl_stream_t stream, int32_t *flags);
+
+/* Free every cached workspace of this process (waits for the device). */
+int32_t ccl_release(void);
+
+/*
+ * Kernel timing.  When enabled, the library records CUDA events on the launching stream
+ * around each of its kernel launches; ccl_profile_read waits for them and reports, per
+ * kernel, the number of launches and the summed device time since the last reset.
+ * Launch counts are kept whether or not timing is enabled.
+ */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} ccl_kernel_time;
+
+int32_t ccl_profile_enable(int32_t on);
+int32_t ccl_profile_reset(void);
+/* Fills up to max entries; *count receives the number of kernels known. */
+int32_t ccl_profile_read(ccl_kernel_time *out, int32_t max, int32_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCL_H_ */

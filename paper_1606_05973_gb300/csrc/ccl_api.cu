@@ -1,0 +1,435 @@
+// C ABI of the labelling library (declared in include/ccl.h): argument checks, workspace
+// management, the launch sequence per image, host-buffer and batch entry points, and the
+// kernel timing hooks.
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string.h>
+#include <utility>
+#include <vector>
+
+#include "../../include/ccl.h"
+#include "ccl_internal.h"
+
+namespace {
+
+using namespace ccl;
+
+// ---- workspace cache -----------------------------------------------------------------------
+// One workspace per (device, stream).  Layout: a 256-byte header {K, status, ...} followed
+// by the per-image arrays (and, for host-buffer calls, a device copy of the image and of
+// the labels).  Work on one stream is ordered, so reusing its workspace is safe.
+constexpr int64_t HDR = 256;
+
+struct Workspace {
+    void *dev = nullptr;
+    int64_t bytes = 0;
+    int32_t *host_hdr = nullptr;  // pinned, 2 ints: K and status read back together
+};
+
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+int32_t map_cuda(cudaError_t e) { return e == cudaSuccess ? CCL_OK : (e == cudaErrorMemoryAllocation ? CCL_ERR_OUT_OF_MEMORY : CCL_ERR_CUDA); }
+
+int32_t get_workspace(cudaStream_t s, int64_t bytes, Workspace **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return map_cuda(e);
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    Workspace &w = g_ws[{dev, s}];
+    if (w.bytes < bytes) {
+        if (w.dev) {
+            // the stream may still use the old buffer
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess)
+                return map_cuda(e);
+            cudaFree(w.dev);
+            w.dev = nullptr;
+            w.bytes = 0;
+        }
+        const int64_t want = bytes + bytes / 8;
+        e = cudaMalloc(&w.dev, (size_t)want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            w.dev = nullptr;
+            return CCL_ERR_OUT_OF_MEMORY;
+        }
+        w.bytes = want;
+        e = cudaMemsetAsync(w.dev, 0, HDR, s);
+        if (e != cudaSuccess)
+            return map_cuda(e);
+    }
+    if (!w.host_hdr) {
+        e = cudaMallocHost(&w.host_hdr, 2 * sizeof(int32_t));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            w.host_hdr = nullptr;
+            return CCL_ERR_OUT_OF_MEMORY;
+        }
+    }
+    *out = &w;
+    return CCL_OK;
+}
+
+// ---- profiling -----------------------------------------------------------------------------
+struct ProfRec {
+    int kid;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+std::atomic<int> g_prof_on{0};
+std::atomic<int64_t> g_launches[KID_COUNT];
+double g_ms[KID_COUNT];
+int64_t g_timed[KID_COUNT];
+std::vector<ProfRec> g_pending;
+std::vector<cudaEvent_t> g_event_pool;
+thread_local ProfRec t_open{-1, nullptr, nullptr};
+
+cudaEvent_t pool_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int32_t check_args(const void *img, int32_t H, int32_t W, int64_t pitch, int32_t conn, const void *labels)
+{
+    if (H < 0 || W < 0)
+        return CCL_ERR_INVALID_ARGUMENT;
+    if (H == 0 || W == 0)
+        return conn == 8 ? CCL_OK : (conn == 4 ? CCL_ERR_UNSUPPORTED : CCL_ERR_INVALID_ARGUMENT);
+    if (!img || !labels || pitch < W)
+        return CCL_ERR_INVALID_ARGUMENT;
+    if ((int64_t)H * (int64_t)W >= ((int64_t)1 << 31) - 1)
+        return CCL_ERR_INVALID_ARGUMENT;
+    if (conn == 4)
+        return CCL_ERR_UNSUPPORTED;
+    if (conn != 8)
+        return CCL_ERR_INVALID_ARGUMENT;
+    const Layout L = main_layout(H, W);
+    if (L.nP >= ((int64_t)1 << 31) - 1)  // global node ids are int32
+        return CCL_ERR_UNSUPPORTED;
+    return CCL_OK;
+}
+
+// Enqueue the path for one image whose K goes to k_dev (device) and whose status bits go
+// to the workspace header.  `layout_base` is the workspace area for the per-image arrays.
+int32_t enqueue_one(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t *labels,
+                    int32_t *k_dev, Workspace *w, char *layout_base, cudaStream_t s)
+{
+    cudaError_t e = kernels_init();
+    if (e != cudaSuccess)
+        return map_cuda(e);
+    const Layout L = main_layout(H, W);
+    Img a;
+    memset(&a, 0, sizeof(a));
+    a.img = img;
+    a.pitch = pitch;
+    a.H = H;
+    a.W = W;
+    a.vec_in = ((reinterpret_cast<uintptr_t>(img) & 15) == 0) && (pitch % 16 == 0);
+    a.labels = labels;
+    a.vec_out = ((reinterpret_cast<uintptr_t>(labels) & 15) == 0) && (W % 4 == 0);
+    a.K = k_dev;
+    a.status = reinterpret_cast<int *>(static_cast<char *>(w->dev) + 4);
+    bind_workspace(a, L, layout_base);
+    return map_cuda(launch_label(a, L, s));
+}
+
+int32_t read_k_and_status(Workspace *w, const int32_t *k_dev, int32_t *num_components, cudaStream_t s)
+{
+    cudaError_t e = cudaMemcpyAsync(w->host_hdr, k_dev, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w->host_hdr + 1, static_cast<char *>(w->dev) + 4, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return map_cuda(e);
+    const int32_t st = w->host_hdr[1];
+    if (st) {
+        cudaMemsetAsync(static_cast<char *>(w->dev) + 4, 0, 4, s);
+        cudaStreamSynchronize(s);
+        return (st & CCL_STATUS_LOOP_CAP) ? CCL_ERR_TIMEOUT : CCL_ERR_INTERNAL;
+    }
+    if (num_components)
+        *num_components = w->host_hdr[0];
+    return CCL_OK;
+}
+
+}  // namespace
+
+namespace ccl {
+
+void prof_begin(int kid, cudaStream_t s)
+{
+    g_launches[kid].fetch_add(1, std::memory_order_relaxed);
+    if (!g_prof_on.load(std::memory_order_relaxed))
+        return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    t_open.kid = kid;
+    t_open.a = pool_event();
+    t_open.b = pool_event();
+    cudaEventRecord(t_open.a, s);
+}
+
+void prof_end(int kid, cudaStream_t s)
+{
+    if (t_open.kid != kid || !t_open.a)
+        return;
+    cudaEventRecord(t_open.b, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_pending.push_back(t_open);
+    t_open = {-1, nullptr, nullptr};
+}
+
+}  // namespace ccl
+
+extern "C" {
+
+const char *ccl_status_string(int32_t status)
+{
+    switch (status) {
+    case CCL_OK: return "ok";
+    case CCL_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case CCL_ERR_UNSUPPORTED: return "unsupported";
+    case CCL_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case CCL_ERR_CUDA: return "CUDA error";
+    case CCL_ERR_TIMEOUT: return "device loop exceeded its iteration cap";
+    case CCL_ERR_BUSY: return "busy";
+    case CCL_ERR_INTERNAL: return "device consistency check failed";
+    default: return "unknown status";
+    }
+}
+
+int32_t ccl_version(void) { return 100; }
+
+int32_t ccl_workspace_bytes(int32_t H, int32_t W, int64_t *bytes)
+{
+    if (!bytes || H < 0 || W < 0)
+        return CCL_ERR_INVALID_ARGUMENT;
+    if (H == 0 || W == 0) {
+        *bytes = HDR;
+        return CCL_OK;
+    }
+    *bytes = HDR + main_layout(H, W).bytes;
+    return CCL_OK;
+}
+
+int32_t ccl_label_async(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes,
+                        int32_t connectivity, int32_t *labels, int32_t *num_components_dev,
+                        ccl_stream_t stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int32_t rc = check_args(img, H, W, pitch_bytes, connectivity, labels);
+    if (rc != CCL_OK)
+        return rc;
+    if (H == 0 || W == 0) {
+        if (num_components_dev)
+            return map_cuda(cudaMemsetAsync(num_components_dev, 0, 4, s));
+        return CCL_OK;
+    }
+    Workspace *w = nullptr;
+    rc = get_workspace(s, HDR + main_layout(H, W).bytes, &w);
+    if (rc != CCL_OK)
+        return rc;
+    int32_t *k_dev = num_components_dev ? num_components_dev : static_cast<int32_t *>(w->dev);
+    return enqueue_one(img, H, W, pitch_bytes, labels, k_dev, w, static_cast<char *>(w->dev) + HDR, s);
+}
+
+int32_t ccl_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes, int32_t connectivity,
+                  int32_t *labels, int32_t *num_components, ccl_stream_t stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int32_t rc = check_args(img, H, W, pitch_bytes, connectivity, labels);
+    if (rc != CCL_OK)
+        return rc;
+    if (H == 0 || W == 0) {
+        if (num_components)
+            *num_components = 0;
+        return CCL_OK;
+    }
+    Workspace *w = nullptr;
+    rc = get_workspace(s, HDR + main_layout(H, W).bytes, &w);
+    if (rc != CCL_OK)
+        return rc;
+    int32_t *k_dev = static_cast<int32_t *>(w->dev);
+    rc = enqueue_one(img, H, W, pitch_bytes, labels, k_dev, w, static_cast<char *>(w->dev) + HDR, s);
+    if (rc != CCL_OK || !num_components)
+        return rc;
+    return read_k_and_status(w, k_dev, num_components, s);
+}
+
+int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch_bytes,
+                       int32_t connectivity, int32_t *labels_host, int32_t *num_components,
+                       ccl_stream_t stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int32_t rc = check_args(img_host, H, W, pitch_bytes, connectivity, labels_host);
+    if (rc != CCL_OK)
+        return rc;
+    if (H == 0 || W == 0) {
+        if (num_components)
+            *num_components = 0;
+        return CCL_OK;
+    }
+    const Layout L = main_layout(H, W);
+    const int64_t dpitch = (W + 15) & ~(int64_t)15;
+    const int64_t img_bytes = align256((int64_t)H * dpitch);
+    const int64_t lab_bytes = align256((int64_t)H * W * 4);
+    Workspace *w = nullptr;
+    rc = get_workspace(s, HDR + L.bytes + img_bytes + lab_bytes, &w);
+    if (rc != CCL_OK)
+        return rc;
+    char *base = static_cast<char *>(w->dev);
+    uint8_t *d_img = reinterpret_cast<uint8_t *>(base + HDR + L.bytes);
+    int32_t *d_lab = reinterpret_cast<int32_t *>(base + HDR + L.bytes + img_bytes);
+    cudaError_t e = cudaMemcpy2DAsync(d_img, (size_t)dpitch, img_host, (size_t)pitch_bytes, (size_t)W,
+                                      (size_t)H, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess)
+        return map_cuda(e);
+    int32_t *k_dev = reinterpret_cast<int32_t *>(base);
+    rc = enqueue_one(d_img, H, W, dpitch, d_lab, k_dev, w, base + HDR, s);
+    if (rc != CCL_OK)
+        return rc;
+    e = cudaMemcpyAsync(labels_host, d_lab, (size_t)H * W * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess)
+        return map_cuda(e);
+    int32_t k = 0;
+    rc = read_k_and_status(w, k_dev, &k, s);
+    if (rc == CCL_OK && num_components)
+        *num_components = k;
+    return rc;
+}
+
+int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, int32_t *num_components_dev,
+                        ccl_stream_t stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (n < 0 || (n > 0 && !imgs))
+        return CCL_ERR_INVALID_ARGUMENT;
+    int64_t need = HDR;
+    for (int32_t i = 0; i < n; i++) {
+        const int32_t rc = check_args(imgs[i].img, imgs[i].H, imgs[i].W, imgs[i].pitch_bytes, connectivity,
+                                      imgs[i].labels);
+        if (rc != CCL_OK)
+            return rc;
+        if (imgs[i].H > 0 && imgs[i].W > 0) {
+            const int64_t b = HDR + main_layout(imgs[i].H, imgs[i].W).bytes;
+            need = b > need ? b : need;
+        }
+    }
+    if (n == 0)
+        return CCL_OK;
+    Workspace *w = nullptr;
+    int32_t rc = get_workspace(s, need, &w);
+    if (rc != CCL_OK)
+        return rc;
+    for (int32_t i = 0; i < n; i++) {
+        const ccl_image &im = imgs[i];
+        int32_t *k_dev = num_components_dev ? num_components_dev + i : static_cast<int32_t *>(w->dev);
+        if (im.H == 0 || im.W == 0) {
+            if (num_components_dev) {
+                cudaError_t e = cudaMemsetAsync(k_dev, 0, 4, s);
+                if (e != cudaSuccess)
+                    return map_cuda(e);
+            }
+            continue;
+        }
+        rc = enqueue_one(im.img, im.H, im.W, im.pitch_bytes, im.labels, k_dev, w,
+                         static_cast<char *>(w->dev) + HDR, s);
+        if (rc != CCL_OK)
+            return rc;
+    }
+    return CCL_OK;
+}
+
+int32_t ccl_device_status(ccl_stream_t stream, int32_t *flags)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!flags)
+        return CCL_ERR_INVALID_ARGUMENT;
+    Workspace *w = nullptr;
+    int32_t rc = get_workspace(s, HDR, &w);
+    if (rc != CCL_OK)
+        return rc;
+    cudaError_t e = cudaMemcpyAsync(w->host_hdr + 1, static_cast<char *>(w->dev) + 4, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(static_cast<char *>(w->dev) + 4, 0, 4, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return map_cuda(e);
+    *flags = w->host_hdr[1];
+    return CCL_OK;
+}
+
+int32_t ccl_release(void)
+{
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    cudaError_t e = cudaDeviceSynchronize();
+    for (auto &kv : g_ws) {
+        if (kv.second.dev)
+            cudaFree(kv.second.dev);
+        if (kv.second.host_hdr)
+            cudaFreeHost(kv.second.host_hdr);
+    }
+    g_ws.clear();
+    return map_cuda(e);
+}
+
+int32_t ccl_profile_enable(int32_t on)
+{
+    g_prof_on.store(on ? 1 : 0);
+    return CCL_OK;
+}
+
+int32_t ccl_profile_reset(void)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &r : g_pending) {
+        cudaEventSynchronize(r.b);
+        g_event_pool.push_back(r.a);
+        g_event_pool.push_back(r.b);
+    }
+    g_pending.clear();
+    for (int k = 0; k < KID_COUNT; k++) {
+        g_launches[k].store(0);
+        g_ms[k] = 0.0;
+        g_timed[k] = 0;
+    }
+    return CCL_OK;
+}
+
+int32_t ccl_profile_read(ccl_kernel_time *out, int32_t max, int32_t *count)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &r : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            g_ms[r.kid] += ms;
+            g_timed[r.kid] += 1;
+        }
+        g_event_pool.push_back(r.a);
+        g_event_pool.push_back(r.b);
+    }
+    g_pending.clear();
+    if (count)
+        *count = KID_COUNT;
+    for (int k = 0; k < KID_COUNT && k < max; k++) {
+        memset(out[k].name, 0, sizeof(out[k].name));
+        strncpy(out[k].name, kernel_name(k), sizeof(out[k].name) - 1);
+        out[k].launches = g_launches[k].load();
+        out[k].total_ms = g_ms[k];
+    }
+    return CCL_OK;
+}
+
+}  // extern "C"

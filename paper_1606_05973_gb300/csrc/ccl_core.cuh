@@ -1,0 +1,880 @@
+// Tile-level phases of the GPU labelling path, written once as __host__ __device__
+// functions.  The CUDA kernels in ccl_kernels.cu run them with one CTA per tile and a
+// __syncthreads() between phases.
+//
+// Method (PARemSP, arXiv 1606.05973):
+//  * Section IV / Algorithm 7 split the image into chunks that are labelled
+//    independently, each with its own label range, and then merge the chunk boundaries
+//    with a concurrent Rem union (Algorithm 8).  Here the chunks are 2-D tiles of TH x TW
+//    pixels, one per CTA, labelled in shared memory.
+//  * Algorithm 6 (Scan_ARemSP) labels two rows at a time (e and g of Fig. 1b get one
+//    label).  Here a tile is a stack of two-row strips; under 8-connectivity every
+//    maximal run of columns that holds an object pixel in either row of a strip is
+//    connected (vertical and diagonal neighbours inside the strip), so each such
+//    "strip run" is one union-find node.
+//  * Algorithm 2 (merge, Rem's union with splicing) joins nodes; the lock of Algorithm 8
+//    becomes a compare-and-swap on the root and splices become atomic minimums.  Links
+//    always go from the larger index to the smaller one, so the root of every set is its
+//    smallest index (the invariant p[x] <= x of Algorithm 2).
+//  * A node's index is the tile raster position of its first pixel; the smallest index of
+//    a component is then its raster-first pixel, which fixes the canonical numbering
+//    (background 0, components 1..K in raster order of first pixels).
+//  * Algorithm 3 (flatten) and the labelling pass become: count global roots per
+//    (image row, tile column) segment, exclusive-scan the counts in raster order, give
+//    each root its rank + 1, and write every pixel's label.
+#pragma once
+#include <stdint.h>
+#include <string.h>
+
+#if defined(__CUDACC__)
+#define CCL_HD __host__ __device__ __forceinline__
+#else
+#define CCL_HD inline
+#endif
+
+namespace ccl {
+
+// ---- flags and sentinels ---------------------------------------------------------------
+constexpr int REDIR = 0x40000000;      // shared-memory slot that points at its run's node
+constexpr int LABFLAG = (int)0x80000000u;  // shared-memory slot that holds a final label
+constexpr int NONE = -1;
+constexpr int CONT = -2;
+
+// device status word bits (ccl.h exposes them as CCL_STATUS_*)
+constexpr int ST_LOOP_CAP = 1;   // a union-find loop exceeded its iteration cap
+constexpr int ST_BOUNDS = 2;     // a checked index was out of range (debug builds)
+constexpr int ST_BAD_VALUE = 4;  // a value that cannot occur was read (debug builds)
+
+constexpr int SMEM_LOOP_CAP = 1 << 20;
+constexpr int GLOBAL_LOOP_CAP = 1 << 24;
+
+// ---- portable bit and atomic helpers ---------------------------------------------------
+CCL_HD int popc32(uint32_t v)
+{
+#if defined(__CUDA_ARCH__)
+    return __popc(v);
+#else
+    return __builtin_popcount(v);
+#endif
+}
+CCL_HD int msb32(uint32_t v)  // v != 0
+{
+#if defined(__CUDA_ARCH__)
+    return 31 - __clz(v);
+#else
+    return 31 - __builtin_clz(v);
+#endif
+}
+CCL_HD int ctz32(uint32_t v)  // 32 for v == 0
+{
+#if defined(__CUDA_ARCH__)
+    return v ? __ffs((int)v) - 1 : 32;
+#else
+    return v ? __builtin_ctz(v) : 32;
+#endif
+}
+CCL_HD uint32_t mask_le(int b) { return b >= 31 ? 0xFFFFFFFFu : ((2u << b) - 1u); }
+CCL_HD uint32_t mask_lt(int b) { return b <= 0 ? 0u : (b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u)); }
+CCL_HD int imin(int a, int b) { return a < b ? a : b; }
+
+CCL_HD int at_cas(int *a, int cmp, int val)
+{
+#if defined(__CUDA_ARCH__)
+    return atomicCAS(a, cmp, val);
+#else
+    int old = *a;
+    if (old == cmp)
+        *a = val;
+    return old;
+#endif
+}
+CCL_HD void at_min(int *a, int v)
+{
+#if defined(__CUDA_ARCH__)
+    atomicMin(a, v);
+#else
+    if (v < *a)
+        *a = v;
+#endif
+}
+CCL_HD void at_or(uint32_t *a, uint32_t v)
+{
+#if defined(__CUDA_ARCH__)
+    atomicOr(a, v);
+#else
+    *a |= v;
+#endif
+}
+CCL_HD void flag_status(int *st, int f)
+{
+#if defined(__CUDA_ARCH__)
+    atomicOr(st, f);
+#else
+    *st |= f;
+#endif
+}
+// shared memory: a fresh read every time (no register caching across loop iterations)
+CCL_HD int ld_s(const int *a)
+{
+#if defined(__CUDA_ARCH__)
+    return *(const volatile int *)a;
+#else
+    return *a;
+#endif
+}
+// global memory written by other CTAs in the same launch: read through L2, not L1
+CCL_HD int ld_g(const int *a)
+{
+#if defined(__CUDA_ARCH__)
+    return __ldcg(a);
+#else
+    return *a;
+#endif
+}
+
+#if defined(CCL_DEBUG)
+template <class I> CCL_HD I chk(I i, I n, int *st)
+{
+    if (i < 0 || i >= n) {
+        flag_status(st, ST_BOUNDS);
+        return 0;
+    }
+    return i;
+}
+#define CCL_CHK(i, n, st) ::ccl::chk((i), (n), (st))
+#else
+#define CCL_CHK(i, n, st) (i)
+#endif
+
+// 16 bytes -> 16 object bits (bit i = byte i != 0)
+CCL_HD uint32_t nz_nibble(uint32_t v)
+{
+    // bit 7 of each byte is set iff the byte is non-zero (no carry leaves a byte)
+    const uint32_t m = (((v & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | v) & 0x80808080u;
+    // gather bits 0, 8, 16, 24 of (m >> 7) into bits 28..31 (cross terms land elsewhere)
+    return ((m >> 7) * 0x10204080u) >> 28;
+}
+CCL_HD uint32_t nz_mask16(const uint8_t *src)
+{
+    uint32_t v[4];
+#if defined(__CUDA_ARCH__)
+    const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(src));
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+#else
+    memcpy(v, src, 16);
+#endif
+    return nz_nibble(v[0]) | (nz_nibble(v[1]) << 4) | (nz_nibble(v[2]) << 8) | (nz_nibble(v[3]) << 12);
+}
+CCL_HD void store4(int *dst, const int v[4])
+{
+#if defined(__CUDA_ARCH__)
+    __stcs(reinterpret_cast<int4 *>(dst), make_int4(v[0], v[1], v[2], v[3]));
+#else
+    memcpy(dst, v, 16);
+#endif
+}
+
+// ---- tile configuration ----------------------------------------------------------------
+template <int TH_, int TW_, int NT_> struct Cfg {
+    static constexpr int TH = TH_;        // tile rows (even: whole strips)
+    static constexpr int TW = TW_;        // tile columns (multiple of 32)
+    static constexpr int NT = NT_;        // threads per CTA
+    static constexpr int NW = TW / 32;    // 32-bit words per tile row
+    static constexpr int NS = TH / 2;     // two-row strips per tile
+    static constexpr int CH = TW / 16;    // 16-byte chunks per tile row
+    static constexpr int ROWCAP = TW / 2; // max components whose first pixel is in one tile row
+    static_assert(TW % 32 == 0 && TH % 2 == 0, "tile shape");
+    static_assert(TH * TW < REDIR, "tile index range");
+};
+
+// Per-image device arguments.  All workspace arrays are owned by the caller of the kernels.
+struct Img {
+    const uint8_t *img;  // H rows of `pitch` bytes; object = non-zero byte
+    int64_t pitch;
+    int H, W;
+    int vec_in;          // img 16-byte aligned and pitch % 16 == 0
+    int nTX, nTY;        // tiles across / down
+    uint32_t *bitpack;   // [H][nTX*NW] object bits, bit b of word w = column 32w+b
+    int *P;              // global parents, index ((y*nTX + tx)*ROWCAP + j)
+    int *nseg;           // [H*nTX] local components whose first pixel lies in (y, tx)
+    int *cnt;            // [H*nTX] global roots per segment, then exclusive offsets
+    int *edgeRow;        // [nTY][2][nTX*TW] node id of top (0) / bottom (1) tile rows, -1 = bg
+    int *edgeCol;        // [nTX][2][nTY*TH] node id of left (0) / right (1) tile columns
+    int *bsum;           // scan block sums
+    int *K;              // number of components (device)
+    int *labels;         // [H][W] int32 output
+    int vec_out;         // labels 16-byte aligned and W % 4 == 0
+    int *status;         // device status word (ST_* bits)
+    int64_t nP, nSeg;    // sizes of P and nseg/cnt (for checked builds)
+};
+
+// Workspace layout for one image (byte offsets, each 256-byte aligned).
+struct Layout {
+    int nTX, nTY;
+    int64_t nSeg, nP, nBitWords, nEdgeRow, nEdgeCol, nBsum;
+    int64_t off_bitpack, off_P, off_nseg, off_cnt, off_edgeRow, off_edgeCol, off_bsum, bytes;
+};
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_NT = 256;
+constexpr int SCAN_BLOCK = SCAN_ITEMS * SCAN_NT;
+
+CCL_HD int64_t align256(int64_t v) { return (v + 255) & ~(int64_t)255; }
+
+template <class C> CCL_HD Layout plan_layout(int H, int W)
+{
+    Layout L;
+    L.nTX = (W + C::TW - 1) / C::TW;
+    L.nTY = (H + C::TH - 1) / C::TH;
+    L.nSeg = (int64_t)H * L.nTX;
+    L.nP = L.nSeg * C::ROWCAP;
+    L.nBitWords = (int64_t)H * L.nTX * C::NW;
+    L.nEdgeRow = (int64_t)L.nTY * 2 * L.nTX * C::TW;
+    L.nEdgeCol = (int64_t)L.nTX * 2 * L.nTY * C::TH;
+    L.nBsum = (L.nSeg + SCAN_BLOCK - 1) / SCAN_BLOCK + 1;
+    int64_t o = 0;
+    L.off_bitpack = o; o = align256(o + L.nBitWords * 4);
+    L.off_P = o; o = align256(o + L.nP * 4);
+    L.off_nseg = o; o = align256(o + L.nSeg * 4);
+    L.off_cnt = o; o = align256(o + L.nSeg * 4);
+    L.off_edgeRow = o; o = align256(o + L.nEdgeRow * 4);
+    L.off_edgeCol = o; o = align256(o + L.nEdgeCol * 4);
+    L.off_bsum = o; o = align256(o + L.nBsum * 4);
+    L.bytes = o;
+    return L;
+}
+
+// ---- shared-memory tile state ------------------------------------------------------------
+template <class C> struct Smem {
+    uint32_t bits[C::TH][C::NW];      // object bits of the tile (rows beyond H are 0)
+    uint32_t rootbits[C::TH][C::NW];  // local roots (first pixels of local components)
+    uint32_t startsM[C::NS][C::NW];   // run starts of (row 2s | row 2s+1)
+    int rootpre[C::TH][C::NW];        // exclusive popcount prefix of rootbits along a row
+    int cout_[C::NS][C::NW];          // run start covering bit 31 (CONT: from the left, NONE)
+    int carry[C::NS][C::NW];          // start of the run entering word w from the left
+    int par[C::TH * C::TW];           // union-find parents at node positions + slots
+};
+
+// Rem's union with splicing (Algorithm 2) made safe for concurrent threads (Algorithm 8):
+// the locked "still a root? then link" step is one compare-and-swap, and a splice
+// p[r] <- p[other] is an atomic minimum so that parents never grow.
+CCL_HD void rem_unite_s(int *par, int n, int x, int y, int *st)
+{
+    int rx = CCL_CHK(x, n, st), ry = CCL_CHK(y, n, st);
+    (void)n;
+    for (int it = 0; it < SMEM_LOOP_CAP; it++) {
+        const int px = CCL_CHK(ld_s(&par[rx]), n, st);
+        const int py = CCL_CHK(ld_s(&par[ry]), n, st);
+        if (px == py)
+            return;
+        if (px > py) {
+            if (px == rx) {
+                if (at_cas(&par[rx], rx, py) == rx)
+                    return;
+                continue;
+            }
+            at_min(&par[rx], py);
+            rx = px;
+        } else {
+            if (py == ry) {
+                if (at_cas(&par[ry], ry, px) == ry)
+                    return;
+                continue;
+            }
+            at_min(&par[ry], px);
+            ry = py;
+        }
+    }
+    flag_status(st, ST_LOOP_CAP);
+}
+
+CCL_HD void rem_unite_g(int *P, int64_t n, int x, int y, int *st)
+{
+    int rx = (int)CCL_CHK((int64_t)x, n, st), ry = (int)CCL_CHK((int64_t)y, n, st);
+    (void)n;
+    for (int it = 0; it < GLOBAL_LOOP_CAP; it++) {
+        const int px = (int)CCL_CHK((int64_t)ld_g(&P[rx]), n, st);
+        const int py = (int)CCL_CHK((int64_t)ld_g(&P[ry]), n, st);
+        if (px == py)
+            return;
+        if (px > py) {
+            if (px == rx) {
+                if (at_cas(&P[rx], rx, py) == rx)
+                    return;
+                continue;
+            }
+            at_min(&P[rx], py);
+            rx = px;
+        } else {
+            if (py == ry) {
+                if (at_cas(&P[ry], ry, px) == ry)
+                    return;
+                continue;
+            }
+            at_min(&P[ry], px);
+            ry = py;
+        }
+    }
+    flag_status(st, ST_LOOP_CAP);
+}
+
+CCL_HD int find_s(const int *par, int n, int x, int *st)
+{
+    (void)n;
+    x = CCL_CHK(x, n, st);
+    for (int it = 0; it < SMEM_LOOP_CAP; it++) {
+        const int p = CCL_CHK(ld_s(&par[x]), n, st);
+        if (p == x)
+            return x;
+        x = p;
+    }
+    flag_status(st, ST_LOOP_CAP);
+    return x;
+}
+
+CCL_HD int find_g(const int *P, int64_t n, int x, int *st)
+{
+    (void)n;
+    x = (int)CCL_CHK((int64_t)x, n, st);
+    for (int it = 0; it < GLOBAL_LOOP_CAP; it++) {
+        const int p = (int)CCL_CHK((int64_t)ld_g(&P[x]), n, st);
+        if (p == x)
+            return x;
+        x = p;
+    }
+    flag_status(st, ST_LOOP_CAP);
+    return x;
+}
+
+template <class C> struct Tile {
+    using S = Smem<C>;
+
+    // -- phase: image bytes -> object bits (and clear the root bits) ----------------------
+    CCL_HD static void load_image(const Img &a, S &s, int ty, int tx, int tid)
+    {
+        const int y0 = ty * C::TH, x0 = tx * C::TW;
+        uint16_t *half = reinterpret_cast<uint16_t *>(&s.bits[0][0]);
+        for (int q = tid; q < C::TH * C::CH; q += C::NT) {
+            const int r = q / C::CH, c = q % C::CH;
+            const int y = y0 + r, x = x0 + 16 * c;
+            uint32_t m = 0;
+            if (y < a.H && x < a.W) {
+                const uint8_t *src = a.img + (int64_t)y * a.pitch + x;
+                if (a.vec_in && x + 16 <= a.W) {
+                    m = nz_mask16(src);
+                } else {
+                    const int n = imin(16, a.W - x);
+                    for (int i = 0; i < n; i++)
+                        m |= (src[i] != 0 ? 1u : 0u) << i;
+                }
+            }
+            half[r * C::CH + c] = (uint16_t)m;  // little-endian: half 2w is the low half of word w
+        }
+        for (int q = tid; q < C::TH * C::NW; q += C::NT)
+            (&s.rootbits[0][0])[q] = 0u;
+    }
+
+    CCL_HD static void store_bitpack(const Img &a, const S &s, int ty, int tx, int tid)
+    {
+        const int y0 = ty * C::TH;
+        const int64_t WW = (int64_t)a.nTX * C::NW;
+        for (int q = tid; q < C::TH * C::NW; q += C::NT) {
+            const int r = q / C::NW, w = q % C::NW;
+            if (y0 + r < a.H)
+                a.bitpack[CCL_CHK((int64_t)(y0 + r) * WW + tx * C::NW + w, (int64_t)a.H * WW, a.status)] =
+                    s.bits[r][w];
+        }
+    }
+
+    CCL_HD static void load_bitpack(const Img &a, S &s, int ty, int tx, int tid)
+    {
+        const int y0 = ty * C::TH;
+        const int64_t WW = (int64_t)a.nTX * C::NW;
+        for (int q = tid; q < C::TH * C::NW; q += C::NT) {
+            const int r = q / C::NW, w = q % C::NW;
+            s.bits[r][w] = (y0 + r < a.H)
+                ? a.bitpack[CCL_CHK((int64_t)(y0 + r) * WW + tx * C::NW + w, (int64_t)a.H * WW, a.status)]
+                : 0u;
+            s.rootbits[r][w] = 0u;
+        }
+    }
+
+    CCL_HD static uint32_t strip_word(const S &s, int st, int w)
+    {
+        return s.bits[2 * st][w] | s.bits[2 * st + 1][w];
+    }
+
+    // Tile raster position of the first pixel (raster order) of the strip run that starts
+    // at bit b of word w: the first object pixel of the upper row inside the run if any,
+    // else the run's first column in the lower row.
+    CCL_HD static int first_pixel(const S &s, int st, int w, int b, uint32_t R0, uint32_t M)
+    {
+        const int x0 = w * 32 + b;
+        const int len = ctz32(~(M >> b));  // <= 32 - b
+        const uint32_t rm = (len >= 32) ? 0xFFFFFFFFu : (((1u << len) - 1u) << b);
+        const uint32_t hit = R0 & rm;
+        if (hit)
+            return 2 * st * C::TW + w * 32 + ctz32(hit);
+        if (b + len < 32)
+            return (2 * st + 1) * C::TW + x0;
+        for (int w2 = w + 1; w2 < C::NW; w2++) {
+            const uint32_t R0b = s.bits[2 * st][w2];
+            const uint32_t Mb = R0b | s.bits[2 * st + 1][w2];
+            const int l2 = ctz32(~Mb);
+            const uint32_t rm2 = (l2 >= 32) ? 0xFFFFFFFFu : ((1u << l2) - 1u);
+            const uint32_t h2 = R0b & rm2;
+            if (h2)
+                return 2 * st * C::TW + w2 * 32 + ctz32(h2);
+            if (l2 < 32)
+                break;
+        }
+        return (2 * st + 1) * C::TW + x0;
+    }
+
+    // -- phase: strip runs -> union-find nodes ----------------------------------------------
+    // Node of a run: par[id] = id at the run's first pixel.  The run-start slot (upper row,
+    // first column) is either that node or an unused position that then points at it.
+    CCL_HD static void runs(const Img &a, S &s, int tid)
+    {
+        (void)a;
+        for (int u = tid; u < C::NS * C::NW; u += C::NT) {
+            const int st = u / C::NW, w = u % C::NW;
+            const uint32_t R0 = s.bits[2 * st][w];
+            const uint32_t M = R0 | s.bits[2 * st + 1][w];
+            const uint32_t prev = (w > 0) ? (strip_word(s, st, w - 1) >> 31) : 0u;
+            const uint32_t starts = M & ~((M << 1) | prev);
+            s.startsM[st][w] = starts;
+            s.cout_[st][w] = (M >> 31) ? (starts ? w * 32 + msb32(starts) : CONT) : NONE;
+            uint32_t todo = starts;
+            while (todo) {
+                const int b = ctz32(todo);
+                todo &= todo - 1u;
+                const int x0 = w * 32 + b;
+                const int id = first_pixel(s, st, w, b, R0, M);
+                const int slot = 2 * st * C::TW + x0;
+                s.par[CCL_CHK(id, C::TH * C::TW, a.status)] = id;
+                if (slot != id)
+                    s.par[slot] = REDIR | id;
+            }
+        }
+    }
+
+    // -- phase: per strip, the start of the run that enters each word from the left --------
+    CCL_HD static void carry_scan(S &s, int tid)
+    {
+        for (int st = tid; st < C::NS; st += C::NT) {
+            int c = NONE;
+            s.carry[st][0] = NONE;
+            for (int w = 1; w < C::NW; w++) {
+                const int o = s.cout_[st][w - 1];
+                c = (o == CONT) ? c : o;
+                s.carry[st][w] = c;
+            }
+        }
+    }
+
+    // start column of the strip run covering object column x of strip st
+    CCL_HD static int run_start(const S &s, int st, int x, int *stw)
+    {
+        const int w = x >> 5, b = x & 31;
+        const uint32_t le = s.startsM[st][w] & mask_le(b);
+        const int r = le ? (w * 32 + msb32(le)) : s.carry[st][w];
+#if defined(CCL_DEBUG)
+        if (r < 0 || r > x) {
+            flag_status(stw, ST_BAD_VALUE);
+            return x;
+        }
+#else
+        (void)stw;
+#endif
+        return r;
+    }
+
+    CCL_HD static int node_of_slot(const S &s, int st, int x0)
+    {
+        const int slot = 2 * st * C::TW + x0;
+        const int v = ld_s(&s.par[slot]);
+        const int node = (v & REDIR) ? (v & ~REDIR) : slot;
+#if defined(CCL_DEBUG)
+        if (node < 0 || node >= C::TH * C::TW)
+            return 0;
+#endif
+        return node;
+    }
+
+    CCL_HD static int node_of(const S &s, int st, int x, int *stw)
+    {
+        return node_of_slot(s, st, run_start(s, st, x, stw));
+    }
+
+    // -- phase: join strip runs that touch across strip boundaries ------------------------
+    // Rows A = 2s-1 (last row of strip s-1) and B = 2s (first row of strip s).  Every pair
+    // of single-row runs (one in A, one in B) that are 8-adjacent is found exactly once:
+    // either the B run starts where A has a pixel at that column or one to the left, or
+    // the A run starts one column right of a B pixel.
+    CCL_HD static void unions(const Img &a, S &s, int tid)
+    {
+        for (int u = tid; u < C::NS * C::NW; u += C::NT) {
+            const int st = u / C::NW, w = u % C::NW;
+            if (st == 0)
+                continue;
+            const uint32_t A = s.bits[2 * st - 1][w], B = s.bits[2 * st][w];
+            const uint32_t Ap = (w > 0) ? (s.bits[2 * st - 1][w - 1] >> 31) : 0u;
+            const uint32_t Bp = (w > 0) ? (s.bits[2 * st][w - 1] >> 31) : 0u;
+            const uint32_t Ash = (A << 1) | Ap, Bsh = (B << 1) | Bp;
+            uint32_t ev1 = (B & ~Bsh) & (A | Ash);
+            uint32_t ev2 = (A & ~Ash) & Bsh;
+            while (ev1) {
+                const int b = ctz32(ev1);
+                ev1 &= ev1 - 1u;
+                const int xb = w * 32 + b;
+                const int xa = ((A >> b) & 1u) ? xb : xb - 1;
+                rem_unite_s(s.par, C::TH * C::TW, node_of(s, st, xb, a.status), node_of(s, st - 1, xa, a.status), a.status);
+            }
+            while (ev2) {
+                const int b = ctz32(ev2);
+                ev2 &= ev2 - 1u;
+                const int xa = w * 32 + b;
+                rem_unite_s(s.par, C::TH * C::TW, node_of(s, st - 1, xa, a.status), node_of(s, st, xa - 1, a.status), a.status);
+            }
+        }
+    }
+
+    // -- phase: resolve every node to its root; mark roots ---------------------------------
+    CCL_HD static void roots(const Img &a, S &s, int tid)
+    {
+        for (int u = tid; u < C::NS * C::NW; u += C::NT) {
+            const int st = u / C::NW, w = u % C::NW;
+            uint32_t todo = s.startsM[st][w];
+            while (todo) {
+                const int b = ctz32(todo);
+                todo &= todo - 1u;
+                const int node = node_of_slot(s, st, w * 32 + b);
+                const int r = find_s(s.par, C::TH * C::TW, node, a.status);
+                s.par[node] = r;
+                if (r == node)
+                    at_or(&s.rootbits[node / C::TW][(node % C::TW) >> 5], 1u << (node & 31));
+            }
+        }
+    }
+
+    // -- phase: rank of roots along each tile row; segment sizes --------------------------
+    CCL_HD static void root_prefix(const Img &a, S &s, int ty, int tx, int tid, bool write_nseg)
+    {
+        const int y0 = ty * C::TH;
+        for (int r = tid; r < C::TH; r += C::NT) {
+            int pre = 0;
+            for (int w = 0; w < C::NW; w++) {
+                s.rootpre[r][w] = pre;
+                pre += popc32(s.rootbits[r][w]);
+            }
+            if (write_nseg && y0 + r < a.H)
+                a.nseg[CCL_CHK((int64_t)(y0 + r) * a.nTX + tx, a.nSeg, a.status)] = pre;
+        }
+    }
+
+    // global node id of a local root at tile raster position `root`
+    CCL_HD static int64_t gid_of(const Img &a, const S &s, int ty, int tx, int root)
+    {
+        const int rr = root / C::TW, cc = root % C::TW;
+        const int j = s.rootpre[rr][cc >> 5] + popc32(s.rootbits[rr][cc >> 5] & mask_lt(cc & 31));
+        return ((int64_t)(ty * C::TH + rr) * a.nTX + tx) * C::ROWCAP + j;
+    }
+
+    // -- phase: one global union-find node per local root, P[id] = id ---------------------
+    CCL_HD static void init_nodes(const Img &a, const S &s, int ty, int tx, int tid)
+    {
+        for (int q = tid; q < C::TH * C::NW; q += C::NT) {
+            const int r = q / C::NW, w = q % C::NW;
+            uint32_t rb = s.rootbits[r][w];
+            int64_t gid = ((int64_t)(ty * C::TH + r) * a.nTX + tx) * C::ROWCAP + s.rootpre[r][w];
+            while (rb) {
+                rb &= rb - 1u;
+                a.P[CCL_CHK(gid, a.nP, a.status)] = (int)gid;
+                gid++;
+            }
+        }
+    }
+
+    CCL_HD static int pixel_gid(const Img &a, const S &s, int ty, int tx, int r, int x)
+    {
+        if (!((s.bits[r][x >> 5] >> (x & 31)) & 1u))
+            return -1;
+        const int node = node_of(s, r >> 1, x, a.status);
+        const int root = CCL_CHK(ld_s(&s.par[node]), C::TH * C::TW, a.status);
+        return (int)gid_of(a, s, ty, tx, root);
+    }
+
+    // -- phase: node ids along the tile's four edges (for the boundary merge) -------------
+    CCL_HD static void edges(const Img &a, const S &s, int ty, int tx, int tid)
+    {
+        const int64_t WP = (int64_t)a.nTX * C::TW, HP = (int64_t)a.nTY * C::TH;
+        for (int x = tid; x < C::TW; x += C::NT) {
+            a.edgeRow[CCL_CHK((int64_t)(2 * ty) * WP + tx * C::TW + x, (int64_t)a.nTY * 2 * WP, a.status)] =
+                pixel_gid(a, s, ty, tx, 0, x);
+            a.edgeRow[CCL_CHK((int64_t)(2 * ty + 1) * WP + tx * C::TW + x, (int64_t)a.nTY * 2 * WP, a.status)] =
+                pixel_gid(a, s, ty, tx, C::TH - 1, x);
+        }
+        for (int r = tid; r < C::TH; r += C::NT) {
+            a.edgeCol[CCL_CHK((int64_t)(2 * tx) * HP + ty * C::TH + r, (int64_t)a.nTX * 2 * HP, a.status)] =
+                pixel_gid(a, s, ty, tx, r, 0);
+            a.edgeCol[CCL_CHK((int64_t)(2 * tx + 1) * HP + ty * C::TH + r, (int64_t)a.nTX * 2 * HP, a.status)] =
+                pixel_gid(a, s, ty, tx, r, C::TW - 1);
+        }
+    }
+
+    // -- final pass: labels of this tile's local roots from the global table ---------------
+    // After flatten P[id] is either -(final label) (a global root) or the id of its global
+    // root, whose entry holds -(final label).
+    CCL_HD static void root_labels_to_smem(const Img &a, S &s, int ty, int tx, int tid)
+    {
+        for (int q = tid; q < C::TH * C::NW; q += C::NT) {
+            const int r = q / C::NW, w = q % C::NW;
+            uint32_t rb = s.rootbits[r][w];
+            int64_t gid = ((int64_t)(ty * C::TH + r) * a.nTX + tx) * C::ROWCAP + s.rootpre[r][w];
+            while (rb) {
+                const int b = ctz32(rb);
+                rb &= rb - 1u;
+                const int v = a.P[CCL_CHK(gid, a.nP, a.status)];
+                int lab = (v < 0) ? -v : -a.P[CCL_CHK((int64_t)v, a.nP, a.status)];
+#if defined(CCL_DEBUG)
+                if (lab <= 0) {
+                    flag_status(a.status, ST_BAD_VALUE);
+                    lab = 0;
+                }
+#endif
+                s.par[r * C::TW + w * 32 + b] = lab | LABFLAG;
+                gid++;
+            }
+        }
+    }
+
+    // every run-start slot receives its run's final label (flagged)
+    CCL_HD static void run_labels(const Img &a, S &s, int tid)
+    {
+        for (int u = tid; u < C::NS * C::NW; u += C::NT) {
+            const int st = u / C::NW, w = u % C::NW;
+            uint32_t todo = s.startsM[st][w];
+            while (todo) {
+                const int b = ctz32(todo);
+                todo &= todo - 1u;
+                const int slot = 2 * st * C::TW + w * 32 + b;
+                const int v = ld_s(&s.par[slot]);
+                int lab;
+                if (v < 0) {
+                    lab = v;  // the slot is a root: already a flagged label
+                } else {
+                    const int node = (v & REDIR) ? (v & ~REDIR) : slot;
+                    const int pv = (node == slot) ? v : ld_s(&s.par[node]);
+                    lab = (pv < 0) ? pv : ld_s(&s.par[CCL_CHK(pv, C::TH * C::TW, a.status)]);
+                }
+#if defined(CCL_DEBUG)
+                if (lab >= 0)
+                    flag_status(a.status, ST_BAD_VALUE);
+#endif
+                s.par[slot] = lab;
+            }
+        }
+    }
+
+    CCL_HD static void write_labels(const Img &a, const S &s, int ty, int tx, int tid)
+    {
+        const int y0 = ty * C::TH, x0 = tx * C::TW;
+        constexpr int G = C::TW / 4;
+        for (int q = tid; q < C::TH * G; q += C::NT) {
+            const int r = q / G, x = (q % G) * 4;
+            const int y = y0 + r, gx = x0 + x;
+            if (y >= a.H || gx >= a.W)
+                continue;
+            const int st = r >> 1;
+            const uint32_t row = s.bits[r][x >> 5];
+            int v[4];
+            for (int k = 0; k < 4; k++) {
+                const int b = (x & 31) + k;
+                if ((row >> b) & 1u) {
+                    const int xs = run_start(s, st, x + k, a.status);
+                    v[k] = s.par[2 * st * C::TW + xs] & 0x7FFFFFFF;
+                } else {
+                    v[k] = 0;
+                }
+            }
+            int *dst = a.labels + (int64_t)y * a.W + gx;
+            if (a.vec_out && gx + 4 <= a.W) {
+                store4(dst, v);
+            } else {
+                for (int k = 0; k < 4; k++)
+                    if (gx + k < a.W)
+                        dst[k] = v[k];
+            }
+        }
+    }
+};
+
+// ---- boundary merge (between tiles), Algorithm 7's boundary loop -------------------------
+// For an object pixel e on one side of a tile edge, with b the pixel facing it and a, c
+// the two diagonal ones: join e with b if b is an object pixel, else with a and c.  A pair
+// already joined through the previous pixel along the edge (same node id) is skipped.
+template <class C> CCL_HD void merge_h(const Img &a, int ty, int x)
+{
+    const int64_t WP = (int64_t)a.nTX * C::TW;
+    const int *top = a.edgeRow + (int64_t)(2 * ty) * WP;
+    const int *above = a.edgeRow + (int64_t)(2 * ty - 1) * WP;
+    const int e = top[x];
+    if (e < 0)
+        return;
+    const int b = above[x];
+    const int aa = (x > 0) ? above[x - 1] : -1;
+    const int c = (x + 1 < a.W) ? above[x + 1] : -1;
+    const bool same_prev = (x > 0) && top[x - 1] == e;
+    if (b >= 0) {
+        if (!same_prev)
+            rem_unite_g(a.P, a.nP, e, b, a.status);
+    } else {
+        if (aa >= 0 && !same_prev)
+            rem_unite_g(a.P, a.nP, e, aa, a.status);
+        if (c >= 0)
+            rem_unite_g(a.P, a.nP, e, c, a.status);
+    }
+}
+
+template <class C> CCL_HD void merge_v(const Img &a, int tx, int y)
+{
+    const int64_t HP = (int64_t)a.nTY * C::TH;
+    const int *left = a.edgeCol + (int64_t)(2 * tx - 1) * HP;
+    const int *me = a.edgeCol + (int64_t)(2 * tx) * HP;
+    const int e = me[y];
+    if (e < 0)
+        return;
+    const int yb0 = (y / C::TH) * C::TH;
+    const int yb1 = imin(yb0 + C::TH, a.H);
+    const int b = left[y];
+    const int aa = (y - 1 >= yb0) ? left[y - 1] : -1;
+    const int c = (y + 1 < yb1) ? left[y + 1] : -1;
+    const bool same_prev = (y - 1 >= yb0) && me[y - 1] == e;
+    if (b >= 0) {
+        if (!same_prev)
+            rem_unite_g(a.P, a.nP, e, b, a.status);
+    } else {
+        if (aa >= 0 && !same_prev)
+            rem_unite_g(a.P, a.nP, e, aa, a.status);
+        if (c >= 0)
+            rem_unite_g(a.P, a.nP, e, c, a.status);
+    }
+}
+
+// ---- flatten (Algorithm 3) over global nodes, per segment -------------------------------
+template <class C> CCL_HD void flatten_count(const Img &a, int64_t seg)
+{
+    const int n = a.nseg[seg];
+    int c = 0;
+    for (int j = 0; j < n; j++) {
+        const int id = (int)CCL_CHK(seg * C::ROWCAP + j, a.nP, a.status);
+        const int r = find_g(a.P, a.nP, id, a.status);
+        if (r != id)
+            a.P[id] = r;
+        else
+            c++;
+    }
+    a.cnt[seg] = c;
+}
+
+// roots get -(offset + rank within segment + 1): their final label, negated
+template <class C> CCL_HD void label_roots(const Img &a, int64_t seg)
+{
+    const int n = a.nseg[seg];
+    int lab = a.cnt[seg];
+    for (int j = 0; j < n; j++) {
+        const int id = (int)CCL_CHK(seg * C::ROWCAP + j, a.nP, a.status);
+        if (a.P[id] == id) {
+            lab++;
+            a.P[id] = -lab;
+        }
+    }
+}
+
+// ---- exclusive scan of the per-segment root counts (three phases) ----------------------
+struct ScanSmem {
+    int part[SCAN_NT];
+};
+
+CCL_HD void scan_block_sum(const int *v, int64_t n, int *bsum, ScanSmem &s, int b, int tid)
+{
+    const int64_t base = (int64_t)b * SCAN_BLOCK + (int64_t)tid * SCAN_ITEMS;
+    int acc = 0;
+    for (int i = 0; i < SCAN_ITEMS; i++)
+        if (base + i < n)
+            acc += v[base + i];
+    s.part[tid] = acc;
+    (void)bsum;
+}
+CCL_HD void scan_block_sum_finish(int *bsum, ScanSmem &s, int b, int tid)
+{
+    if (tid == 0) {
+        int acc = 0;
+        for (int i = 0; i < SCAN_NT; i++)
+            acc += s.part[i];
+        bsum[b] = acc;
+    }
+}
+// one CTA: exclusive scan of the block sums (serial over CTA partials), total -> *K
+CCL_HD void scan_top(int *bsum, int64_t nb, int *K, ScanSmem &s, int tid, int phase)
+{
+    const int64_t per = (nb + SCAN_NT - 1) / SCAN_NT;
+    const int64_t lo = (int64_t)tid * per;
+    const int64_t hi = (lo + per < nb) ? lo + per : nb;
+    if (phase == 0) {
+        int acc = 0;
+        for (int64_t i = lo; i < hi; i++)
+            acc += bsum[i];
+        s.part[tid] = acc;
+    } else if (phase == 1) {
+        if (tid == 0) {
+            int acc = 0;
+            for (int i = 0; i < SCAN_NT; i++) {
+                const int t = s.part[i];
+                s.part[i] = acc;
+                acc += t;
+            }
+            *K = acc;
+        }
+    } else {
+        int acc = s.part[tid];
+        for (int64_t i = lo; i < hi; i++) {
+            const int t = bsum[i];
+            bsum[i] = acc;
+            acc += t;
+        }
+    }
+}
+CCL_HD void scan_apply(int *v, int64_t n, const int *bsum, ScanSmem &s, int b, int tid, int phase)
+{
+    const int64_t base = (int64_t)b * SCAN_BLOCK + (int64_t)tid * SCAN_ITEMS;
+    if (phase == 0) {
+        int acc = 0;
+        for (int i = 0; i < SCAN_ITEMS; i++)
+            if (base + i < n)
+                acc += v[base + i];
+        s.part[tid] = acc;
+    } else if (phase == 1) {
+        if (tid == 0) {
+            int acc = bsum[b];
+            for (int i = 0; i < SCAN_NT; i++) {
+                const int t = s.part[i];
+                s.part[i] = acc;
+                acc += t;
+            }
+        }
+    } else {
+        int acc = s.part[tid];
+        for (int i = 0; i < SCAN_ITEMS; i++)
+            if (base + i < n) {
+                const int t = v[base + i];
+                v[base + i] = acc;
+                acc += t;
+            }
+    }
+}
+
+}  // namespace ccl

@@ -1,0 +1,44 @@
+// Internal interface between the C ABI (ccl_api.cu) and the kernel launchers
+// (ccl_kernels.cu).  Not installed; the public interface is include/ccl.h.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ccl_core.cuh"
+
+namespace ccl {
+
+// Kernels of the single-image path, in launch order.
+enum KernelId {
+    KID_TILE_LOCAL = 0,  // image -> bit tiles, local union-find, local roots, edges
+    KID_MERGE,           // boundary merge across tile edges (global Rem union)
+    KID_FLATTEN,         // global roots: flatten + count per segment
+    KID_SCAN_SUM,        // exclusive scan of the per-segment root counts (3 launches)
+    KID_SCAN_TOP,
+    KID_SCAN_APPLY,
+    KID_LABEL_ROOTS,     // final label of each global root
+    KID_FINAL,           // recompute local structure, write int32 labels
+    KID_COUNT
+};
+const char *kernel_name(int kid);
+
+// Launch-side hooks implemented by the API layer (profiling and launch counting).
+void prof_begin(int kid, cudaStream_t s);
+void prof_end(int kid, cudaStream_t s);
+
+// Tile shape used by the single-image path.
+using MainCfg = Cfg<64, 256, 256>;
+
+Layout main_layout(int H, int W);
+
+// Fill the workspace pointers of `a` (everything but img, labels, K and status) from the
+// base of the image's part of a workspace.
+void bind_workspace(Img &a, const Layout &L, void *ws);
+
+// Enqueue the whole labelling path for one image on `s`.  `a` must be fully bound.
+cudaError_t launch_label(const Img &a, const Layout &L, cudaStream_t s);
+
+// One-time per-process setup of kernel attributes (dynamic shared memory).
+cudaError_t kernels_init();
+
+}  // namespace ccl

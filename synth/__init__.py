@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "bernoulli", "blobs", "serpentine", "checkerboard", "dot_lattice", "striped_rows",
-    "batch_specs", "make_batch_image", "sha256", "sweep_8192", "pad_pitch",
+    "batch_specs", "make_batch_image", "sha256", "sweep_8192", "pad_pitch", "blobs_device",
 ]
 
 
@@ -103,6 +103,29 @@ def blobs(h: int, w: int, sigma: float, seed: int, chunk_rows: int = 2048) -> np
         col = np.fft.irfft(np.fft.rfft(noise[:, x0:x1], axis=0) * fk[:, None], n=h, axis=0)
         out[:, x0:x1] = col > 0
     return out
+
+
+def blobs_device(h: int, w: int, sigma: float, seed: int, device):
+    """Same recipe as ``blobs`` (numpy PCG64 noise, periodic Gaussian smoothing truncated at
+    4 sigma, threshold at 0), with the smoothing done by torch FFTs on ``device``.  Returns a
+    uint8 torch tensor on ``device``; callers that need the bytes on the host copy them, so
+    every consumer still sees identical bytes."""
+    import torch
+
+    rng = _rng(seed)
+    noise = torch.from_numpy(rng.standard_normal((h, w), dtype=np.float32)).to(device)
+    k = _gauss_kernel(sigma)
+    r = (k.size - 1) // 2
+    for axis in (0, 1):
+        n = noise.shape[axis]
+        kk = np.zeros(n, dtype=np.float32)
+        for i, v in enumerate(k):
+            kk[(i - r) % n] += v
+        fk = torch.fft.rfft(torch.from_numpy(kk).to(device))
+        shape = [1, 1]
+        shape[axis] = fk.numel()
+        noise = torch.fft.irfft(torch.fft.rfft(noise, dim=axis) * fk.reshape(shape), n=n, dim=axis)
+    return (noise > 0).to(torch.uint8)
 
 
 def serpentine(h: int, w: int) -> np.ndarray:

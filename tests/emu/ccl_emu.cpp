@@ -1,0 +1,178 @@
+// Host emulation of the GPU labelling path, for tests only.
+//
+// It compiles the very same tile phases (paper_1606_05973_gb300/csrc/ccl_core.cuh) with a
+// host C++ compiler and runs every CTA's threads one after another within each phase, in
+// a seeded random order, with the shared-memory tile poisoned before use.  Built with
+// AddressSanitizer it checks the kernels' index arithmetic and the absence of reads of
+// unwritten shared memory on the CPU, before anything runs on a GPU.  The library never
+// loads this file; it is not a way to label images in production.
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <random>
+#include <vector>
+
+#include "../../paper_1606_05973_gb300/csrc/ccl_core.cuh"
+
+using namespace ccl;
+
+namespace {
+
+template <class C> struct Emu {
+    std::mt19937_64 rng;
+    std::vector<int> order;
+
+    explicit Emu(uint64_t seed) : rng(seed), order(C::NT) { std::iota(order.begin(), order.end(), 0); }
+
+    template <class F> void phase(F f)
+    {
+        std::shuffle(order.begin(), order.end(), rng);
+        for (int t : order)
+            f(t);
+    }
+
+    int64_t run(const uint8_t *img, int H, int W, int64_t pitch, int32_t *labels, int32_t *status)
+    {
+        if (H == 0 || W == 0)
+            return 0;
+        const Layout L = plan_layout<C>(H, W);
+        std::vector<unsigned char> ws((size_t)L.bytes + 64);
+        // poison the workspace: every value the kernels read must have been written
+        memset(ws.data(), 0x7B, ws.size());
+        int K = -1;
+        Img a;
+        memset(&a, 0, sizeof(a));
+        a.img = img;
+        a.pitch = pitch;
+        a.H = H;
+        a.W = W;
+        a.vec_in = ((uintptr_t)img % 16 == 0) && (pitch % 16 == 0);
+        a.labels = labels;
+        a.vec_out = ((uintptr_t)labels % 16 == 0) && (W % 4 == 0);
+        a.K = &K;
+        a.status = status;
+        char *b = (char *)ws.data();
+        a.nTX = L.nTX;
+        a.nTY = L.nTY;
+        a.bitpack = (uint32_t *)(b + L.off_bitpack);
+        a.P = (int *)(b + L.off_P);
+        a.nseg = (int *)(b + L.off_nseg);
+        a.cnt = (int *)(b + L.off_cnt);
+        a.edgeRow = (int *)(b + L.off_edgeRow);
+        a.edgeCol = (int *)(b + L.off_edgeCol);
+        a.bsum = (int *)(b + L.off_bsum);
+        a.nP = L.nP;
+        a.nSeg = L.nSeg;
+
+        const int ntiles = L.nTX * L.nTY;
+        std::vector<int> tiles(ntiles);
+        std::iota(tiles.begin(), tiles.end(), 0);
+        auto *s = new Smem<C>;
+        using T = Tile<C>;
+
+        // tile_local
+        std::shuffle(tiles.begin(), tiles.end(), rng);
+        for (int tile : tiles) {
+            const int ty = tile / a.nTX, tx = tile % a.nTX;
+            memset(s, 0x7F, sizeof(*s));
+            phase([&](int t) { T::load_image(a, *s, ty, tx, t); });
+            phase([&](int t) { T::store_bitpack(a, *s, ty, tx, t); T::runs(a, *s, t); });
+            phase([&](int t) { T::carry_scan(*s, t); });
+            phase([&](int t) { T::unions(a, *s, t); });
+            phase([&](int t) { T::roots(a, *s, t); });
+            phase([&](int t) { T::root_prefix(a, *s, ty, tx, t, true); });
+            phase([&](int t) { T::init_nodes(a, *s, ty, tx, t); T::edges(a, *s, ty, tx, t); });
+        }
+        // boundary merge, items in random order
+        {
+            const int64_t nh = (int64_t)(a.nTY - 1) * a.W, nv = (int64_t)(a.nTX - 1) * a.H;
+            std::vector<int64_t> items(nh + nv);
+            std::iota(items.begin(), items.end(), 0);
+            std::shuffle(items.begin(), items.end(), rng);
+            for (int64_t i : items) {
+                if (i < nh)
+                    merge_h<C>(a, 1 + (int)(i / a.W), (int)(i % a.W));
+                else
+                    merge_v<C>(a, 1 + (int)((i - nh) / a.H), (int)((i - nh) % a.H));
+            }
+        }
+        {
+            std::vector<int64_t> segs(L.nSeg);
+            std::iota(segs.begin(), segs.end(), 0);
+            std::shuffle(segs.begin(), segs.end(), rng);
+            for (int64_t sg : segs)
+                flatten_count<C>(a, sg);
+        }
+        {
+            const int64_t nb = (L.nSeg + SCAN_BLOCK - 1) / SCAN_BLOCK;
+            ScanSmem ss;
+            for (int64_t bb = 0; bb < nb; bb++) {
+                phase256([&](int t) { scan_block_sum(a.cnt, L.nSeg, a.bsum, ss, (int)bb, t); });
+                phase256([&](int t) { scan_block_sum_finish(a.bsum, ss, (int)bb, t); });
+            }
+            for (int ph = 0; ph < 3; ph++)
+                phase256([&](int t) { scan_top(a.bsum, nb, a.K, ss, t, ph); });
+            for (int64_t bb = 0; bb < nb; bb++)
+                for (int ph = 0; ph < 3; ph++)
+                    phase256([&](int t) { scan_apply(a.cnt, L.nSeg, a.bsum, ss, (int)bb, t, ph); });
+        }
+        {
+            std::vector<int64_t> segs(L.nSeg);
+            std::iota(segs.begin(), segs.end(), 0);
+            std::shuffle(segs.begin(), segs.end(), rng);
+            for (int64_t sg : segs)
+                label_roots<C>(a, sg);
+        }
+        std::shuffle(tiles.begin(), tiles.end(), rng);
+        for (int tile : tiles) {
+            const int ty = tile / a.nTX, tx = tile % a.nTX;
+            memset(s, 0x7F, sizeof(*s));
+            phase([&](int t) { T::load_bitpack(a, *s, ty, tx, t); });
+            phase([&](int t) { T::runs(a, *s, t); });
+            phase([&](int t) { T::carry_scan(*s, t); });
+            phase([&](int t) { T::unions(a, *s, t); });
+            phase([&](int t) { T::roots(a, *s, t); });
+            phase([&](int t) { T::root_prefix(a, *s, ty, tx, t, false); });
+            phase([&](int t) { T::root_labels_to_smem(a, *s, ty, tx, t); });
+            phase([&](int t) { T::run_labels(a, *s, t); });
+            phase([&](int t) { T::write_labels(a, *s, ty, tx, t); });
+        }
+        delete s;
+        return K;
+    }
+
+    template <class F> void phase256(F f)
+    {
+        std::vector<int> o(SCAN_NT);
+        std::iota(o.begin(), o.end(), 0);
+        std::shuffle(o.begin(), o.end(), rng);
+        for (int t : o)
+            f(t);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+// shapes: 0 = the library's main tile (64x256, 256 threads); 1 = small tile (4x32, 32 threads)
+int64_t emu_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t *labels,
+                  uint64_t seed, int32_t shape, int32_t *status)
+{
+    *status = 0;
+    if (shape == 0) {
+        Emu<Cfg<64, 256, 256>> e(seed);
+        return e.run(img, H, W, pitch, labels, status);
+    } else if (shape == 1) {
+        Emu<Cfg<4, 32, 32>> e(seed);
+        return e.run(img, H, W, pitch, labels, status);
+    } else {
+        Emu<Cfg<8, 64, 64>> e(seed);
+        return e.run(img, H, W, pitch, labels, status);
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+"""Builds and drives the host emulation of the GPU path (tests only).
+
+``build(sanitize)`` compiles tests/emu/ccl_emu.cpp with g++ (optionally with
+AddressSanitizer and UBSan); ``Emu(path).label(img, seed, shape)`` runs it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(HERE, "_build")
+SRC = os.path.join(HERE, "ccl_emu.cpp")
+CORE = os.path.join(HERE, "..", "..", "paper_1606_05973_gb300", "csrc", "ccl_core.cuh")
+
+SAN = ["-fsanitize=address,undefined", "-fno-omit-frame-pointer", "-fno-sanitize-recover=undefined"]
+
+
+def asan_runtime() -> str | None:
+    r = subprocess.run(["gcc", "-print-file-name=libasan.so"], capture_output=True, text=True)
+    p = r.stdout.strip()
+    return p if os.path.isabs(p) and os.path.exists(p) else None
+
+
+def build(sanitize: bool = True) -> str:
+    os.makedirs(OUT, exist_ok=True)
+    so = os.path.join(OUT, "libccl_emu_san.so" if sanitize else "libccl_emu.so")
+    newest = max(os.path.getmtime(SRC), os.path.getmtime(CORE))
+    if os.path.exists(so) and os.path.getmtime(so) >= newest:
+        return so
+    cmd = ["g++", "-std=c++17", "-O1", "-g", "-DCCL_DEBUG", "-shared", "-fPIC", "-o", so, SRC]
+    if sanitize:
+        cmd[1:1] = SAN
+    subprocess.run(cmd, check=True)
+    return so
+
+
+class Emu:
+    def __init__(self, path: str):
+        self.lib = ctypes.CDLL(path)
+        f = self.lib.emu_label
+        f.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                      ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p]
+        f.restype = ctypes.c_int64
+
+    def label(self, img: np.ndarray, seed: int = 1, shape: int = 0, pitch: int | None = None, fill: int = 7):
+        import synth
+
+        h, w = img.shape
+        if pitch is None:
+            src = np.ascontiguousarray(img)
+            pitch = max(w, 1)
+        else:
+            src = synth.pad_pitch(img, pitch, fill)
+        lab = np.full((h, w), -7, np.int32)
+        st = np.zeros(1, np.int32)
+        k = self.lib.emu_label(src.ctypes.data, h, w, pitch, lab.ctypes.data, seed, shape, st.ctypes.data)
+        return lab, int(k), int(st[0])

@@ -1,0 +1,54 @@
+"""Stress run of the emulated GPU path against the oracle (run in a child process so that
+the sanitizer runtime can be preloaded).  Exit code 0 = every case matched."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.abspath(os.path.join(os.path.dirname(__file__), "..", ".."))
+sys.path[:0] = [ROOT, os.path.join(ROOT, "tests")]
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+from emu.emu import Emu  # noqa: E402
+
+
+def main(path, n_random):
+    emu = Emu(path)
+    bad = 0
+    imgs = []
+    for h, w in [(8, 64), (9, 65), (7, 63), (16, 128), (33, 97), (66, 300), (129, 257)]:
+        imgs += [synth.serpentine(h, w), synth.checkerboard(h, w), synth.dot_lattice(h, w),
+                 synth.striped_rows(h, w), synth.blobs(h, w, 2.0, h + w), np.ones((h, w), np.uint8),
+                 np.ascontiguousarray(synth.serpentine(w, h).T)]
+        for p in (0.2, 0.41, 0.6, 0.8):
+            imgs.append(synth.bernoulli(h, w, p, int(p * 1000) + h))
+    for i, img in enumerate(imgs):
+        ref, rk = oracle.cclremsp(img)
+        for shape in (0, 1, 2):
+            for seed in range(2):
+                pitch = None if seed == 0 else img.shape[1] + 3 + (i % 16)
+                lab, k, st = emu.label(img, seed=i * 7 + seed, shape=shape, pitch=pitch)
+                if not (k == rk and st == 0 and np.array_equal(lab, ref)):
+                    bad += 1
+                    print("mismatch", img.shape, shape, seed, k, rk, st)
+    rng = np.random.default_rng(5)
+    for i in range(n_random):
+        h = int(rng.integers(1, 20))
+        w = int(rng.integers(1, 140))
+        img = (rng.random((h, w)) < rng.uniform(0.15, 0.9)).astype(np.uint8)
+        ref, rk = oracle.cclremsp(img)
+        lab, k, st = emu.label(img, seed=i, shape=1 + (i % 2))
+        if not (k == rk and st == 0 and np.array_equal(lab, ref)):
+            bad += 1
+            print("random mismatch", h, w, k, rk, st)
+    for img in (np.zeros((0, 3), np.uint8), np.zeros((3, 0), np.uint8)):
+        lab, k, st = emu.label(img)
+        if k != 0:
+            bad += 1
+    print("bad", bad)
+    return bad
+
+
+if __name__ == "__main__":
+    sys.exit(1 if main(sys.argv[1], int(sys.argv[2])) else 0)

@@ -1,0 +1,88 @@
+"""GPU tests of the other entry points: batch, host buffers, asynchronous K, argument
+errors, kernel timing and launch counts."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu import stream_handle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ccl():
+    import paper_1606_05973_gb300 as m
+
+    return m
+
+
+def test_batch_equals_single(ccl):
+    import torch
+
+    specs = synth.batch_specs(n=40, seed=100, lo=16, hi=700)
+    imgs = [synth.make_batch_image(s) for s in specs]
+    imgs.append(np.zeros((0, 5), np.uint8))
+    dev = [torch.from_numpy(im).cuda() for im in imgs]
+    outs, ks = ccl.label_batch(dev)
+    ks = ks.cpu().numpy()
+    for im, o, k in zip(imgs, outs, ks):
+        ref, rk = oracle.cclremsp(im)
+        assert k == rk
+        assert np.array_equal(o.cpu().numpy(), ref)
+
+
+def test_host_buffers(ccl):
+    import torch
+
+    img = synth.bernoulli(1500, 2100, 0.55, 5)
+    pinned = torch.from_numpy(img).pin_memory()
+    out = torch.empty(img.shape, dtype=torch.int32).pin_memory()
+    lab, k = ccl.label_host(pinned, out=out)
+    ref, rk = oracle.cclremsp(img)
+    assert k == rk and np.array_equal(lab.numpy(), ref)
+    lab2, k2 = ccl.label_host(img)  # pageable numpy
+    assert k2 == rk and np.array_equal(lab2, ref)
+
+
+def test_async_count(ccl):
+    import torch
+
+    img = synth.bernoulli(999, 1234, 0.35, 6)
+    lab, kd = ccl.label(torch.from_numpy(img).cuda(), sync=False)
+    torch.cuda.synchronize()
+    ref, rk = oracle.cclremsp(img)
+    assert int(kd.item()) == rk and np.array_equal(lab.cpu().numpy(), ref)
+
+
+def test_argument_errors(ccl):
+    import torch
+
+    lib = ccl.lib()
+    s = stream_handle()
+    buf = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    lab = torch.zeros(64, dtype=torch.int32, device="cuda")
+    k = ctypes.c_int32(0)
+    assert lib.ccl_label(buf.data_ptr(), 4, 4, 4, 4, lab.data_ptr(), ctypes.byref(k), s) == 2
+    assert lib.ccl_label(buf.data_ptr(), 4, 4, 4, 6, lab.data_ptr(), ctypes.byref(k), s) == 1
+    assert lib.ccl_label(buf.data_ptr(), 4, 4, 3, 8, lab.data_ptr(), ctypes.byref(k), s) == 1
+    assert lib.ccl_label(None, 4, 4, 4, 8, lab.data_ptr(), ctypes.byref(k), s) == 1
+    assert lib.ccl_label(buf.data_ptr(), -1, 4, 4, 8, lab.data_ptr(), ctypes.byref(k), s) == 1
+    assert lib.ccl_label(buf.data_ptr(), 1 << 16, 1 << 15, 1 << 15, 8, lab.data_ptr(), ctypes.byref(k), s) == 1
+
+
+def test_profile_counts_launches(ccl):
+    import torch
+
+    img = torch.from_numpy(synth.bernoulli(512, 512, 0.5, 1)).cuda()
+    ccl.ccl_profile_reset()
+    ccl.ccl_profile_enable(1)
+    ccl.label(img)
+    ccl.label(img)
+    ccl.ccl_profile_enable(0)
+    kt = ccl.kernel_times()
+    assert kt["tile_local"][0] == 2 and kt["final_labels"][0] == 2
+    assert kt["final_labels"][1] > 0.0
+    ccl.ccl_profile_reset()
