@@ -41,7 +41,8 @@ typedef enum {
     CCL_ERR_CUDA = 4,             /* a CUDA runtime call failed */
     CCL_ERR_TIMEOUT = 5,          /* a device loop hit its iteration cap (see status bits) */
     CCL_ERR_BUSY = 6,             /* server: over its memory cap and told not to wait */
-    CCL_ERR_INTERNAL = 7          /* a device-side consistency check failed */
+    CCL_ERR_INTERNAL = 7,         /* a device-side consistency check failed */
+    CCL_ERR_TOO_LARGE = 8         /* ccl_label_static: image needs more than its fixed scratch */
 } ccl_status;
 
 /* Device status word bits (ccl_device_status). */
@@ -119,6 +120,31 @@ typedef struct {
  */
 int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity,
                         int32_t *num_components_dev, ccl_stream_t stream);
+
+/*
+ * ccl_label_static - as ccl_label_async, but it allocates nothing.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate device memory:
+ * a host framework that owns all device memory through its own pool and forbids
+ * plug-ins to call cudaMalloc, a real-time loop that must never stall in the allocator,
+ * or a process whose memory budget is fixed at start-up.
+ *
+ * Scratch: one fixed device array of 16 MiB inside the library (every GPU that loads the
+ * library holds it until the process exits).  An image fits when its workspace
+ * (ccl_workspace_bytes) is at most 16 MiB, e.g. 2048 x 2048; larger images return
+ * CCL_ERR_TOO_LARGE and nothing is launched.
+ *
+ * The first call on each device looks up the array's device address (with that device
+ * current) and caches it; make that first call before any stream capture.  The call
+ * clears the status word it uses, launches the same kernels as ccl_label, and writes K
+ * to the DEVICE int32 num_components_dev (may be NULL).  It does not synchronise.
+ *
+ * All calls in the process share the one array, which keeps the last call's contents:
+ * calls whose work may overlap on the GPU (different streams, or different host threads)
+ * race on it and give wrong labels.  Order them on one stream, or serialise them.
+ */
+int32_t ccl_label_static(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes,
+                         int32_t connectivity, int32_t *labels, int32_t *num_components_dev,
+                         ccl_stream_t stream);
 
 /* Bytes of workspace one image of H x W needs (for capacity planning). */
 int32_t ccl_workspace_bytes(int32_t H, int32_t W, int64_t *bytes);

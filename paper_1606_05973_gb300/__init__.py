@@ -17,8 +17,8 @@ import threading
 from .build import build, lib_path
 
 __all__ = [
-    "CCLError", "CCLUnavailable", "load", "lib", "ccl_label", "ccl_label_async", "ccl_label_host",
-    "ccl_label_batch", "ccl_workspace_bytes", "ccl_device_status", "ccl_release",
+    "CCLError", "CCLUnavailable", "load", "lib", "ccl_label", "ccl_label_async", "ccl_label_static",
+    "ccl_label_host", "ccl_label_batch", "ccl_workspace_bytes", "ccl_device_status", "ccl_release",
     "ccl_profile_enable", "ccl_profile_reset", "ccl_profile_read", "ccl_status_string",
     "ccl_version", "label", "label_batch", "label_host", "kernel_times", "CCL_OK",
 ]
@@ -26,7 +26,7 @@ __all__ = [
 CCL_OK = 0
 STATUS_NAMES = {0: "CCL_OK", 1: "CCL_ERR_INVALID_ARGUMENT", 2: "CCL_ERR_UNSUPPORTED",
                 3: "CCL_ERR_OUT_OF_MEMORY", 4: "CCL_ERR_CUDA", 5: "CCL_ERR_TIMEOUT",
-                6: "CCL_ERR_BUSY", 7: "CCL_ERR_INTERNAL"}
+                6: "CCL_ERR_BUSY", 7: "CCL_ERR_INTERNAL", 8: "CCL_ERR_TOO_LARGE"}
 
 
 class CCLError(RuntimeError):
@@ -57,6 +57,7 @@ _SIGS = {
     "ccl_version": ([], _I32),
     "ccl_label": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
     "ccl_label_async": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
+    "ccl_label_static": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
     "ccl_label_host": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
     "ccl_label_batch": ([_P, _I32, _I32, _P, _P], _I32),
     "ccl_workspace_bytes": ([_I32, _I32, _P], _I32),
@@ -111,6 +112,12 @@ def ccl_label(img, H, W, pitch_bytes, connectivity, labels, num_components, stre
 
 def ccl_label_async(img, H, W, pitch_bytes, connectivity, labels, num_components_dev, stream) -> int:
     return lib().ccl_label_async(img, H, W, pitch_bytes, connectivity, labels, num_components_dev, stream)
+
+
+def ccl_label_static(img, H, W, pitch_bytes, connectivity, labels, num_components_dev, stream) -> int:
+    """ccl_label_async without any device allocation (fixed 16 MiB scratch in the library);
+    for callers that may not allocate device memory."""
+    return lib().ccl_label_static(img, H, W, pitch_bytes, connectivity, labels, num_components_dev, stream)
 
 
 def ccl_label_host(img_host, H, W, pitch_bytes, connectivity, labels_host, num_components, stream) -> int:

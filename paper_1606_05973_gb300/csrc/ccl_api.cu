@@ -205,6 +205,7 @@ const char *ccl_status_string(int32_t status)
     case CCL_ERR_TIMEOUT: return "device loop exceeded its iteration cap";
     case CCL_ERR_BUSY: return "busy";
     case CCL_ERR_INTERNAL: return "device consistency check failed";
+    case CCL_ERR_TOO_LARGE: return "image needs more than the fixed 16 MiB scratch of ccl_label_static";
     default: return "unknown status";
     }
 }
