@@ -54,13 +54,15 @@ def env_int(name, default):
 
 # ---- workloads ---------------------------------------------------------------------------
 
-def make_workload(name, device):
+def make_workload(name, device, only=None):
     """Returns (list of (label, uint8 CUDA tensor), description dict)."""
     import torch
 
     imgs = []
     if name == "sweep8192":
         for kind, arg, seed in synth.SWEEP_8192:
+            if only and only != (f"bernoulli_p{arg}" if kind == "bernoulli" else f"blobs_sigma{arg:g}"):
+                continue
             if kind == "bernoulli":
                 t = torch.from_numpy(synth.bernoulli(8192, 8192, arg, seed)).to(device)
                 imgs.append((f"bernoulli_p{arg}", t))
@@ -197,7 +199,12 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     lib = ccl.lib()
-    imgs, desc = make_workload(args.workload, dev)
+    imgs, desc = make_workload(args.workload, dev, args.only)
+    if args.only:
+        imgs = [(n, t) for n, t in imgs if n == args.only]
+        if not imgs:
+            raise SystemExit(f"--only {args.only}: no such image in {args.workload}")
+        desc = {**desc, "images": 1, "only": args.only}
     labels = [torch.empty(tuple(t.shape), dtype=torch.int32, device=dev) for _, t in imgs]
     kdev = torch.zeros(len(imgs), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
@@ -290,8 +297,9 @@ def run_ours(args, rank, world, local_rank):
     step_ms = ms_max / args.steps
     value = world * px_per_step / (step_ms * 1e-3) / 1e9
     peak, peak_kind = hbm_peak()
-    # dominant kernel by summed device time
-    dom = max(kt.items(), key=lambda kv: kv[1][1])
+    # dominant kernel by summed device time (among those with an algorithmic byte model)
+    overall = max(kt.items(), key=lambda kv: kv[1][1])[0]
+    dom = max(((k, v) for k, v in kt.items() if k in KERNEL_BYTES_PER_PX), key=lambda kv: kv[1][1])
     dname, (dl, dms) = dom[0], dom[1]
     per_launch_px = px_per_step / len(imgs)  # each kernel launch covers one image
     roof = None
@@ -301,7 +309,7 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                 "traffic": tr, "algorithmic_bytes_per_launch": KERNEL_BYTES_PER_PX[dname] * per_launch_px,
-                "avg_launch_ms": round(dms / dl, 4)}
+                "avg_launch_ms": round(dms / dl, 4), "dominant_overall": overall}
     path_gbs = PATH_BYTES_PER_PX * px_per_step / (step_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -412,6 +420,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["sweep8192", "big21568", "small1024"], default="sweep8192")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default=None, help="keep one image of the workload (profiling)")
     ap.add_argument("--cpu-budget-s", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3:

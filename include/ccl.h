@@ -49,6 +49,7 @@ typedef enum {
 #define CCL_STATUS_LOOP_CAP 1  /* a union-find loop exceeded its iteration cap */
 #define CCL_STATUS_BOUNDS 2    /* checked builds: an index was out of range (access skipped) */
 #define CCL_STATUS_BAD_VALUE 4 /* checked builds: a value that cannot occur was read */
+#define CCL_STATUS_BARRIER 8   /* a grid barrier of the global kernel stopped waiting */
 
 /* Human-readable name of a status code (static string). */
 const char *ccl_status_string(int32_t status);

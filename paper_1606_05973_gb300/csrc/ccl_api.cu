@@ -16,7 +16,8 @@ namespace {
 using namespace ccl;
 
 // ---- workspace cache -----------------------------------------------------------------------
-// One workspace per (device, stream).  Layout: a 256-byte header {K, status, ...} followed
+// One workspace per (device, stream).  Layout: a 256-byte header {K, status, grid barrier
+// state of the global kernel at byte 16} followed
 // by the per-image arrays (and, for host-buffer calls, a device copy of the image and of
 // the labels).  Work on one stream is ordered, so reusing its workspace is safe.
 constexpr int64_t HDR = 256;
@@ -140,6 +141,7 @@ int32_t enqueue_one(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int
     a.vec_out = ((reinterpret_cast<uintptr_t>(labels) & 15) == 0) && (W % 4 == 0);
     a.K = k_dev;
     a.status = reinterpret_cast<int *>(static_cast<char *>(w->dev) + 4);
+    a.gsync = reinterpret_cast<GridSync *>(static_cast<char *>(w->dev) + 16);
     bind_workspace(a, L, layout_base);
     return map_cuda(launch_label(a, L, s));
 }
@@ -157,7 +159,7 @@ int32_t read_k_and_status(Workspace *w, const int32_t *k_dev, int32_t *num_compo
     if (st) {
         cudaMemsetAsync(static_cast<char *>(w->dev) + 4, 0, 4, s);
         cudaStreamSynchronize(s);
-        return (st & CCL_STATUS_LOOP_CAP) ? CCL_ERR_TIMEOUT : CCL_ERR_INTERNAL;
+        return (st & (CCL_STATUS_LOOP_CAP | CCL_STATUS_BARRIER)) ? CCL_ERR_TIMEOUT : CCL_ERR_INTERNAL;
     }
     if (num_components)
         *num_components = w->host_hdr[0];

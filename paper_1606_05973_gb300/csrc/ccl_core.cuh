@@ -16,12 +16,18 @@
 //    becomes a compare-and-swap on the root and splices become atomic minimums.  Links
 //    always go from the larger index to the smaller one, so the root of every set is its
 //    smallest index (the invariant p[x] <= x of Algorithm 2).
-//  * A node's index is the tile raster position of its first pixel; the smallest index of
-//    a component is then its raster-first pixel, which fixes the canonical numbering
-//    (background 0, components 1..K in raster order of first pixels).
+//  * Runs are numbered per strip in column order, so the run covering a pixel is found
+//    with one popcount.  Links go from the larger number to the smaller, so a local root
+//    is the top-left run of its component; the component's raster-first pixel lies in
+//    that run's strip and is found with an atomic minimum over the runs there.
+//  * Local roots get global ids whose order is raster order ((row, tile column) segment,
+//    then rank in the segment), so the global Rem union again makes every component's
+//    root its raster-first pixel, which fixes the canonical numbering (background 0,
+//    components 1..K in raster order of first pixels).
 //  * Algorithm 3 (flatten) and the labelling pass become: count global roots per
 //    (image row, tile column) segment, exclusive-scan the counts in raster order, give
-//    each root its rank + 1, and write every pixel's label.
+//    each root its rank + 1, and write every pixel's label.  The first kernel stores one
+//    16-bit root code per strip run, so the final kernel only maps runs to labels.
 #pragma once
 #include <stdint.h>
 #include <string.h>
@@ -35,15 +41,12 @@
 namespace ccl {
 
 // ---- flags and sentinels ---------------------------------------------------------------
-constexpr int REDIR = 0x40000000;      // shared-memory slot that points at its run's node
-constexpr int LABFLAG = (int)0x80000000u;  // shared-memory slot that holds a final label
-constexpr int NONE = -1;
-constexpr int CONT = -2;
 
 // device status word bits (ccl.h exposes them as CCL_STATUS_*)
 constexpr int ST_LOOP_CAP = 1;   // a union-find loop exceeded its iteration cap
 constexpr int ST_BOUNDS = 2;     // a checked index was out of range (debug builds)
 constexpr int ST_BAD_VALUE = 4;  // a value that cannot occur was read (debug builds)
+constexpr int ST_BARRIER = 8;    // a grid barrier gave up waiting (should never happen)
 
 constexpr int SMEM_LOOP_CAP = 1 << 20;
 constexpr int GLOBAL_LOOP_CAP = 1 << 24;
@@ -186,8 +189,10 @@ template <int TH_, int TW_, int NT_> struct Cfg {
     static constexpr int NS = TH / 2;     // two-row strips per tile
     static constexpr int CH = TW / 16;    // 16-byte chunks per tile row
     static constexpr int ROWCAP = TW / 2; // max components whose first pixel is in one tile row
+    static constexpr int RC = TW / 2;     // max strip runs in one strip
+    static constexpr int RMAX = NS * RC;  // max strip runs in one tile
     static_assert(TW % 32 == 0 && TH % 2 == 0, "tile shape");
-    static_assert(TH * TW < REDIR, "tile index range");
+    static_assert(TH * ROWCAP <= 65536, "root codes must fit 16 bits");
 };
 
 // Per-image device arguments.  All workspace arrays are owned by the caller of the kernels.
@@ -198,28 +203,28 @@ struct Img {
     int vec_in;          // img 16-byte aligned and pitch % 16 == 0
     int nTX, nTY;        // tiles across / down
     uint32_t *bitpack;   // [H][nTX*NW] object bits, bit b of word w = column 32w+b
+    uint16_t *runinfo;   // [tile][strip][RC] root code of each strip run (row*ROWCAP + j)
     int *P;              // global parents, index ((y*nTX + tx)*ROWCAP + j)
     int *nseg;           // [H*nTX] local components whose first pixel lies in (y, tx)
     int *cnt;            // [H*nTX] global roots per segment, then exclusive offsets
     int *edgeRow;        // [nTY][2][nTX*TW] node id of top (0) / bottom (1) tile rows, -1 = bg
     int *edgeCol;        // [nTX][2][nTY*TH] node id of left (0) / right (1) tile columns
-    int *bsum;           // scan block sums
+    int *bsum;           // per-CTA root counts of the global kernel, then their offsets
     int *K;              // number of components (device)
+    struct GridSync *gsync;  // grid barrier state of the global kernel (workspace header)
     int *labels;         // [H][W] int32 output
     int vec_out;         // labels 16-byte aligned and W % 4 == 0
     int *status;         // device status word (ST_* bits)
-    int64_t nP, nSeg;    // sizes of P and nseg/cnt (for checked builds)
+    int64_t nP, nSeg, nRunInfo;  // array sizes (for checked builds)
 };
 
 // Workspace layout for one image (byte offsets, each 256-byte aligned).
 struct Layout {
     int nTX, nTY;
-    int64_t nSeg, nP, nBitWords, nEdgeRow, nEdgeCol, nBsum;
-    int64_t off_bitpack, off_P, off_nseg, off_cnt, off_edgeRow, off_edgeCol, off_bsum, bytes;
+    int64_t nSeg, nP, nBitWords, nEdgeRow, nEdgeCol, nBsum, nRunInfo;
+    int64_t off_bitpack, off_runinfo, off_P, off_nseg, off_cnt, off_edgeRow, off_edgeCol, off_bsum, bytes;
 };
-constexpr int SCAN_ITEMS = 8;
-constexpr int SCAN_NT = 256;
-constexpr int SCAN_BLOCK = SCAN_ITEMS * SCAN_NT;
+constexpr int MAX_GLOBAL_CTAS = 4096;  // upper bound on the global kernel's grid
 
 CCL_HD int64_t align256(int64_t v) { return (v + 255) & ~(int64_t)255; }
 
@@ -231,11 +236,13 @@ template <class C> CCL_HD Layout plan_layout(int H, int W)
     L.nSeg = (int64_t)H * L.nTX;
     L.nP = L.nSeg * C::ROWCAP;
     L.nBitWords = (int64_t)H * L.nTX * C::NW;
+    L.nRunInfo = (int64_t)L.nTX * L.nTY * C::RMAX;
     L.nEdgeRow = (int64_t)L.nTY * 2 * L.nTX * C::TW;
     L.nEdgeCol = (int64_t)L.nTX * 2 * L.nTY * C::TH;
-    L.nBsum = (L.nSeg + SCAN_BLOCK - 1) / SCAN_BLOCK + 1;
+    L.nBsum = MAX_GLOBAL_CTAS;
     int64_t o = 0;
     L.off_bitpack = o; o = align256(o + L.nBitWords * 4);
+    L.off_runinfo = o; o = align256(o + L.nRunInfo * 2);
     L.off_P = o; o = align256(o + L.nP * 4);
     L.off_nseg = o; o = align256(o + L.nSeg * 4);
     L.off_cnt = o; o = align256(o + L.nSeg * 4);
@@ -247,15 +254,26 @@ template <class C> CCL_HD Layout plan_layout(int H, int W)
 }
 
 // ---- shared-memory tile state ------------------------------------------------------------
-template <class C> struct Smem {
-    uint32_t bits[C::TH][C::NW];      // object bits of the tile (rows beyond H are 0)
-    uint32_t rootbits[C::TH][C::NW];  // local roots (first pixels of local components)
-    uint32_t startsM[C::NS][C::NW];   // run starts of (row 2s | row 2s+1)
-    int rootpre[C::TH][C::NW];        // exclusive popcount prefix of rootbits along a row
-    int cout_[C::NS][C::NW];          // run start covering bit 31 (CONT: from the left, NONE)
-    int carry[C::NS][C::NW];          // start of the run entering word w from the left
-    int par[C::TH * C::TW];           // union-find parents at node positions + slots
+// Strip runs are numbered per strip in column order: run k of strip s is union-find node
+// u = s*RC + k.  The run covering object column x of strip s is therefore
+//   u = s*RC + (number of run starts of strip s at columns <= x) - 1,
+// which needs only a popcount and a per-word prefix of start counts.
+template <class C> struct SmemRuns {
+    uint32_t bits[C::TH][C::NW];     // object bits of the tile (rows beyond H are 0)
+    uint32_t starts[C::NS][C::NW];   // run starts of (row 2s | row 2s+1)
+    int rpre[C::NS][C::NW];          // run starts of strip s before word w
 };
+template <class C> struct SmemL : SmemRuns<C> {
+    int par[C::RMAX];                // union-find parents; a root holds ROOTFLAG | first pixel
+    uint32_t rootbits[C::TH][C::NW]; // first pixels of the local components
+    int rootpre[C::TH][C::NW];       // exclusive popcount prefix of rootbits along a row
+};
+template <class C> struct SmemF : SmemRuns<C> {
+    int lab[C::RMAX];                // final label of every strip run
+};
+
+constexpr int ROOTFLAG = (int)0x80000000u;
+constexpr int POSMASK = 0x7FFFFFFF;
 
 // Rem's union with splicing (Algorithm 2) made safe for concurrent threads (Algorithm 8):
 // the locked "still a root? then link" step is one compare-and-swap, and a splice
@@ -320,63 +338,86 @@ CCL_HD void rem_unite_g(int *P, int64_t n, int x, int y, int *st)
     flag_status(st, ST_LOOP_CAP);
 }
 
+// root of x; an entry holding ROOTFLAG (negative) or itself is a root
 CCL_HD int find_s(const int *par, int n, int x, int *st)
 {
     (void)n;
     x = CCL_CHK(x, n, st);
     for (int it = 0; it < SMEM_LOOP_CAP; it++) {
-        const int p = CCL_CHK(ld_s(&par[x]), n, st);
-        if (p == x)
+        const int p = ld_s(&par[x]);
+        if (p < 0 || p == x)
             return x;
-        x = p;
+        x = CCL_CHK(p, n, st);
     }
     flag_status(st, ST_LOOP_CAP);
     return x;
 }
 
-CCL_HD int find_g(const int *P, int64_t n, int x, int *st)
+// read-only global load (P after flatten, run codes): may use the non-coherent cache
+template <class T> CCL_HD T ld_ro(const T *a)
 {
-    (void)n;
-    x = (int)CCL_CHK((int64_t)x, n, st);
-    for (int it = 0; it < GLOBAL_LOOP_CAP; it++) {
-        const int p = (int)CCL_CHK((int64_t)ld_g(&P[x]), n, st);
-        if (p == x)
-            return x;
-        x = p;
-    }
-    flag_status(st, ST_LOOP_CAP);
-    return x;
+#if defined(__CUDA_ARCH__)
+    return __ldg(a);
+#else
+    return *a;
+#endif
 }
 
 template <class C> struct Tile {
-    using S = Smem<C>;
+    using SR = SmemRuns<C>;
+    using SL = SmemL<C>;
+    using SF = SmemF<C>;
 
-    // -- phase: image bytes -> object bits (and clear the root bits) ----------------------
-    CCL_HD static void load_image(const Img &a, S &s, int ty, int tx, int tid)
+    // -- phase: image bytes -> object bits; clear root bits; every parent starts as a root --
+    CCL_HD static void load_image(const Img &a, SL &s, int ty, int tx, int tid)
     {
         const int y0 = ty * C::TH, x0 = tx * C::TW;
         uint16_t *half = reinterpret_cast<uint16_t *>(&s.bits[0][0]);
-        for (int q = tid; q < C::TH * C::CH; q += C::NT) {
-            const int r = q / C::CH, c = q % C::CH;
-            const int y = y0 + r, x = x0 + 16 * c;
-            uint32_t m = 0;
-            if (y < a.H && x < a.W) {
-                const uint8_t *src = a.img + (int64_t)y * a.pitch + x;
-                if (a.vec_in && x + 16 <= a.W) {
-                    m = nz_mask16(src);
-                } else {
-                    const int n = imin(16, a.W - x);
-                    for (int i = 0; i < n; i++)
-                        m |= (src[i] != 0 ? 1u : 0u) << i;
+        constexpr int PER = (C::TH * C::CH + C::NT - 1) / C::NT;
+        const bool full = a.vec_in && (y0 + C::TH <= a.H) && (x0 + C::TW <= a.W);
+        if (full) {
+            // interior tile: issue every 16-byte load before using any of them
+            uint32_t m[PER];
+#pragma unroll
+            for (int i = 0; i < PER; i++) {
+                const int q = tid + i * C::NT;
+                m[i] = 0;
+                if (q < C::TH * C::CH) {
+                    const int r = q / C::CH, c = q % C::CH;
+                    m[i] = nz_mask16(a.img + (int64_t)(y0 + r) * a.pitch + x0 + 16 * c);
                 }
             }
-            half[r * C::CH + c] = (uint16_t)m;  // little-endian: half 2w is the low half of word w
+#pragma unroll
+            for (int i = 0; i < PER; i++) {
+                const int q = tid + i * C::NT;
+                if (q < C::TH * C::CH)
+                    half[q] = (uint16_t)m[i];
+            }
+        } else {
+            for (int q = tid; q < C::TH * C::CH; q += C::NT) {
+                const int r = q / C::CH, c = q % C::CH;
+                const int y = y0 + r, x = x0 + 16 * c;
+                uint32_t m = 0;
+                if (y < a.H && x < a.W) {
+                    const uint8_t *src = a.img + (int64_t)y * a.pitch + x;
+                    if (a.vec_in && x + 16 <= a.W) {
+                        m = nz_mask16(src);
+                    } else {
+                        const int n = imin(16, a.W - x);
+                        for (int i = 0; i < n; i++)
+                            m |= (src[i] != 0 ? 1u : 0u) << i;
+                    }
+                }
+                half[q] = (uint16_t)m;  // little-endian: half 2w is the low half of word w
+            }
         }
         for (int q = tid; q < C::TH * C::NW; q += C::NT)
             (&s.rootbits[0][0])[q] = 0u;
+        for (int q = tid; q < C::RMAX; q += C::NT)
+            s.par[q] = q;
     }
 
-    CCL_HD static void store_bitpack(const Img &a, const S &s, int ty, int tx, int tid)
+    CCL_HD static void store_bitpack(const Img &a, const SR &s, int ty, int tx, int tid)
     {
         const int y0 = ty * C::TH;
         const int64_t WW = (int64_t)a.nTX * C::NW;
@@ -388,20 +429,19 @@ template <class C> struct Tile {
         }
     }
 
-    CCL_HD static void load_bitpack(const Img &a, S &s, int ty, int tx, int tid)
+    CCL_HD static void load_bitpack(const Img &a, SR &s, int ty, int tx, int tid)
     {
         const int y0 = ty * C::TH;
         const int64_t WW = (int64_t)a.nTX * C::NW;
         for (int q = tid; q < C::TH * C::NW; q += C::NT) {
             const int r = q / C::NW, w = q % C::NW;
             s.bits[r][w] = (y0 + r < a.H)
-                ? a.bitpack[CCL_CHK((int64_t)(y0 + r) * WW + tx * C::NW + w, (int64_t)a.H * WW, a.status)]
+                ? ld_ro(&a.bitpack[CCL_CHK((int64_t)(y0 + r) * WW + tx * C::NW + w, (int64_t)a.H * WW, a.status)])
                 : 0u;
-            s.rootbits[r][w] = 0u;
         }
     }
 
-    CCL_HD static uint32_t strip_word(const S &s, int st, int w)
+    CCL_HD static uint32_t strip_word(const SR &s, int st, int w)
     {
         return s.bits[2 * st][w] | s.bits[2 * st + 1][w];
     }
@@ -409,8 +449,10 @@ template <class C> struct Tile {
     // Tile raster position of the first pixel (raster order) of the strip run that starts
     // at bit b of word w: the first object pixel of the upper row inside the run if any,
     // else the run's first column in the lower row.
-    CCL_HD static int first_pixel(const S &s, int st, int w, int b, uint32_t R0, uint32_t M)
+    CCL_HD static int first_pixel(const SR &s, int st, int w, int b)
     {
+        const uint32_t R0 = s.bits[2 * st][w];
+        const uint32_t M = R0 | s.bits[2 * st + 1][w];
         const int x0 = w * 32 + b;
         const int len = ctz32(~(M >> b));  // <= 32 - b
         const uint32_t rm = (len >= 32) ? 0xFFFFFFFFu : (((1u << len) - 1u) << b);
@@ -433,80 +475,37 @@ template <class C> struct Tile {
         return (2 * st + 1) * C::TW + x0;
     }
 
-    // -- phase: strip runs -> union-find nodes ----------------------------------------------
-    // Node of a run: par[id] = id at the run's first pixel.  The run-start slot (upper row,
-    // first column) is either that node or an unused position that then points at it.
-    CCL_HD static void runs(const Img &a, S &s, int tid)
+    // -- phase: strip run starts and their number per word ---------------------------------
+    CCL_HD static void strip_runs(SR &s, int tid)
     {
-        (void)a;
         for (int u = tid; u < C::NS * C::NW; u += C::NT) {
             const int st = u / C::NW, w = u % C::NW;
-            const uint32_t R0 = s.bits[2 * st][w];
-            const uint32_t M = R0 | s.bits[2 * st + 1][w];
+            const uint32_t M = strip_word(s, st, w);
             const uint32_t prev = (w > 0) ? (strip_word(s, st, w - 1) >> 31) : 0u;
             const uint32_t starts = M & ~((M << 1) | prev);
-            s.startsM[st][w] = starts;
-            s.cout_[st][w] = (M >> 31) ? (starts ? w * 32 + msb32(starts) : CONT) : NONE;
-            uint32_t todo = starts;
-            while (todo) {
-                const int b = ctz32(todo);
-                todo &= todo - 1u;
-                const int x0 = w * 32 + b;
-                const int id = first_pixel(s, st, w, b, R0, M);
-                const int slot = 2 * st * C::TW + x0;
-                s.par[CCL_CHK(id, C::TH * C::TW, a.status)] = id;
-                if (slot != id)
-                    s.par[slot] = REDIR | id;
-            }
+            s.starts[st][w] = starts;
+            s.rpre[st][w] = popc32(starts);
         }
     }
 
-    // -- phase: per strip, the start of the run that enters each word from the left --------
-    CCL_HD static void carry_scan(S &s, int tid)
+    // -- phase: exclusive prefix of the start counts along each strip ----------------------
+    CCL_HD static void strip_prefix(SR &s, int tid)
     {
         for (int st = tid; st < C::NS; st += C::NT) {
-            int c = NONE;
-            s.carry[st][0] = NONE;
-            for (int w = 1; w < C::NW; w++) {
-                const int o = s.cout_[st][w - 1];
-                c = (o == CONT) ? c : o;
-                s.carry[st][w] = c;
+            int acc = 0;
+            for (int w = 0; w < C::NW; w++) {
+                const int c = s.rpre[st][w];
+                s.rpre[st][w] = acc;
+                acc += c;
             }
         }
     }
 
-    // start column of the strip run covering object column x of strip st
-    CCL_HD static int run_start(const S &s, int st, int x, int *stw)
+    // union-find node of the strip run covering object column x of strip st
+    CCL_HD static int node(const SR &s, int st, int x)
     {
         const int w = x >> 5, b = x & 31;
-        const uint32_t le = s.startsM[st][w] & mask_le(b);
-        const int r = le ? (w * 32 + msb32(le)) : s.carry[st][w];
-#if defined(CCL_DEBUG)
-        if (r < 0 || r > x) {
-            flag_status(stw, ST_BAD_VALUE);
-            return x;
-        }
-#else
-        (void)stw;
-#endif
-        return r;
-    }
-
-    CCL_HD static int node_of_slot(const S &s, int st, int x0)
-    {
-        const int slot = 2 * st * C::TW + x0;
-        const int v = ld_s(&s.par[slot]);
-        const int node = (v & REDIR) ? (v & ~REDIR) : slot;
-#if defined(CCL_DEBUG)
-        if (node < 0 || node >= C::TH * C::TW)
-            return 0;
-#endif
-        return node;
-    }
-
-    CCL_HD static int node_of(const S &s, int st, int x, int *stw)
-    {
-        return node_of_slot(s, st, run_start(s, st, x, stw));
+        return st * C::RC + s.rpre[st][w] + popc32(s.starts[st][w] & mask_le(b)) - 1;
     }
 
     // -- phase: join strip runs that touch across strip boundaries ------------------------
@@ -514,7 +513,7 @@ template <class C> struct Tile {
     // of single-row runs (one in A, one in B) that are 8-adjacent is found exactly once:
     // either the B run starts where A has a pixel at that column or one to the left, or
     // the A run starts one column right of a B pixel.
-    CCL_HD static void unions(const Img &a, S &s, int tid)
+    CCL_HD static void unions(const Img &a, SL &s, int tid)
     {
         for (int u = tid; u < C::NS * C::NW; u += C::NT) {
             const int st = u / C::NW, w = u % C::NW;
@@ -531,37 +530,72 @@ template <class C> struct Tile {
                 ev1 &= ev1 - 1u;
                 const int xb = w * 32 + b;
                 const int xa = ((A >> b) & 1u) ? xb : xb - 1;
-                rem_unite_s(s.par, C::TH * C::TW, node_of(s, st, xb, a.status), node_of(s, st - 1, xa, a.status), a.status);
+                rem_unite_s(s.par, C::RMAX, node(s, st, xb), node(s, st - 1, xa), a.status);
             }
             while (ev2) {
                 const int b = ctz32(ev2);
                 ev2 &= ev2 - 1u;
                 const int xa = w * 32 + b;
-                rem_unite_s(s.par, C::TH * C::TW, node_of(s, st - 1, xa, a.status), node_of(s, st, xa - 1, a.status), a.status);
+                rem_unite_s(s.par, C::RMAX, node(s, st - 1, xa), node(s, st, xa - 1), a.status);
             }
         }
     }
 
-    // -- phase: resolve every node to its root; mark roots ---------------------------------
-    CCL_HD static void roots(const Img &a, S &s, int tid)
+    // -- phase: every run points at its root; a root records its own first pixel ---------
+    CCL_HD static void roots(const Img &a, SL &s, int tid)
     {
         for (int u = tid; u < C::NS * C::NW; u += C::NT) {
             const int st = u / C::NW, w = u % C::NW;
-            uint32_t todo = s.startsM[st][w];
+            uint32_t todo = s.starts[st][w];
+            int v = st * C::RC + s.rpre[st][w];
             while (todo) {
                 const int b = ctz32(todo);
                 todo &= todo - 1u;
-                const int node = node_of_slot(s, st, w * 32 + b);
-                const int r = find_s(s.par, C::TH * C::TW, node, a.status);
-                s.par[node] = r;
-                if (r == node)
-                    at_or(&s.rootbits[node / C::TW][(node % C::TW) >> 5], 1u << (node & 31));
+                const int r = find_s(s.par, C::RMAX, v, a.status);
+                s.par[v] = (r == v) ? (ROOTFLAG | first_pixel(s, st, w, b)) : r;
+                v++;
+            }
+        }
+    }
+
+    // -- phase: a component's first pixel lies in its root's strip (the root is its top-left
+    // run there); lower it to the smallest first pixel of the component's runs in that strip
+    CCL_HD static void first_pixels(const Img &a, SL &s, int tid)
+    {
+        for (int u = tid; u < C::NS * C::NW; u += C::NT) {
+            const int st = u / C::NW, w = u % C::NW;
+            uint32_t todo = s.starts[st][w];
+            int v = st * C::RC + s.rpre[st][w];
+            while (todo) {
+                const int b = ctz32(todo);
+                todo &= todo - 1u;
+                const int r = ld_s(&s.par[v]);
+                if (r >= 0 && r / C::RC == st)
+                    at_min(&s.par[CCL_CHK(r, C::RMAX, a.status)], ROOTFLAG | first_pixel(s, st, w, b));
+                v++;
+            }
+        }
+    }
+
+    // -- phase: mark each local component's first pixel ---------------------------------
+    CCL_HD static void mark_roots(const Img &a, SL &s, int tid)
+    {
+        for (int u = tid; u < C::NS * C::NW; u += C::NT) {
+            const int st = u / C::NW, w = u % C::NW;
+            const int n = popc32(s.starts[st][w]);
+            const int v0 = st * C::RC + s.rpre[st][w];
+            for (int k = 0; k < n; k++) {
+                const int p = s.par[v0 + k];
+                if (p < 0) {
+                    const int pos = CCL_CHK(p & POSMASK, C::TH * C::TW, a.status);
+                    at_or(&s.rootbits[pos / C::TW][(pos % C::TW) >> 5], 1u << (pos & 31));
+                }
             }
         }
     }
 
     // -- phase: rank of roots along each tile row; segment sizes --------------------------
-    CCL_HD static void root_prefix(const Img &a, S &s, int ty, int tx, int tid, bool write_nseg)
+    CCL_HD static void root_prefix(const Img &a, SL &s, int ty, int tx, int tid)
     {
         const int y0 = ty * C::TH;
         for (int r = tid; r < C::TH; r += C::NT) {
@@ -570,22 +604,44 @@ template <class C> struct Tile {
                 s.rootpre[r][w] = pre;
                 pre += popc32(s.rootbits[r][w]);
             }
-            if (write_nseg && y0 + r < a.H)
+            if (y0 + r < a.H)
                 a.nseg[CCL_CHK((int64_t)(y0 + r) * a.nTX + tx, a.nSeg, a.status)] = pre;
         }
     }
 
-    // global node id of a local root at tile raster position `root`
-    CCL_HD static int64_t gid_of(const Img &a, const S &s, int ty, int tx, int root)
+    // tile-local code (row * ROWCAP + j) of the component whose first pixel is `pos`
+    CCL_HD static int code_of(const SL &s, int pos)
     {
-        const int rr = root / C::TW, cc = root % C::TW;
+        const int rr = pos / C::TW, cc = pos % C::TW;
         const int j = s.rootpre[rr][cc >> 5] + popc32(s.rootbits[rr][cc >> 5] & mask_lt(cc & 31));
+        return rr * C::ROWCAP + j;
+    }
+
+    CCL_HD static int64_t gid_of_code(const Img &a, int ty, int tx, int code)
+    {
+        const int rr = code / C::ROWCAP, j = code % C::ROWCAP;
         return ((int64_t)(ty * C::TH + rr) * a.nTX + tx) * C::ROWCAP + j;
     }
 
-    // -- phase: one global union-find node per local root, P[id] = id ---------------------
-    CCL_HD static void init_nodes(const Img &a, const S &s, int ty, int tx, int tid)
+    // first pixel of the component of run v
+    CCL_HD static int comp_pos(const Img &a, const SL &s, int v)
     {
+        const int p = s.par[v];
+        const int r = (p < 0) ? v : CCL_CHK(p, C::RMAX, a.status);
+        return CCL_CHK(s.par[r] & POSMASK, C::TH * C::TW, a.status);
+    }
+
+    // -- phase: run codes for the final pass, one global node per local root, edge ids ------
+    CCL_HD static void outputs(const Img &a, const SL &s, int ty, int tx, int tid)
+    {
+        const int64_t tbase = ((int64_t)ty * a.nTX + tx) * C::RMAX;
+        for (int u = tid; u < C::NS * C::NW; u += C::NT) {
+            const int st = u / C::NW, w = u % C::NW;
+            const int n = popc32(s.starts[st][w]);
+            const int v0 = st * C::RC + s.rpre[st][w];
+            for (int k = 0; k < n; k++)
+                a.runinfo[CCL_CHK(tbase + v0 + k, a.nRunInfo, a.status)] = (uint16_t)code_of(s, comp_pos(a, s, v0 + k));
+        }
         for (int q = tid; q < C::TH * C::NW; q += C::NT) {
             const int r = q / C::NW, w = q % C::NW;
             uint32_t rb = s.rootbits[r][w];
@@ -596,20 +652,6 @@ template <class C> struct Tile {
                 gid++;
             }
         }
-    }
-
-    CCL_HD static int pixel_gid(const Img &a, const S &s, int ty, int tx, int r, int x)
-    {
-        if (!((s.bits[r][x >> 5] >> (x & 31)) & 1u))
-            return -1;
-        const int node = node_of(s, r >> 1, x, a.status);
-        const int root = CCL_CHK(ld_s(&s.par[node]), C::TH * C::TW, a.status);
-        return (int)gid_of(a, s, ty, tx, root);
-    }
-
-    // -- phase: node ids along the tile's four edges (for the boundary merge) -------------
-    CCL_HD static void edges(const Img &a, const S &s, int ty, int tx, int tid)
-    {
         const int64_t WP = (int64_t)a.nTX * C::TW, HP = (int64_t)a.nTY * C::TH;
         for (int x = tid; x < C::TW; x += C::NT) {
             a.edgeRow[CCL_CHK((int64_t)(2 * ty) * WP + tx * C::TW + x, (int64_t)a.nTY * 2 * WP, a.status)] =
@@ -625,61 +667,45 @@ template <class C> struct Tile {
         }
     }
 
-    // -- final pass: labels of this tile's local roots from the global table ---------------
+    CCL_HD static int pixel_gid(const Img &a, const SL &s, int ty, int tx, int r, int x)
+    {
+        if (!((s.bits[r][x >> 5] >> (x & 31)) & 1u))
+            return -1;
+        return (int)gid_of_code(a, ty, tx, code_of(s, comp_pos(a, s, node(s, r >> 1, x))));
+    }
+
+    // -- final pass: the label of every strip run, from its code and the global table ------
     // After flatten P[id] is either -(final label) (a global root) or the id of its global
     // root, whose entry holds -(final label).
-    CCL_HD static void root_labels_to_smem(const Img &a, S &s, int ty, int tx, int tid)
+    CCL_HD static void run_labels(const Img &a, SF &s, int ty, int tx, int tid)
     {
-        for (int q = tid; q < C::TH * C::NW; q += C::NT) {
-            const int r = q / C::NW, w = q % C::NW;
-            uint32_t rb = s.rootbits[r][w];
-            int64_t gid = ((int64_t)(ty * C::TH + r) * a.nTX + tx) * C::ROWCAP + s.rootpre[r][w];
-            while (rb) {
-                const int b = ctz32(rb);
-                rb &= rb - 1u;
-                const int v = a.P[CCL_CHK(gid, a.nP, a.status)];
-                int lab = (v < 0) ? -v : -a.P[CCL_CHK((int64_t)v, a.nP, a.status)];
-#if defined(CCL_DEBUG)
-                if (lab <= 0) {
-                    flag_status(a.status, ST_BAD_VALUE);
-                    lab = 0;
-                }
-#endif
-                s.par[r * C::TW + w * 32 + b] = lab | LABFLAG;
-                gid++;
-            }
-        }
-    }
-
-    // every run-start slot receives its run's final label (flagged)
-    CCL_HD static void run_labels(const Img &a, S &s, int tid)
-    {
+        const int64_t tbase = ((int64_t)ty * a.nTX + tx) * C::RMAX;
         for (int u = tid; u < C::NS * C::NW; u += C::NT) {
             const int st = u / C::NW, w = u % C::NW;
-            uint32_t todo = s.startsM[st][w];
-            while (todo) {
-                const int b = ctz32(todo);
-                todo &= todo - 1u;
-                const int slot = 2 * st * C::TW + w * 32 + b;
-                const int v = ld_s(&s.par[slot]);
-                int lab;
-                if (v < 0) {
-                    lab = v;  // the slot is a root: already a flagged label
-                } else {
-                    const int node = (v & REDIR) ? (v & ~REDIR) : slot;
-                    const int pv = (node == slot) ? v : ld_s(&s.par[node]);
-                    lab = (pv < 0) ? pv : ld_s(&s.par[CCL_CHK(pv, C::TH * C::TW, a.status)]);
-                }
+            const int n = popc32(s.starts[st][w]);
+            const int v0 = st * C::RC + s.rpre[st][w];
+            int prev_code = -1, prev_lab = 0;
+            for (int k = 0; k < n; k++) {
+                const int code = ld_ro(&a.runinfo[CCL_CHK(tbase + v0 + k, a.nRunInfo, a.status)]);
+                if (code != prev_code) {
+                    const int64_t gid = CCL_CHK(gid_of_code(a, ty, tx, code), a.nP, a.status);
+                    const int v = ld_ro(&a.P[gid]);
+                    int lab = (v < 0) ? -v : -ld_ro(&a.P[CCL_CHK((int64_t)v, a.nP, a.status)]);
 #if defined(CCL_DEBUG)
-                if (lab >= 0)
-                    flag_status(a.status, ST_BAD_VALUE);
+                    if (lab <= 0) {
+                        flag_status(a.status, ST_BAD_VALUE);
+                        lab = 0;
+                    }
 #endif
-                s.par[slot] = lab;
+                    prev_code = code;
+                    prev_lab = lab;
+                }
+                s.lab[v0 + k] = prev_lab;
             }
         }
     }
 
-    CCL_HD static void write_labels(const Img &a, const S &s, int ty, int tx, int tid)
+    CCL_HD static void write_labels(const Img &a, const SF &s, int ty, int tx, int tid)
     {
         const int y0 = ty * C::TH, x0 = tx * C::TW;
         constexpr int G = C::TW / 4;
@@ -688,17 +714,14 @@ template <class C> struct Tile {
             const int y = y0 + r, gx = x0 + x;
             if (y >= a.H || gx >= a.W)
                 continue;
-            const int st = r >> 1;
-            const uint32_t row = s.bits[r][x >> 5];
+            const int st = r >> 1, w = x >> 5;
+            const uint32_t row = s.bits[r][w];
+            const uint32_t starts = s.starts[st][w];
+            const int base = st * C::RC + s.rpre[st][w] - 1;
             int v[4];
             for (int k = 0; k < 4; k++) {
                 const int b = (x & 31) + k;
-                if ((row >> b) & 1u) {
-                    const int xs = run_start(s, st, x + k, a.status);
-                    v[k] = s.par[2 * st * C::TW + xs] & 0x7FFFFFFF;
-                } else {
-                    v[k] = 0;
-                }
+                v[k] = ((row >> b) & 1u) ? s.lab[CCL_CHK(base + popc32(starts & mask_le(b)), C::RMAX, a.status)] : 0;
             }
             int *dst = a.labels + (int64_t)y * a.W + gx;
             if (a.vec_out && gx + 4 <= a.W) {
@@ -764,117 +787,106 @@ template <class C> CCL_HD void merge_v(const Img &a, int tx, int y)
     }
 }
 
-// ---- flatten (Algorithm 3) over global nodes, per segment -------------------------------
-template <class C> CCL_HD void flatten_count(const Img &a, int64_t seg)
+// ---- global phase: flatten (Algorithm 3) and canonical numbering ------------------------
+// After the boundary merge every component is a tree over global node ids in which a
+// parent always has a smaller id (raster order), and the root is the component's
+// raster-first pixel.  Flatten is done by pointer jumping: in each round every node
+// follows up to JUMP_HOPS links and points at the farthest node reached, so the reach
+// grows geometrically and a path of n nodes needs about log(n)/log(JUMP_HOPS+1) rounds
+// (the paper's sequential flatten needs one pass because it visits labels in increasing
+// order; that order is not available to parallel threads).
+constexpr int JUMP_HOPS = 16;
+constexpr int MAX_ROUNDS = 40;
+
+// one round over the nodes of segment `seg`; true if some node has not reached its root
+template <class C> CCL_HD bool jump_segment(const Img &a, int64_t seg)
 {
     const int n = a.nseg[seg];
+    bool more = false;
+    for (int j = 0; j < n; j++) {
+        const int id = (int)CCL_CHK(seg * C::ROWCAP + j, a.nP, a.status);
+        const int p = ld_g(&a.P[id]);
+        if (p == id)
+            continue;
+        int r = (int)CCL_CHK((int64_t)p, a.nP, a.status);
+        bool root = false;
+        for (int h = 0; h < JUMP_HOPS; h++) {
+            const int q = (int)CCL_CHK((int64_t)ld_g(&a.P[r]), a.nP, a.status);
+            if (q == r) {
+                root = true;
+                break;
+            }
+            r = q;
+        }
+        if (r != p)
+            a.P[id] = r;  // only this thread writes P[id] in a round; r is an ancestor of id
+        more |= !root;
+    }
+    return more;
+}
+
+template <class C> CCL_HD int count_roots(const Img &a, int64_t s0, int64_t s1)
+{
     int c = 0;
-    for (int j = 0; j < n; j++) {
-        const int id = (int)CCL_CHK(seg * C::ROWCAP + j, a.nP, a.status);
-        const int r = find_g(a.P, a.nP, id, a.status);
-        if (r != id)
-            a.P[id] = r;
-        else
-            c++;
+    for (int64_t seg = s0; seg < s1; seg++) {
+        const int n = a.nseg[seg];
+        for (int j = 0; j < n; j++) {
+            const int id = (int)CCL_CHK(seg * C::ROWCAP + j, a.nP, a.status);
+            c += (ld_g(&a.P[id]) == id) ? 1 : 0;
+        }
     }
-    a.cnt[seg] = c;
+    return c;
 }
 
-// roots get -(offset + rank within segment + 1): their final label, negated
-template <class C> CCL_HD void label_roots(const Img &a, int64_t seg)
+// roots of segments [s0, s1) get -(label): labels continue from `off` in raster order
+template <class C> CCL_HD void label_roots(const Img &a, int64_t s0, int64_t s1, int off)
 {
-    const int n = a.nseg[seg];
-    int lab = a.cnt[seg];
-    for (int j = 0; j < n; j++) {
-        const int id = (int)CCL_CHK(seg * C::ROWCAP + j, a.nP, a.status);
-        if (a.P[id] == id) {
-            lab++;
-            a.P[id] = -lab;
+    for (int64_t seg = s0; seg < s1; seg++) {
+        const int n = a.nseg[seg];
+        for (int j = 0; j < n; j++) {
+            const int id = (int)CCL_CHK(seg * C::ROWCAP + j, a.nP, a.status);
+            if (ld_g(&a.P[id]) == id) {
+                off++;
+                a.P[id] = -off;
+            }
         }
     }
 }
 
-// ---- exclusive scan of the per-segment root counts (three phases) ----------------------
-struct ScanSmem {
-    int part[SCAN_NT];
+// contiguous range of segments owned by thread (block b, thread t) for counting/labelling
+CCL_HD void seg_range(int64_t nSeg, int nblocks, int nt, int b, int t, int64_t *s0, int64_t *s1)
+{
+    const int64_t nthreads = (int64_t)nblocks * nt;
+    const int64_t per = (nSeg + nthreads - 1) / nthreads;
+    const int64_t lo = ((int64_t)b * nt + t) * per;
+    *s0 = lo < nSeg ? lo : nSeg;
+    *s1 = (lo + per) < nSeg ? (lo + per) : nSeg;
+}
+
+// Exclusive scan of one value per thread across a CTA of GNT threads (Hillis-Steele in
+// shared memory, double-buffered so that each step reads only the previous step's
+// values).  Run as: scan_put; sync; for k < log2(GNT): scan_step(k); sync; then scan_get.
+constexpr int GNT = 256;
+constexpr int GNT_LOG = 8;
+struct ScanBuf {
+    int v[2][GNT];
 };
+CCL_HD void scan_put(ScanBuf &s, int tid, int x) { s.v[0][tid] = x; }
+CCL_HD void scan_step(ScanBuf &s, int tid, int k)
+{
+    const int d = 1 << k;
+    const int src = k & 1;
+    s.v[src ^ 1][tid] = s.v[src][tid] + (tid >= d ? s.v[src][tid - d] : 0);
+}
+// inclusive result after GNT_LOG steps lives in buffer GNT_LOG & 1
+CCL_HD int scan_incl(const ScanBuf &s, int tid) { return s.v[GNT_LOG & 1][tid]; }
 
-CCL_HD void scan_block_sum(const int *v, int64_t n, int *bsum, ScanSmem &s, int b, int tid)
-{
-    const int64_t base = (int64_t)b * SCAN_BLOCK + (int64_t)tid * SCAN_ITEMS;
-    int acc = 0;
-    for (int i = 0; i < SCAN_ITEMS; i++)
-        if (base + i < n)
-            acc += v[base + i];
-    s.part[tid] = acc;
-    (void)bsum;
-}
-CCL_HD void scan_block_sum_finish(int *bsum, ScanSmem &s, int b, int tid)
-{
-    if (tid == 0) {
-        int acc = 0;
-        for (int i = 0; i < SCAN_NT; i++)
-            acc += s.part[i];
-        bsum[b] = acc;
-    }
-}
-// one CTA: exclusive scan of the block sums (serial over CTA partials), total -> *K
-CCL_HD void scan_top(int *bsum, int64_t nb, int *K, ScanSmem &s, int tid, int phase)
-{
-    const int64_t per = (nb + SCAN_NT - 1) / SCAN_NT;
-    const int64_t lo = (int64_t)tid * per;
-    const int64_t hi = (lo + per < nb) ? lo + per : nb;
-    if (phase == 0) {
-        int acc = 0;
-        for (int64_t i = lo; i < hi; i++)
-            acc += bsum[i];
-        s.part[tid] = acc;
-    } else if (phase == 1) {
-        if (tid == 0) {
-            int acc = 0;
-            for (int i = 0; i < SCAN_NT; i++) {
-                const int t = s.part[i];
-                s.part[i] = acc;
-                acc += t;
-            }
-            *K = acc;
-        }
-    } else {
-        int acc = s.part[tid];
-        for (int64_t i = lo; i < hi; i++) {
-            const int t = bsum[i];
-            bsum[i] = acc;
-            acc += t;
-        }
-    }
-}
-CCL_HD void scan_apply(int *v, int64_t n, const int *bsum, ScanSmem &s, int b, int tid, int phase)
-{
-    const int64_t base = (int64_t)b * SCAN_BLOCK + (int64_t)tid * SCAN_ITEMS;
-    if (phase == 0) {
-        int acc = 0;
-        for (int i = 0; i < SCAN_ITEMS; i++)
-            if (base + i < n)
-                acc += v[base + i];
-        s.part[tid] = acc;
-    } else if (phase == 1) {
-        if (tid == 0) {
-            int acc = bsum[b];
-            for (int i = 0; i < SCAN_NT; i++) {
-                const int t = s.part[i];
-                s.part[i] = acc;
-                acc += t;
-            }
-        }
-    } else {
-        int acc = s.part[tid];
-        for (int i = 0; i < SCAN_ITEMS; i++)
-            if (base + i < n) {
-                const int t = v[base + i];
-                v[base + i] = acc;
-                acc += t;
-            }
-    }
-}
+// Grid-wide state of the global kernel, in the workspace header.  k_tile_local zeroes it
+// before every use (it runs first on the same stream).
+struct GridSync {
+    unsigned arrive;
+    int round_more[MAX_ROUNDS];
+};
+static_assert(16 + sizeof(GridSync) <= 256, "grid state must fit the 256-byte workspace header");
 
 }  // namespace ccl

@@ -10,14 +10,9 @@ namespace ccl {
 
 // Kernels of the single-image path, in launch order.
 enum KernelId {
-    KID_TILE_LOCAL = 0,  // image -> bit tiles, local union-find, local roots, edges
-    KID_MERGE,           // boundary merge across tile edges (global Rem union)
-    KID_FLATTEN,         // global roots: flatten + count per segment
-    KID_SCAN_SUM,        // exclusive scan of the per-segment root counts (3 launches)
-    KID_SCAN_TOP,
-    KID_SCAN_APPLY,
-    KID_LABEL_ROOTS,     // final label of each global root
-    KID_FINAL,           // recompute local structure, write int32 labels
+    KID_TILE_LOCAL = 0,  // image -> bit tiles, local union-find, local roots, run codes, edges
+    KID_GLOBAL,          // boundary merge, flatten, root scan and labels (cooperative grid)
+    KID_FINAL,           // label of every strip run, int32 labels
     KID_COUNT
 };
 const char *kernel_name(int kid);

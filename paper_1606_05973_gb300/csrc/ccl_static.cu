@@ -20,7 +20,8 @@
 
 #define CCL_STATIC_SCRATCH_BYTES (16ll << 20)
 
-// header (256 bytes: K at 0, status word at 4) + the per-image arrays of ccl::Layout
+// header (256 bytes: K at 0, status word at 4, grid barrier state at 16) + the per-image
+// arrays of ccl::Layout
 static __device__ __align__(256) unsigned char g_ccl_static_scratch[CCL_STATIC_SCRATCH_BYTES];
 
 namespace {
@@ -98,6 +99,7 @@ extern "C" int32_t ccl_label_static(const uint8_t *img, int32_t H, int32_t W, in
     a.vec_out = ((reinterpret_cast<uintptr_t>(labels) & 15) == 0) && (W % 4 == 0);
     a.K = num_components_dev ? num_components_dev : reinterpret_cast<int *>(b);
     a.status = reinterpret_cast<int *>(b + 4);
+    a.gsync = reinterpret_cast<GridSync *>(b + 16);
     bind_workspace(a, L, b + hdr);
     return launch_label(a, L, s) == cudaSuccess ? CCL_OK : CCL_ERR_CUDA;
 }

@@ -58,6 +58,8 @@ template <class C> struct Emu {
         a.nTX = L.nTX;
         a.nTY = L.nTY;
         a.bitpack = (uint32_t *)(b + L.off_bitpack);
+        a.runinfo = (uint16_t *)(b + L.off_runinfo);
+        a.nRunInfo = L.nRunInfo;
         a.P = (int *)(b + L.off_P);
         a.nseg = (int *)(b + L.off_nseg);
         a.cnt = (int *)(b + L.off_cnt);
@@ -70,7 +72,8 @@ template <class C> struct Emu {
         const int ntiles = L.nTX * L.nTY;
         std::vector<int> tiles(ntiles);
         std::iota(tiles.begin(), tiles.end(), 0);
-        auto *s = new Smem<C>;
+        auto *s = new SmemL<C>;
+        auto *f = new SmemF<C>;
         using T = Tile<C>;
 
         // tile_local
@@ -79,12 +82,14 @@ template <class C> struct Emu {
             const int ty = tile / a.nTX, tx = tile % a.nTX;
             memset(s, 0x7F, sizeof(*s));
             phase([&](int t) { T::load_image(a, *s, ty, tx, t); });
-            phase([&](int t) { T::store_bitpack(a, *s, ty, tx, t); T::runs(a, *s, t); });
-            phase([&](int t) { T::carry_scan(*s, t); });
+            phase([&](int t) { T::store_bitpack(a, *s, ty, tx, t); T::strip_runs(*s, t); });
+            phase([&](int t) { T::strip_prefix(*s, t); });
             phase([&](int t) { T::unions(a, *s, t); });
             phase([&](int t) { T::roots(a, *s, t); });
-            phase([&](int t) { T::root_prefix(a, *s, ty, tx, t, true); });
-            phase([&](int t) { T::init_nodes(a, *s, ty, tx, t); T::edges(a, *s, ty, tx, t); });
+            phase([&](int t) { T::first_pixels(a, *s, t); });
+            phase([&](int t) { T::mark_roots(a, *s, t); });
+            phase([&](int t) { T::root_prefix(a, *s, ty, tx, t); });
+            phase([&](int t) { T::outputs(a, *s, ty, tx, t); });
         }
         // boundary merge, items in random order
         {
@@ -99,58 +104,68 @@ template <class C> struct Emu {
                     merge_v<C>(a, 1 + (int)((i - nh) / a.H), (int)((i - nh) % a.H));
             }
         }
+        // flatten: rounds of pointer jumping over the segments (random order) until a
+        // round leaves every node at its root, as the cooperative kernel does
         {
             std::vector<int64_t> segs(L.nSeg);
             std::iota(segs.begin(), segs.end(), 0);
-            std::shuffle(segs.begin(), segs.end(), rng);
-            for (int64_t sg : segs)
-                flatten_count<C>(a, sg);
-        }
-        {
-            const int64_t nb = (L.nSeg + SCAN_BLOCK - 1) / SCAN_BLOCK;
-            ScanSmem ss;
-            for (int64_t bb = 0; bb < nb; bb++) {
-                phase256([&](int t) { scan_block_sum(a.cnt, L.nSeg, a.bsum, ss, (int)bb, t); });
-                phase256([&](int t) { scan_block_sum_finish(a.bsum, ss, (int)bb, t); });
+            for (int r = 0; r < MAX_ROUNDS; r++) {
+                std::shuffle(segs.begin(), segs.end(), rng);
+                bool more = false;
+                for (int64_t sg : segs)
+                    more |= jump_segment<C>(a, sg);
+                if (!more)
+                    break;
+                if (r == MAX_ROUNDS - 1)
+                    *a.status |= ST_LOOP_CAP;
             }
-            for (int ph = 0; ph < 3; ph++)
-                phase256([&](int t) { scan_top(a.bsum, nb, a.K, ss, t, ph); });
-            for (int64_t bb = 0; bb < nb; bb++)
-                for (int ph = 0; ph < 3; ph++)
-                    phase256([&](int t) { scan_apply(a.cnt, L.nSeg, a.bsum, ss, (int)bb, t, ph); });
         }
+        // root count, scan and labels with a pseudo-grid of G CTAs of GNT threads
         {
-            std::vector<int64_t> segs(L.nSeg);
-            std::iota(segs.begin(), segs.end(), 0);
-            std::shuffle(segs.begin(), segs.end(), rng);
-            for (int64_t sg : segs)
-                label_roots<C>(a, sg);
+            const int G = (int)std::min<int64_t>(3, (L.nSeg + GNT - 1) / GNT);
+            std::vector<int> tot(G), excl((size_t)G * GNT), cnt((size_t)G * GNT);
+            for (int bb = 0; bb < G; bb++) {
+                ScanBuf sb;
+                for (int t = 0; t < GNT; t++) {
+                    int64_t s0, s1;
+                    seg_range(L.nSeg, G, GNT, bb, t, &s0, &s1);
+                    cnt[(size_t)bb * GNT + t] = count_roots<C>(a, s0, s1);
+                    scan_put(sb, t, cnt[(size_t)bb * GNT + t]);
+                }
+                for (int k = 0; k < GNT_LOG; k++)
+                    for (int t = 0; t < GNT; t++)
+                        scan_step(sb, t, k);
+                for (int t = 0; t < GNT; t++)
+                    excl[(size_t)bb * GNT + t] = scan_incl(sb, t) - cnt[(size_t)bb * GNT + t];
+                tot[bb] = scan_incl(sb, GNT - 1);
+            }
+            int acc = 0;
+            for (int bb = 0; bb < G; bb++) {
+                const int t = tot[bb];
+                tot[bb] = acc;
+                acc += t;
+            }
+            *a.K = acc;
+            for (int bb = 0; bb < G; bb++)
+                for (int t = 0; t < GNT; t++) {
+                    int64_t s0, s1;
+                    seg_range(L.nSeg, G, GNT, bb, t, &s0, &s1);
+                    label_roots<C>(a, s0, s1, tot[bb] + excl[(size_t)bb * GNT + t]);
+                }
         }
         std::shuffle(tiles.begin(), tiles.end(), rng);
         for (int tile : tiles) {
             const int ty = tile / a.nTX, tx = tile % a.nTX;
-            memset(s, 0x7F, sizeof(*s));
-            phase([&](int t) { T::load_bitpack(a, *s, ty, tx, t); });
-            phase([&](int t) { T::runs(a, *s, t); });
-            phase([&](int t) { T::carry_scan(*s, t); });
-            phase([&](int t) { T::unions(a, *s, t); });
-            phase([&](int t) { T::roots(a, *s, t); });
-            phase([&](int t) { T::root_prefix(a, *s, ty, tx, t, false); });
-            phase([&](int t) { T::root_labels_to_smem(a, *s, ty, tx, t); });
-            phase([&](int t) { T::run_labels(a, *s, t); });
-            phase([&](int t) { T::write_labels(a, *s, ty, tx, t); });
+            memset(f, 0x7F, sizeof(*f));
+            phase([&](int t) { T::load_bitpack(a, *f, ty, tx, t); });
+            phase([&](int t) { T::strip_runs(*f, t); });
+            phase([&](int t) { T::strip_prefix(*f, t); });
+            phase([&](int t) { T::run_labels(a, *f, ty, tx, t); });
+            phase([&](int t) { T::write_labels(a, *f, ty, tx, t); });
         }
         delete s;
+        delete f;
         return K;
-    }
-
-    template <class F> void phase256(F f)
-    {
-        std::vector<int> o(SCAN_NT);
-        std::iota(o.begin(), o.end(), 0);
-        std::shuffle(o.begin(), o.end(), rng);
-        for (int t : o)
-            f(t);
     }
 };
 

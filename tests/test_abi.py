@@ -66,5 +66,6 @@ def test_argument_checks_need_no_gpu(lib):
     assert lib.ccl_label(p, 0, 9, 9, 8, p, ctypes.byref(k), None) == 0 and k.value == 0
     nb = ctypes.c_int64(0)
     assert lib.ccl_workspace_bytes(8192, 8192, ctypes.byref(nb)) == 0
-    # bit pack 1/8 B/px + parents (row segments) 2 B/px + edge ids + segment counts
-    assert 2.0 * 8192 * 8192 < nb.value < 2.5 * 8192 * 8192
+    # bit pack 1/8 B/px + run codes 1/2 B/px + parents (row segments) 2 B/px + edge ids
+    # + segment counts
+    assert 2.5 * 8192 * 8192 < nb.value < 3.0 * 8192 * 8192
