@@ -37,11 +37,27 @@
 #else
 #define CCL_HD inline
 #endif
+#if defined(__CUDA_ARCH__)
+#define CCL_UNROLL _Pragma("unroll")
+#else
+#define CCL_UNROLL
+#endif
+
+// Host builds of these functions exist only for the test emulator (tests/emu), which runs
+// every CTA with one OS thread per CUDA thread; it provides the emu_* hooks below.
+#if !defined(__CUDA_ARCH__)
+void emu_cta_sync();
+void emu_grid_sync();
+void emu_yield();
+uint32_t emu_ballot(bool p);
+int emu_shfl(int v, int src, int width);
+int emu_shfl_up(int v, int delta, int width);
+int emu_lane();
+#endif
 
 namespace ccl {
 
 // ---- flags and sentinels ---------------------------------------------------------------
-
 // device status word bits (ccl.h exposes them as CCL_STATUS_*)
 constexpr int ST_LOOP_CAP = 1;   // a union-find loop exceeded its iteration cap
 constexpr int ST_BOUNDS = 2;     // a checked index was out of range (debug builds)
@@ -50,6 +66,60 @@ constexpr int ST_BARRIER = 8;    // a grid barrier gave up waiting (should never
 
 constexpr int SMEM_LOOP_CAP = 1 << 20;
 constexpr int GLOBAL_LOOP_CAP = 1 << 24;
+
+// ---- CTA / warp primitives ------------------------------------------------------------------
+CCL_HD void cta_sync()
+{
+#if defined(__CUDA_ARCH__)
+    __syncthreads();
+#else
+    emu_cta_sync();
+#endif
+}
+CCL_HD int lane_id()
+{
+#if defined(__CUDA_ARCH__)
+    return (int)(threadIdx.x & 31);
+#else
+    return emu_lane();
+#endif
+}
+// all 32 lanes of the warp must call these together
+CCL_HD uint32_t warp_ballot(bool p)
+{
+#if defined(__CUDA_ARCH__)
+    return __ballot_sync(0xFFFFFFFFu, p);
+#else
+    return emu_ballot(p);
+#endif
+}
+CCL_HD int warp_shfl(int v, int src, int width = 32)
+{
+#if defined(__CUDA_ARCH__)
+    return __shfl_sync(0xFFFFFFFFu, v, src, width);
+#else
+    return emu_shfl(v, src, width);
+#endif
+}
+CCL_HD int warp_shfl_up(int v, int delta, int width = 32)
+{
+#if defined(__CUDA_ARCH__)
+    return __shfl_up_sync(0xFFFFFFFFu, v, delta, width);
+#else
+    return emu_shfl_up(v, delta, width);
+#endif
+}
+// inclusive sum over groups of `width` consecutive lanes (width a power of two <= 32)
+CCL_HD int warp_incl_sum(int v, int width)
+{
+    const int lw = lane_id() & (width - 1);
+    for (int d = 1; d < width; d <<= 1) {
+        const int t = warp_shfl_up(v, d, width);
+        if (lw >= d)
+            v += t;
+    }
+    return v;
+}
 
 // ---- portable bit and atomic helpers ---------------------------------------------------
 CCL_HD int popc32(uint32_t v)
@@ -77,6 +147,8 @@ CCL_HD int ctz32(uint32_t v)  // 32 for v == 0
 #endif
 }
 CCL_HD uint32_t mask_le(int b) { return b >= 31 ? 0xFFFFFFFFu : ((2u << b) - 1u); }
+// bits 0..b set; b = -1 gives 0
+CCL_HD uint32_t mask_upto(int b) { return b < 0 ? 0u : (b >= 31 ? 0xFFFFFFFFu : ((2u << b) - 1u)); }
 CCL_HD uint32_t mask_lt(int b) { return b <= 0 ? 0u : (b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u)); }
 CCL_HD int imin(int a, int b) { return a < b ? a : b; }
 
@@ -85,10 +157,9 @@ CCL_HD int at_cas(int *a, int cmp, int val)
 #if defined(__CUDA_ARCH__)
     return atomicCAS(a, cmp, val);
 #else
-    int old = *a;
-    if (old == cmp)
-        *a = val;
-    return old;
+    emu_yield();
+    __atomic_compare_exchange_n(a, &cmp, val, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST);
+    return cmp;
 #endif
 }
 CCL_HD void at_min(int *a, int v)
@@ -96,8 +167,10 @@ CCL_HD void at_min(int *a, int v)
 #if defined(__CUDA_ARCH__)
     atomicMin(a, v);
 #else
-    if (v < *a)
-        *a = v;
+    emu_yield();
+    int cur = __atomic_load_n(a, __ATOMIC_SEQ_CST);
+    while (v < cur && !__atomic_compare_exchange_n(a, &cur, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {
+    }
 #endif
 }
 CCL_HD void at_or(uint32_t *a, uint32_t v)
@@ -105,7 +178,7 @@ CCL_HD void at_or(uint32_t *a, uint32_t v)
 #if defined(__CUDA_ARCH__)
     atomicOr(a, v);
 #else
-    *a |= v;
+    __atomic_fetch_or(a, v, __ATOMIC_SEQ_CST);
 #endif
 }
 CCL_HD void flag_status(int *st, int f)
@@ -113,16 +186,54 @@ CCL_HD void flag_status(int *st, int f)
 #if defined(__CUDA_ARCH__)
     atomicOr(st, f);
 #else
-    *st |= f;
+    __atomic_fetch_or(st, f, __ATOMIC_SEQ_CST);
 #endif
 }
-// shared memory: a fresh read every time (no register caching across loop iterations)
+CCL_HD uint32_t at_cas_u(uint32_t *a, uint32_t cmp, uint32_t val)
+{
+#if defined(__CUDA_ARCH__)
+    return atomicCAS(a, cmp, val);
+#else
+    emu_yield();
+    __atomic_compare_exchange_n(a, &cmp, val, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST);
+    return cmp;
+#endif
+}
+CCL_HD void at_min_u(uint32_t *a, uint32_t v)
+{
+#if defined(__CUDA_ARCH__)
+    atomicMin(a, v);
+#else
+    emu_yield();
+    uint32_t cur = __atomic_load_n(a, __ATOMIC_SEQ_CST);
+    while (v < cur && !__atomic_compare_exchange_n(a, &cur, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {
+    }
+#endif
+}
+// shared memory written by other threads of the CTA in the same phase: a fresh read every
+// time (no register caching across loop iterations)
+CCL_HD uint32_t ld_su(const uint32_t *a)
+{
+#if defined(__CUDA_ARCH__)
+    return *(const volatile uint32_t *)a;
+#else
+    return __atomic_load_n(a, __ATOMIC_RELAXED);
+#endif
+}
+CCL_HD void st_su(uint32_t *a, uint32_t v)
+{
+#if defined(__CUDA_ARCH__)
+    *a = v;
+#else
+    __atomic_store_n(a, v, __ATOMIC_RELAXED);
+#endif
+}
 CCL_HD int ld_s(const int *a)
 {
 #if defined(__CUDA_ARCH__)
     return *(const volatile int *)a;
 #else
-    return *a;
+    return __atomic_load_n(a, __ATOMIC_RELAXED);
 #endif
 }
 // global memory written by other CTAs in the same launch: read through L2, not L1
@@ -131,7 +242,29 @@ CCL_HD int ld_g(const int *a)
 #if defined(__CUDA_ARCH__)
     return __ldcg(a);
 #else
-    return *a;
+    return __atomic_load_n(a, __ATOMIC_RELAXED);
+#endif
+}
+// four consecutive ints from a 16-byte aligned address, through L2
+CCL_HD void ld_g4(const int *a, int v[4])
+{
+#if defined(__CUDA_ARCH__)
+    const int4 q = __ldcg(reinterpret_cast<const int4 *>(a));
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+#else
+    for (int k = 0; k < 4; k++)
+        v[k] = __atomic_load_n(a + k, __ATOMIC_RELAXED);
+#endif
+}
+CCL_HD void st_g(int *a, int v)
+{
+#if defined(__CUDA_ARCH__)
+    *a = v;
+#else
+    __atomic_store_n(a, v, __ATOMIC_RELAXED);
 #endif
 }
 
@@ -193,6 +326,8 @@ template <int TH_, int TW_, int NT_> struct Cfg {
     static constexpr int RMAX = NS * RC;  // max strip runs in one tile
     static_assert(TW % 32 == 0 && TH % 2 == 0, "tile shape");
     static_assert(TH * ROWCAP <= 65536, "root codes must fit 16 bits");
+    static_assert(TH * TW < 65535 && RMAX <= 65536, "positions and run numbers must fit 16 bits");
+    static_assert(ROWCAP % 4 == 0, "segments are read four parents at a time");
 };
 
 // Per-image device arguments.  All workspace arrays are owned by the caller of the kernels.
@@ -263,8 +398,11 @@ template <class C> struct SmemRuns {
     uint32_t starts[C::NS][C::NW];   // run starts of (row 2s | row 2s+1)
     int rpre[C::NS][C::NW];          // run starts of strip s before word w
 };
+// A parent word holds the parent's run number in its low 16 bits.  The high 16 bits are
+// all ones while runs are joined (so every comparison of two words compares parents), and
+// a root's high half later receives its component's first pixel (tile raster position).
 template <class C> struct SmemL : SmemRuns<C> {
-    int par[C::RMAX];                // union-find parents; a root holds ROOTFLAG | first pixel
+    uint32_t par[C::RMAX];           // union-find parents (see above)
     uint32_t rootbits[C::TH][C::NW]; // first pixels of the local components
     int rootpre[C::TH][C::NW];       // exclusive popcount prefix of rootbits along a row
 };
@@ -272,37 +410,37 @@ template <class C> struct SmemF : SmemRuns<C> {
     int lab[C::RMAX];                // final label of every strip run
 };
 
-constexpr int ROOTFLAG = (int)0x80000000u;
-constexpr int POSMASK = 0x7FFFFFFF;
+constexpr uint32_t PAR_HI = 0xFFFF0000u;
+constexpr uint32_t PAR_LO = 0x0000FFFFu;
 
 // Rem's union with splicing (Algorithm 2) made safe for concurrent threads (Algorithm 8):
 // the locked "still a root? then link" step is one compare-and-swap, and a splice
 // p[r] <- p[other] is an atomic minimum so that parents never grow.
-CCL_HD void rem_unite_s(int *par, int n, int x, int y, int *st)
+CCL_HD void rem_unite_s(uint32_t *par, int n, int x, int y, int *st)
 {
     int rx = CCL_CHK(x, n, st), ry = CCL_CHK(y, n, st);
     (void)n;
     for (int it = 0; it < SMEM_LOOP_CAP; it++) {
-        const int px = CCL_CHK(ld_s(&par[rx]), n, st);
-        const int py = CCL_CHK(ld_s(&par[ry]), n, st);
+        const uint32_t px = ld_su(&par[rx]);
+        const uint32_t py = ld_su(&par[ry]);
         if (px == py)
             return;
         if (px > py) {
-            if (px == rx) {
-                if (at_cas(&par[rx], rx, py) == rx)
+            if ((int)(px & PAR_LO) == rx) {
+                if (at_cas_u(&par[rx], px, py) == px)
                     return;
                 continue;
             }
-            at_min(&par[rx], py);
-            rx = px;
+            at_min_u(&par[rx], py);
+            rx = CCL_CHK((int)(px & PAR_LO), n, st);
         } else {
-            if (py == ry) {
-                if (at_cas(&par[ry], ry, px) == ry)
+            if ((int)(py & PAR_LO) == ry) {
+                if (at_cas_u(&par[ry], py, px) == py)
                     return;
                 continue;
             }
-            at_min(&par[ry], px);
-            ry = py;
+            at_min_u(&par[ry], px);
+            ry = CCL_CHK((int)(py & PAR_LO), n, st);
         }
     }
     flag_status(st, ST_LOOP_CAP);
@@ -338,14 +476,14 @@ CCL_HD void rem_unite_g(int *P, int64_t n, int x, int y, int *st)
     flag_status(st, ST_LOOP_CAP);
 }
 
-// root of x; an entry holding ROOTFLAG (negative) or itself is a root
-CCL_HD int find_s(const int *par, int n, int x, int *st)
+// root of run x (a run whose parent is itself)
+CCL_HD int find_s(const uint32_t *par, int n, int x, int *st)
 {
     (void)n;
     x = CCL_CHK(x, n, st);
     for (int it = 0; it < SMEM_LOOP_CAP; it++) {
-        const int p = ld_s(&par[x]);
-        if (p < 0 || p == x)
+        const int p = (int)(ld_su(&par[x]) & PAR_LO);
+        if (p == x)
             return x;
         x = CCL_CHK(p, n, st);
     }
@@ -414,7 +552,7 @@ template <class C> struct Tile {
         for (int q = tid; q < C::TH * C::NW; q += C::NT)
             (&s.rootbits[0][0])[q] = 0u;
         for (int q = tid; q < C::RMAX; q += C::NT)
-            s.par[q] = q;
+            s.par[q] = PAR_HI | (uint32_t)q;
     }
 
     CCL_HD static void store_bitpack(const Img &a, const SR &s, int ty, int tx, int tid)
@@ -475,28 +613,28 @@ template <class C> struct Tile {
         return (2 * st + 1) * C::TW + x0;
     }
 
-    // -- phase: strip run starts and their number per word ---------------------------------
-    CCL_HD static void strip_runs(SR &s, int tid)
+    CCL_HD static uint32_t starts_of(const SR &s, int st, int w)
     {
-        for (int u = tid; u < C::NS * C::NW; u += C::NT) {
-            const int st = u / C::NW, w = u % C::NW;
-            const uint32_t M = strip_word(s, st, w);
-            const uint32_t prev = (w > 0) ? (strip_word(s, st, w - 1) >> 31) : 0u;
-            const uint32_t starts = M & ~((M << 1) | prev);
-            s.starts[st][w] = starts;
-            s.rpre[st][w] = popc32(starts);
-        }
+        const uint32_t M = strip_word(s, st, w);
+        const uint32_t prev = (w > 0) ? (strip_word(s, st, w - 1) >> 31) : 0u;
+        return M & ~((M << 1) | prev);
     }
 
-    // -- phase: exclusive prefix of the start counts along each strip ----------------------
-    CCL_HD static void strip_prefix(SR &s, int tid)
+    // -- phase: strip run starts, and how many runs of the strip start before each word.
+    // The NW words of a strip sit in NW consecutive lanes, so the prefix is a shuffle scan.
+    CCL_HD static void strip_runs(SR &s, int tid)
     {
-        for (int st = tid; st < C::NS; st += C::NT) {
-            int acc = 0;
-            for (int w = 0; w < C::NW; w++) {
-                const int c = s.rpre[st][w];
-                s.rpre[st][w] = acc;
-                acc += c;
+        static_assert(32 % C::NW == 0 && C::NT % 32 == 0, "a strip's words must share a warp");
+        for (int u0 = 0; u0 < C::NS * C::NW; u0 += C::NT) {
+            const int u = u0 + tid;
+            const bool ok = u < C::NS * C::NW;
+            const int st = ok ? u / C::NW : 0, w = u % C::NW;
+            const uint32_t st_bits = ok ? starts_of(s, st, w) : 0u;
+            const int c = popc32(st_bits);
+            const int incl = warp_incl_sum(c, C::NW);
+            if (ok) {
+                s.starts[st][w] = st_bits;
+                s.rpre[st][w] = incl - c;
             }
         }
     }
@@ -523,25 +661,44 @@ template <class C> struct Tile {
             const uint32_t Ap = (w > 0) ? (s.bits[2 * st - 1][w - 1] >> 31) : 0u;
             const uint32_t Bp = (w > 0) ? (s.bits[2 * st][w - 1] >> 31) : 0u;
             const uint32_t Ash = (A << 1) | Ap, Bsh = (B << 1) | Bp;
-            uint32_t ev1 = (B & ~Bsh) & (A | Ash);
-            uint32_t ev2 = (A & ~Ash) & Bsh;
-            while (ev1) {
-                const int b = ctz32(ev1);
-                ev1 &= ev1 - 1u;
-                const int xb = w * 32 + b;
-                const int xa = ((A >> b) & 1u) ? xb : xb - 1;
-                rem_unite_s(s.par, C::RMAX, node(s, st, xb), node(s, st - 1, xa), a.status);
-            }
-            while (ev2) {
-                const int b = ctz32(ev2);
-                ev2 &= ev2 - 1u;
-                const int xa = w * 32 + b;
-                rem_unite_s(s.par, C::RMAX, node(s, st - 1, xa), node(s, st, xa - 1), a.status);
+            const uint32_t ev1 = (B & ~Bsh) & (A | Ash);
+            const uint32_t ev2 = (A & ~Ash) & Bsh;
+            uint32_t evs = ev1 | ev2;
+            if (!evs)
+                continue;
+            // run of strip s covering bit b of this word (b = -1: the last bit of the word to
+            // the left) is base + popcount(starts & bits 0..b)
+            const uint32_t sA = s.starts[st - 1][w], sB = s.starts[st][w];
+            const int baseA = (st - 1) * C::RC + s.rpre[st - 1][w] - 1;
+            const int baseB = st * C::RC + s.rpre[st][w] - 1;
+            int last_a = -1, last_b = -1;
+            while (evs) {
+                const int b = ctz32(evs);
+                evs &= evs - 1u;
+                if ((ev1 >> b) & 1u) {
+                    const int ba = ((A >> b) & 1u) ? b : b - 1;
+                    const int na = baseA + popc32(sA & mask_upto(ba)), nb = baseB + popc32(sB & mask_upto(b));
+                    if (na != last_a || nb != last_b) {
+                        rem_unite_s(s.par, C::RMAX, nb, na, a.status);
+                        last_a = na;
+                        last_b = nb;
+                    }
+                }
+                if ((ev2 >> b) & 1u) {
+                    const int na = baseA + popc32(sA & mask_upto(b)), nb = baseB + popc32(sB & mask_upto(b - 1));
+                    if (na != last_a || nb != last_b) {
+                        rem_unite_s(s.par, C::RMAX, na, nb, a.status);
+                        last_a = na;
+                        last_b = nb;
+                    }
+                }
             }
         }
     }
 
-    // -- phase: every run points at its root; a root records its own first pixel ---------
+    // -- phase: every run points at its root.  A component's first pixel lies in its
+    // root's strip (the root is its top-left run), so the runs of that strip lower the
+    // root's key (high half of its word) to the smallest first pixel among them.
     CCL_HD static void roots(const Img &a, SL &s, int tid)
     {
         for (int u = tid; u < C::NS * C::NW; u += C::NT) {
@@ -552,26 +709,10 @@ template <class C> struct Tile {
                 const int b = ctz32(todo);
                 todo &= todo - 1u;
                 const int r = find_s(s.par, C::RMAX, v, a.status);
-                s.par[v] = (r == v) ? (ROOTFLAG | first_pixel(s, st, w, b)) : r;
-                v++;
-            }
-        }
-    }
-
-    // -- phase: a component's first pixel lies in its root's strip (the root is its top-left
-    // run there); lower it to the smallest first pixel of the component's runs in that strip
-    CCL_HD static void first_pixels(const Img &a, SL &s, int tid)
-    {
-        for (int u = tid; u < C::NS * C::NW; u += C::NT) {
-            const int st = u / C::NW, w = u % C::NW;
-            uint32_t todo = s.starts[st][w];
-            int v = st * C::RC + s.rpre[st][w];
-            while (todo) {
-                const int b = ctz32(todo);
-                todo &= todo - 1u;
-                const int r = ld_s(&s.par[v]);
-                if (r >= 0 && r / C::RC == st)
-                    at_min(&s.par[CCL_CHK(r, C::RMAX, a.status)], ROOTFLAG | first_pixel(s, st, w, b));
+                if (r != v)
+                    st_su(&s.par[v], PAR_HI | (uint32_t)r);
+                if (r / C::RC == st)
+                    at_min_u(&s.par[r], ((uint32_t)first_pixel(s, st, w, b) << 16) | (uint32_t)r);
                 v++;
             }
         }
@@ -585,9 +726,9 @@ template <class C> struct Tile {
             const int n = popc32(s.starts[st][w]);
             const int v0 = st * C::RC + s.rpre[st][w];
             for (int k = 0; k < n; k++) {
-                const int p = s.par[v0 + k];
-                if (p < 0) {
-                    const int pos = CCL_CHK(p & POSMASK, C::TH * C::TW, a.status);
+                const uint32_t p = s.par[v0 + k];
+                if ((int)(p & PAR_LO) == v0 + k) {
+                    const int pos = CCL_CHK((int)(p >> 16), C::TH * C::TW, a.status);
                     at_or(&s.rootbits[pos / C::TW][(pos % C::TW) >> 5], 1u << (pos & 31));
                 }
             }
@@ -598,14 +739,17 @@ template <class C> struct Tile {
     CCL_HD static void root_prefix(const Img &a, SL &s, int ty, int tx, int tid)
     {
         const int y0 = ty * C::TH;
-        for (int r = tid; r < C::TH; r += C::NT) {
-            int pre = 0;
-            for (int w = 0; w < C::NW; w++) {
-                s.rootpre[r][w] = pre;
-                pre += popc32(s.rootbits[r][w]);
+        for (int q0 = 0; q0 < C::TH * C::NW; q0 += C::NT) {
+            const int q = q0 + tid;
+            const bool ok = q < C::TH * C::NW;
+            const int r = ok ? q / C::NW : 0, w = q % C::NW;
+            const int c = ok ? popc32(s.rootbits[r][w]) : 0;
+            const int incl = warp_incl_sum(c, C::NW);
+            if (ok) {
+                s.rootpre[r][w] = incl - c;
+                if (w == C::NW - 1 && y0 + r < a.H)
+                    a.nseg[CCL_CHK((int64_t)(y0 + r) * a.nTX + tx, a.nSeg, a.status)] = incl;
             }
-            if (y0 + r < a.H)
-                a.nseg[CCL_CHK((int64_t)(y0 + r) * a.nTX + tx, a.nSeg, a.status)] = pre;
         }
     }
 
@@ -623,12 +767,12 @@ template <class C> struct Tile {
         return ((int64_t)(ty * C::TH + rr) * a.nTX + tx) * C::ROWCAP + j;
     }
 
-    // first pixel of the component of run v
+    // first pixel of the component of run v (after the roots phase a run's parent is
+    // its root, and a root's key is its component's first pixel)
     CCL_HD static int comp_pos(const Img &a, const SL &s, int v)
     {
-        const int p = s.par[v];
-        const int r = (p < 0) ? v : CCL_CHK(p, C::RMAX, a.status);
-        return CCL_CHK(s.par[r] & POSMASK, C::TH * C::TW, a.status);
+        const int r = CCL_CHK((int)(s.par[v] & PAR_LO), C::RMAX, a.status);
+        return CCL_CHK((int)(s.par[r] >> 16), C::TH * C::TW, a.status);
     }
 
     // -- phase: run codes for the final pass, one global node per local root, edge ids ------
@@ -685,22 +829,33 @@ template <class C> struct Tile {
             const int n = popc32(s.starts[st][w]);
             const int v0 = st * C::RC + s.rpre[st][w];
             int prev_code = -1, prev_lab = 0;
-            for (int k = 0; k < n; k++) {
-                const int code = ld_ro(&a.runinfo[CCL_CHK(tbase + v0 + k, a.nRunInfo, a.status)]);
-                if (code != prev_code) {
-                    const int64_t gid = CCL_CHK(gid_of_code(a, ty, tx, code), a.nP, a.status);
-                    const int v = ld_ro(&a.P[gid]);
-                    int lab = (v < 0) ? -v : -ld_ro(&a.P[CCL_CHK((int64_t)v, a.nP, a.status)]);
-#if defined(CCL_DEBUG)
-                    if (lab <= 0) {
-                        flag_status(a.status, ST_BAD_VALUE);
-                        lab = 0;
-                    }
-#endif
-                    prev_code = code;
-                    prev_lab = lab;
+            // four runs at a time: their codes, then their parents, then the roots' entries,
+            // so one batch waits for three loads instead of three per run
+            for (int k0 = 0; k0 < n; k0 += 4) {
+                int code[4], v[4];
+                bool fresh[4];
+                for (int k = 0; k < 4; k++)
+                    code[k] = (k0 + k < n) ? ld_ro(&a.runinfo[CCL_CHK(tbase + v0 + k0 + k, a.nRunInfo, a.status)]) : -1;
+                for (int k = 0; k < 4; k++) {
+                    fresh[k] = code[k] >= 0 && code[k] != ((k == 0) ? prev_code : code[k - 1]);
+                    v[k] = fresh[k] ? ld_ro(&a.P[CCL_CHK(gid_of_code(a, ty, tx, code[k]), a.nP, a.status)]) : -1;
                 }
-                s.lab[v0 + k] = prev_lab;
+                for (int k = 0; k < 4; k++)
+                    if (v[k] >= 0)  // not a global root: its entry names the root, which holds -label
+                        v[k] = ld_ro(&a.P[CCL_CHK((int64_t)v[k], a.nP, a.status)]);
+                for (int k = 0; k < 4 && k0 + k < n; k++) {
+                    if (fresh[k]) {
+                        prev_lab = -v[k];
+#if defined(CCL_DEBUG)
+                        if (prev_lab <= 0) {
+                            flag_status(a.status, ST_BAD_VALUE);
+                            prev_lab = 0;
+                        }
+#endif
+                    }
+                    s.lab[v0 + k0 + k] = prev_lab;
+                }
+                prev_code = code[3 < n - k0 - 1 ? 3 : n - k0 - 1];
             }
         }
     }
@@ -739,51 +894,55 @@ template <class C> struct Tile {
 // For an object pixel e on one side of a tile edge, with b the pixel facing it and a, c
 // the two diagonal ones: join e with b if b is an object pixel, else with a and c.  A pair
 // already joined through the previous pixel along the edge (same node id) is skipped.
-template <class C> CCL_HD void merge_h(const Img &a, int ty, int x)
+struct EdgeItem {
+    int e, b, aa, c;
+    bool same_prev;
+};
+
+// item i < nh: horizontal boundary above band 1 + i / W at column i % W; else vertical
+// boundary left of tile column 1 + k / H at row k % H (k = i - nh)
+template <class C> CCL_HD EdgeItem load_edge_item(const Img &a, int64_t i, int64_t nh)
 {
-    const int64_t WP = (int64_t)a.nTX * C::TW;
-    const int *top = a.edgeRow + (int64_t)(2 * ty) * WP;
-    const int *above = a.edgeRow + (int64_t)(2 * ty - 1) * WP;
-    const int e = top[x];
-    if (e < 0)
-        return;
-    const int b = above[x];
-    const int aa = (x > 0) ? above[x - 1] : -1;
-    const int c = (x + 1 < a.W) ? above[x + 1] : -1;
-    const bool same_prev = (x > 0) && top[x - 1] == e;
-    if (b >= 0) {
-        if (!same_prev)
-            rem_unite_g(a.P, a.nP, e, b, a.status);
+    EdgeItem it;
+    if (i < nh) {
+        const int ty = 1 + (int)(i / a.W), x = (int)(i % a.W);
+        const int64_t WP = (int64_t)a.nTX * C::TW;
+        const int *top = a.edgeRow + (int64_t)(2 * ty) * WP;
+        const int *above = a.edgeRow + (int64_t)(2 * ty - 1) * WP;
+        it.e = top[x];
+        it.b = above[x];
+        it.aa = (x > 0) ? above[x - 1] : -1;
+        it.c = (x + 1 < a.W) ? above[x + 1] : -1;
+        it.same_prev = (x > 0) && top[x - 1] == it.e;
     } else {
-        if (aa >= 0 && !same_prev)
-            rem_unite_g(a.P, a.nP, e, aa, a.status);
-        if (c >= 0)
-            rem_unite_g(a.P, a.nP, e, c, a.status);
+        const int64_t k = i - nh;
+        const int tx = 1 + (int)(k / a.H), y = (int)(k % a.H);
+        const int64_t HP = (int64_t)a.nTY * C::TH;
+        const int *left = a.edgeCol + (int64_t)(2 * tx - 1) * HP;
+        const int *me = a.edgeCol + (int64_t)(2 * tx) * HP;
+        const int yb0 = (y / C::TH) * C::TH;
+        const int yb1 = imin(yb0 + C::TH, a.H);
+        it.e = me[y];
+        it.b = left[y];
+        it.aa = (y - 1 >= yb0) ? left[y - 1] : -1;
+        it.c = (y + 1 < yb1) ? left[y + 1] : -1;
+        it.same_prev = (y - 1 >= yb0) && me[y - 1] == it.e;
     }
+    return it;
 }
 
-template <class C> CCL_HD void merge_v(const Img &a, int tx, int y)
+CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it)
 {
-    const int64_t HP = (int64_t)a.nTY * C::TH;
-    const int *left = a.edgeCol + (int64_t)(2 * tx - 1) * HP;
-    const int *me = a.edgeCol + (int64_t)(2 * tx) * HP;
-    const int e = me[y];
-    if (e < 0)
+    if (it.e < 0)
         return;
-    const int yb0 = (y / C::TH) * C::TH;
-    const int yb1 = imin(yb0 + C::TH, a.H);
-    const int b = left[y];
-    const int aa = (y - 1 >= yb0) ? left[y - 1] : -1;
-    const int c = (y + 1 < yb1) ? left[y + 1] : -1;
-    const bool same_prev = (y - 1 >= yb0) && me[y - 1] == e;
-    if (b >= 0) {
-        if (!same_prev)
-            rem_unite_g(a.P, a.nP, e, b, a.status);
+    if (it.b >= 0) {
+        if (!it.same_prev)
+            rem_unite_g(a.P, a.nP, it.e, it.b, a.status);
     } else {
-        if (aa >= 0 && !same_prev)
-            rem_unite_g(a.P, a.nP, e, aa, a.status);
-        if (c >= 0)
-            rem_unite_g(a.P, a.nP, e, c, a.status);
+        if (it.aa >= 0 && !it.same_prev)
+            rem_unite_g(a.P, a.nP, it.e, it.aa, a.status);
+        if (it.c >= 0)
+            rem_unite_g(a.P, a.nP, it.e, it.c, a.status);
     }
 }
 
@@ -796,46 +955,50 @@ template <class C> CCL_HD void merge_v(const Img &a, int tx, int y)
 // (the paper's sequential flatten needs one pass because it visits labels in increasing
 // order; that order is not available to parallel threads).
 constexpr int JUMP_HOPS = 16;
+#ifndef CCL_MERGE_BATCH
+#define CCL_MERGE_BATCH 1
+#endif
+constexpr int MERGE_BATCH = CCL_MERGE_BATCH;
 constexpr int MAX_ROUNDS = 40;
 
-// one round over the nodes of segment `seg`; true if some node has not reached its root
-template <class C> CCL_HD bool jump_segment(const Img &a, int64_t seg)
+// One round over the nodes of segment `seg`: every node that is not a root moves its
+// parent up to JUMP_HOPS ancestors.  A root is an entry equal to its own id or, once the
+// roots are labelled, a negative entry.  Returns true if some node has not reached its
+// root; adds the number of roots to *roots.  The parent words of four nodes are loaded
+// before any is used (one 16-byte load).
+template <class C> CCL_HD bool jump_segment(const Img &a, int64_t seg, int *roots)
 {
     const int n = a.nseg[seg];
+    const int64_t base = seg * C::ROWCAP;
     bool more = false;
-    for (int j = 0; j < n; j++) {
-        const int id = (int)CCL_CHK(seg * C::ROWCAP + j, a.nP, a.status);
-        const int p = ld_g(&a.P[id]);
-        if (p == id)
-            continue;
-        int r = (int)CCL_CHK((int64_t)p, a.nP, a.status);
-        bool root = false;
-        for (int h = 0; h < JUMP_HOPS; h++) {
-            const int q = (int)CCL_CHK((int64_t)ld_g(&a.P[r]), a.nP, a.status);
-            if (q == r) {
-                root = true;
-                break;
+    for (int j0 = 0; j0 < n; j0 += 4) {
+        int p4[4];
+        ld_g4(&a.P[CCL_CHK(base + j0, a.nP, a.status)], p4);  // a segment's slots are 16-byte aligned
+        for (int k = 0; k < 4; k++) {
+            const int id = (int)(base + j0 + k);
+            const int p = p4[k];
+            if (j0 + k >= n)
+                continue;
+            if (p == id || p < 0) {
+                (*roots)++;
+                continue;
             }
-            r = q;
+            int r = (int)CCL_CHK((int64_t)p, a.nP, a.status);
+            bool root = false;
+            for (int h = 0; h < JUMP_HOPS; h++) {
+                const int q = ld_g(&a.P[r]);
+                if (q == r || q < 0) {
+                    root = true;
+                    break;
+                }
+                r = (int)CCL_CHK((int64_t)q, a.nP, a.status);
+            }
+            if (r != p)
+                st_g(&a.P[id], r);  // only this thread writes P[id] in a round; r is an ancestor
+            more |= !root;
         }
-        if (r != p)
-            a.P[id] = r;  // only this thread writes P[id] in a round; r is an ancestor of id
-        more |= !root;
     }
     return more;
-}
-
-template <class C> CCL_HD int count_roots(const Img &a, int64_t s0, int64_t s1)
-{
-    int c = 0;
-    for (int64_t seg = s0; seg < s1; seg++) {
-        const int n = a.nseg[seg];
-        for (int j = 0; j < n; j++) {
-            const int id = (int)CCL_CHK(seg * C::ROWCAP + j, a.nP, a.status);
-            c += (ld_g(&a.P[id]) == id) ? 1 : 0;
-        }
-    }
-    return c;
 }
 
 // roots of segments [s0, s1) get -(label): labels continue from `off` in raster order
@@ -843,11 +1006,16 @@ template <class C> CCL_HD void label_roots(const Img &a, int64_t s0, int64_t s1,
 {
     for (int64_t seg = s0; seg < s1; seg++) {
         const int n = a.nseg[seg];
-        for (int j = 0; j < n; j++) {
-            const int id = (int)CCL_CHK(seg * C::ROWCAP + j, a.nP, a.status);
-            if (ld_g(&a.P[id]) == id) {
-                off++;
-                a.P[id] = -off;
+        const int64_t base = seg * C::ROWCAP;
+        for (int j0 = 0; j0 < n; j0 += 4) {
+            int p4[4];
+            ld_g4(&a.P[CCL_CHK(base + j0, a.nP, a.status)], p4);
+            for (int k = 0; k < 4; k++) {
+                const int id = (int)(base + j0 + k);
+                if (j0 + k < n && p4[k] == id) {
+                    off++;
+                    st_g(&a.P[id], -off);
+                }
             }
         }
     }
@@ -866,8 +1034,13 @@ CCL_HD void seg_range(int64_t nSeg, int nblocks, int nt, int b, int t, int64_t *
 // Exclusive scan of one value per thread across a CTA of GNT threads (Hillis-Steele in
 // shared memory, double-buffered so that each step reads only the previous step's
 // values).  Run as: scan_put; sync; for k < log2(GNT): scan_step(k); sync; then scan_get.
-constexpr int GNT = 256;
-constexpr int GNT_LOG = 8;
+#ifndef CCL_GLOBAL_NT
+#define CCL_GLOBAL_NT 1024
+#endif
+constexpr int GNT = CCL_GLOBAL_NT;
+constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+constexpr int GNT_LOG = ilog2(GNT);
+static_assert((1 << GNT_LOG) == GNT, "global CTA size must be a power of two");
 struct ScanBuf {
     int v[2][GNT];
 };
@@ -888,5 +1061,219 @@ struct GridSync {
     int round_more[MAX_ROUNDS];
 };
 static_assert(16 + sizeof(GridSync) <= 256, "grid state must fit the 256-byte workspace header");
+
+// ---- kernel bodies (shared by the CUDA kernels and the test emulator) ------------------
+// CCL_TICK(k) marks the end of phase k-1 for a phase-timing build (a harness that defines
+// CCL_PHASE_TIMING and supplies ccl_phase_tick); it is empty in the library.
+#if defined(CCL_PHASE_TIMING) && defined(__CUDACC__)
+__device__ void ccl_phase_tick(int kernel, int phase, int tid);
+#endif
+#if defined(CCL_PHASE_TIMING) && defined(__CUDA_ARCH__)
+#define CCL_TICK(kern, k) ccl_phase_tick((kern), (k), tid)
+#else
+#define CCL_TICK(kern, k) ((void)0)
+#endif
+
+// Grid barrier of the cooperative global kernel (all CTAs co-resident).  Each wait is
+// capped: after BARRIER_SPIN_CAP polls a CTA records ST_BARRIER and goes on, so a broken
+// launch ends with an error status instead of hanging the GPU.
+constexpr int BARRIER_SPIN_CAP = 1 << 21;
+
+CCL_HD void grid_sync(GridSync *g, unsigned nblocks, unsigned &epoch, int *status, int tid)
+{
+#if defined(__CUDA_ARCH__)
+    __syncthreads();
+    epoch += 1;
+    if (tid == 0) {
+        __threadfence();
+        atomicAdd(&g->arrive, 1u);
+        const unsigned target = epoch * nblocks;
+        int it = 0;
+        while (*reinterpret_cast<volatile unsigned *>(&g->arrive) < target) {
+            if (++it > BARRIER_SPIN_CAP) {
+                atomicOr(status, ST_BARRIER);
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+#else
+    (void)g;
+    (void)nblocks;
+    (void)status;
+    (void)tid;
+    epoch += 1;
+    emu_grid_sync();
+#endif
+}
+
+// rows a1 + a2 for one tile: bits, strip runs, local Rem union, local roots, run codes,
+// global nodes, tile-edge ids
+template <class C> CCL_HD void tile_local_body(const Img &a, SmemL<C> &s, int tile, int tid)
+{
+    using T = Tile<C>;
+    const int ty = tile / a.nTX, tx = tile % a.nTX;
+    if (tile == 0) {
+        // reset the grid barrier of the global kernel that follows on this stream
+        unsigned *g = reinterpret_cast<unsigned *>(a.gsync);
+        for (int i = tid; i < (int)(sizeof(GridSync) / 4); i += C::NT)
+            g[i] = 0u;
+    }
+    CCL_TICK(0, 0);
+    T::load_image(a, s, ty, tx, tid);
+    cta_sync();
+    CCL_TICK(0, 1);
+    T::store_bitpack(a, s, ty, tx, tid);
+    T::strip_runs(s, tid);
+    cta_sync();
+    CCL_TICK(0, 2);
+    T::unions(a, s, tid);
+    cta_sync();
+    CCL_TICK(0, 3);
+    T::roots(a, s, tid);
+    cta_sync();
+    CCL_TICK(0, 4);
+    T::mark_roots(a, s, tid);
+    cta_sync();
+    CCL_TICK(0, 5);
+    T::root_prefix(a, s, ty, tx, tid);
+    cta_sync();
+    CCL_TICK(0, 6);
+    T::outputs(a, s, ty, tx, tid);
+#if defined(CCL_PHASE_TIMING)
+    cta_sync();
+    CCL_TICK(0, 7);
+#endif
+}
+
+// rows a3, a4, a5 (global part) for CTA b of G: boundary merge, pointer-jumping flatten,
+// root count, scan and labels.  Roots are final once the merge is done, so they are
+// counted during the first jump round and labelled while later rounds (deep trees only)
+// keep shortening the other nodes' paths.
+template <class C> CCL_HD void global_body(const Img &a, ScanBuf &sb, int &s_flag, int b, int G, int tid)
+{
+    unsigned epoch = 0;
+    GridSync *g = a.gsync;
+    const int64_t stride = (int64_t)G * GNT;
+    CCL_TICK(1, 0);
+
+    // a3: boundary merge (Algorithm 7's boundary loop with Algorithm 8's union), the edge
+    // ids of MERGE_BATCH items loaded before any union
+    constexpr int MB = MERGE_BATCH;
+    const int64_t nh = (int64_t)(a.nTY - 1) * a.W;
+    const int64_t nv = (int64_t)(a.nTX - 1) * a.H;
+    for (int64_t i0 = (int64_t)b * GNT + tid; i0 < nh + nv; i0 += MB * stride) {
+        EdgeItem it[MB];
+        CCL_UNROLL
+        for (int k = 0; k < MB; k++) {
+            const int64_t i = i0 + k * stride;
+            if (i < nh + nv)
+                it[k] = load_edge_item<C>(a, i, nh);
+            else
+                it[k].e = -1;
+        }
+        CCL_UNROLL
+        for (int k = 0; k < MB; k++)
+            apply_edge_item(a, it[k]);
+    }
+    grid_sync(g, (unsigned)G, epoch, a.status, tid);
+    CCL_TICK(1, 1);
+
+    // a4 + a5: first jump round over this thread's contiguous raster range of segments,
+    // counting roots; scan of the counts across the CTA, then across CTAs
+    int64_t s0, s1;
+    seg_range(a.nSeg, G, GNT, b, tid, &s0, &s1);
+    int c = 0;
+    bool more = false;
+    for (int64_t seg = s0; seg < s1; seg++)
+        more |= jump_segment<C>(a, seg, &c);
+    if (more)
+        flag_status(&g->round_more[0], 1);
+    scan_put(sb, tid, c);
+    cta_sync();
+    for (int k = 0; k < GNT_LOG; k++) {
+        scan_step(sb, tid, k);
+        cta_sync();
+    }
+    const int incl = scan_incl(sb, tid);
+    if (tid == GNT - 1)
+        st_g(&a.bsum[b], incl);
+    grid_sync(g, (unsigned)G, epoch, a.status, tid);
+    CCL_TICK(1, 2);
+    if (b == 0) {
+        const int per = (G + GNT - 1) / GNT;
+        const int lo = tid * per < G ? tid * per : G;
+        const int hi = lo + per < G ? lo + per : G;
+        int acc = 0;
+        for (int i = lo; i < hi; i++)
+            acc += ld_g(&a.bsum[i]);
+        scan_put(sb, tid, acc);
+        cta_sync();
+        for (int k = 0; k < GNT_LOG; k++) {
+            scan_step(sb, tid, k);
+            cta_sync();
+        }
+        int run = scan_incl(sb, tid) - acc;
+        for (int i = lo; i < hi; i++) {
+            const int t = ld_g(&a.bsum[i]);
+            st_g(&a.bsum[i], run);
+            run += t;
+        }
+        if (tid == GNT - 1)
+            *a.K = scan_incl(sb, tid);
+    }
+    grid_sync(g, (unsigned)G, epoch, a.status, tid);
+    CCL_TICK(1, 3);
+    // root k in raster order receives label k+1 (stored as -(k+1))
+    label_roots<C>(a, s0, s1, ld_g(&a.bsum[b]) + incl - c);
+
+    // further jump rounds while some node has not reached its root
+    for (int r = 0; r < MAX_ROUNDS - 1; r++) {
+        if (tid == 0)
+            s_flag = ld_g(&g->round_more[r]);
+        cta_sync();
+        const int f = s_flag;
+        cta_sync();
+        if (!f)
+            break;
+        bool more_r = false;
+        int dummy = 0;
+        for (int64_t seg = s0; seg < s1; seg++)
+            more_r |= jump_segment<C>(a, seg, &dummy);
+        if (more_r)
+            flag_status(&g->round_more[r + 1], 1);
+        grid_sync(g, (unsigned)G, epoch, a.status, tid);
+        if (r == MAX_ROUNDS - 2 && tid == 0 && b == 0 && ld_g(&g->round_more[r + 1]))
+            flag_status(a.status, ST_LOOP_CAP);
+    }
+#if defined(CCL_PHASE_TIMING)
+    cta_sync();
+    CCL_TICK(1, 4);
+#endif
+}
+
+// row a5 (final part) for one tile: label of every strip run, int32 labels
+template <class C> CCL_HD void final_body(const Img &a, SmemF<C> &s, int tile, int tid)
+{
+    using T = Tile<C>;
+    const int ty = tile / a.nTX, tx = tile % a.nTX;
+    CCL_TICK(2, 0);
+    T::load_bitpack(a, s, ty, tx, tid);
+    cta_sync();
+    CCL_TICK(2, 1);
+    T::strip_runs(s, tid);
+    cta_sync();
+    CCL_TICK(2, 2);
+    T::run_labels(a, s, ty, tx, tid);
+    cta_sync();
+    CCL_TICK(2, 3);
+    T::write_labels(a, s, ty, tx, tid);
+#if defined(CCL_PHASE_TIMING)
+    cta_sync();
+    CCL_TICK(2, 4);
+#endif
+}
 
 }  // namespace ccl

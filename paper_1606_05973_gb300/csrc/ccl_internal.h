@@ -21,8 +21,17 @@ const char *kernel_name(int kid);
 void prof_begin(int kid, cudaStream_t s);
 void prof_end(int kid, cudaStream_t s);
 
-// Tile shape used by the single-image path.
-using MainCfg = Cfg<64, 256, 256>;
+// Tile shape used by the single-image path (rows x columns, threads per CTA).
+#ifndef CCL_TILE_H
+#define CCL_TILE_H 64
+#endif
+#ifndef CCL_TILE_W
+#define CCL_TILE_W 256
+#endif
+#ifndef CCL_TILE_NT
+#define CCL_TILE_NT 256
+#endif
+using MainCfg = Cfg<CCL_TILE_H, CCL_TILE_W, CCL_TILE_NT>;
 
 Layout main_layout(int H, int W);
 

@@ -21,166 +21,26 @@ const char *kernel_name(int kid)
     }
 }
 
-template <class C> __global__ void __launch_bounds__(C::NT) k_tile_local(Img a)
+template <class C> __global__ void __launch_bounds__(C::NT, 2048 / C::NT) k_tile_local(Img a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemL<C> &s = *reinterpret_cast<SmemL<C> *>(smem_raw);
-    const int tile = blockIdx.x;
-    const int ty = tile / a.nTX, tx = tile % a.nTX;
-    const int tid = threadIdx.x;
-    using T = Tile<C>;
-    if (tile == 0) {
-        // reset the grid barrier of the global kernel that follows on this stream
-        unsigned *g = reinterpret_cast<unsigned *>(a.gsync);
-        for (int i = tid; i < (int)(sizeof(GridSync) / 4); i += C::NT)
-            g[i] = 0u;
-    }
-    T::load_image(a, s, ty, tx, tid);
-    __syncthreads();
-    T::store_bitpack(a, s, ty, tx, tid);
-    T::strip_runs(s, tid);
-    __syncthreads();
-    T::strip_prefix(s, tid);
-    __syncthreads();
-    T::unions(a, s, tid);
-    __syncthreads();
-    T::roots(a, s, tid);
-    __syncthreads();
-    T::first_pixels(a, s, tid);
-    __syncthreads();
-    T::mark_roots(a, s, tid);
-    __syncthreads();
-    T::root_prefix(a, s, ty, tx, tid);
-    __syncthreads();
-    T::outputs(a, s, ty, tx, tid);
+    tile_local_body<C>(a, *reinterpret_cast<SmemL<C> *>(smem_raw), blockIdx.x, threadIdx.x);
 }
 
-// Grid barrier for the cooperative global kernel (all CTAs are co-resident).  Each wait
-// is capped: after BARRIER_SPIN_CAP polls the CTA records ST_BARRIER and goes on, so a
-// broken launch ends with an error status instead of hanging the GPU.
-constexpr int BARRIER_SPIN_CAP = 1 << 21;
-
-__device__ __forceinline__ void grid_barrier(GridSync *g, unsigned nblocks, unsigned &epoch, int *status)
-{
-    __syncthreads();
-    epoch += 1;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(&g->arrive, 1u);
-        const unsigned target = epoch * nblocks;
-        int it = 0;
-        while (*reinterpret_cast<volatile unsigned *>(&g->arrive) < target) {
-            if (++it > BARRIER_SPIN_CAP) {
-                atomicOr(status, ST_BARRIER);
-                break;
-            }
-            __nanosleep(32);
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
-
-template <class C> __global__ void __launch_bounds__(GNT) k_global(Img a)
+#ifndef CCL_GLOBAL_MIN_CTAS
+#define CCL_GLOBAL_MIN_CTAS 2
+#endif
+template <class C> __global__ void __launch_bounds__(GNT, CCL_GLOBAL_MIN_CTAS) k_global(Img a)
 {
     __shared__ ScanBuf sb;
     __shared__ int s_flag;
-    const int tid = threadIdx.x, b = blockIdx.x;
-    const unsigned G = gridDim.x;
-    unsigned epoch = 0;
-    GridSync *g = a.gsync;
-    const int64_t stride = (int64_t)G * GNT;
-
-    // a3: boundary merge (Algorithm 7's boundary loop with Algorithm 8's union)
-    const int64_t nh = (int64_t)(a.nTY - 1) * a.W;
-    const int64_t nv = (int64_t)(a.nTX - 1) * a.H;
-    for (int64_t i = (int64_t)b * GNT + tid; i < nh + nv; i += stride) {
-        if (i < nh) {
-            merge_h<C>(a, 1 + (int)(i / a.W), (int)(i % a.W));
-        } else {
-            const int64_t k = i - nh;
-            merge_v<C>(a, 1 + (int)(k / a.H), (int)(k % a.H));
-        }
-    }
-    grid_barrier(g, G, epoch, a.status);
-
-    // a4: flatten by pointer jumping, until a round finds every node at its root
-    for (int r = 0; r < MAX_ROUNDS; r++) {
-        bool more = false;
-        for (int64_t seg = (int64_t)b * GNT + tid; seg < a.nSeg; seg += stride)
-            more |= jump_segment<C>(a, seg);
-        if (more)
-            atomicOr(&g->round_more[r], 1);
-        grid_barrier(g, G, epoch, a.status);
-        if (tid == 0)
-            s_flag = *reinterpret_cast<volatile int *>(&g->round_more[r]);
-        __syncthreads();
-        const int f = s_flag;
-        __syncthreads();
-        if (!f)
-            break;
-        if (r == MAX_ROUNDS - 1 && tid == 0 && b == 0)
-            atomicOr(a.status, ST_LOOP_CAP);
-    }
-
-    // a5: roots per thread over a contiguous raster range of segments, scanned across the
-    // CTA, then across CTAs; root k in raster order receives label k+1
-    int64_t s0, s1;
-    seg_range(a.nSeg, (int)G, GNT, b, tid, &s0, &s1);
-    const int c = count_roots<C>(a, s0, s1);
-    scan_put(sb, tid, c);
-    __syncthreads();
-    for (int k = 0; k < GNT_LOG; k++) {
-        scan_step(sb, tid, k);
-        __syncthreads();
-    }
-    const int incl = scan_incl(sb, tid);
-    if (tid == GNT - 1)
-        a.bsum[b] = incl;
-    grid_barrier(g, G, epoch, a.status);
-    if (b == 0) {
-        const int per = ((int)G + GNT - 1) / GNT;
-        const int lo = tid * per < (int)G ? tid * per : (int)G;
-        const int hi = lo + per < (int)G ? lo + per : (int)G;
-        int acc = 0;
-        for (int i = lo; i < hi; i++)
-            acc += ld_g(&a.bsum[i]);
-        scan_put(sb, tid, acc);
-        __syncthreads();
-        for (int k = 0; k < GNT_LOG; k++) {
-            scan_step(sb, tid, k);
-            __syncthreads();
-        }
-        int run = scan_incl(sb, tid) - acc;
-        for (int i = lo; i < hi; i++) {
-            const int t = ld_g(&a.bsum[i]);
-            a.bsum[i] = run;
-            run += t;
-        }
-        if (tid == GNT - 1)
-            *a.K = scan_incl(sb, tid);
-    }
-    grid_barrier(g, G, epoch, a.status);
-    label_roots<C>(a, s0, s1, ld_g(&a.bsum[b]) + incl - c);
+    global_body<C>(a, sb, s_flag, blockIdx.x, gridDim.x, threadIdx.x);
 }
 
-template <class C> __global__ void __launch_bounds__(C::NT) k_final(Img a)
+template <class C> __global__ void __launch_bounds__(C::NT, 2048 / C::NT) k_final(Img a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemF<C> &s = *reinterpret_cast<SmemF<C> *>(smem_raw);
-    const int tile = blockIdx.x;
-    const int ty = tile / a.nTX, tx = tile % a.nTX;
-    const int tid = threadIdx.x;
-    using T = Tile<C>;
-    T::load_bitpack(a, s, ty, tx, tid);
-    __syncthreads();
-    T::strip_runs(s, tid);
-    __syncthreads();
-    T::strip_prefix(s, tid);
-    __syncthreads();
-    T::run_labels(a, s, ty, tx, tid);
-    __syncthreads();
-    T::write_labels(a, s, ty, tx, tid);
+    final_body<C>(a, *reinterpret_cast<SmemF<C> *>(smem_raw), blockIdx.x, threadIdx.x);
 }
 
 Layout main_layout(int H, int W) { return plan_layout<MainCfg>(H, W); }

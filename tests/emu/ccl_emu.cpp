@@ -1,37 +1,275 @@
 // Host emulation of the GPU labelling path, for tests only.
 //
-// It compiles the very same tile phases (paper_1606_05973_gb300/csrc/ccl_core.cuh) with a
-// host C++ compiler and runs every CTA's threads one after another within each phase, in
-// a seeded random order, with the shared-memory tile poisoned before use.  Built with
-// AddressSanitizer it checks the kernels' index arithmetic and the absence of reads of
-// unwritten shared memory on the CPU, before anything runs on a GPU.  The library never
+// It compiles the very same kernel bodies (paper_1606_05973_gb300/csrc/ccl_core.cuh) with
+// a host C++ compiler and runs each CUDA thread as a fiber:
+//   __syncthreads()        -> a barrier over the CTA's fibers
+//   warp shuffle / ballot  -> a per-warp exchange slot between two warp barriers
+//   atomics                -> a point where the scheduler may switch to another fiber
+//   cooperative grid sync  -> a barrier over every fiber of every CTA
+// Shared memory and the workspace are poisoned before use, and the bounds-checked build
+// is on, so under AddressSanitizer any out-of-range access or read of unwritten memory in
+// the kernels fails here, on the CPU, before anything runs on a GPU.  The library never
 // loads this file; it is not a way to label images in production.
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <ucontext.h>
 
 #include <algorithm>
+#include <array>
+#include <functional>
+#include <memory>
 #include <numeric>
 #include <random>
 #include <vector>
 
 #include "../../paper_1606_05973_gb300/csrc/ccl_core.cuh"
 
+#if defined(__SANITIZE_ADDRESS__)
+#define EMU_ASAN 1
+extern "C" void __sanitizer_start_switch_fiber(void **fake_stack_save, const void *bottom, size_t size);
+extern "C" void __sanitizer_finish_switch_fiber(void *fake_stack_save, const void **bottom_old, size_t *size_old);
+#endif
+
 using namespace ccl;
 
 namespace {
 
-template <class C> struct Emu {
+// Every emulated CUDA thread is a fiber (ucontext) on the calling OS thread.  A seeded
+// scheduler picks which runnable fiber continues whenever one blocks on a barrier or
+// reaches an atomic (emu_yield), so different seeds give different interleavings.  If no
+// fiber can run and some are unfinished (a barrier that not every thread reaches, e.g. a
+// divergent warp shuffle) the emulator aborts instead of hanging.
+struct Barrier {
+    int expected = 0, arrived = 0;
+    std::vector<int> waiting;
+};
+
+struct Fib {
+    ucontext_t ctx;
+    std::unique_ptr<char[]> stack;
+    int cta = 0, tid = 0;
+    bool done = false, runnable = true;
+};
+
+constexpr size_t kStack = 256 * 1024;
+
+struct Sched {
+    std::vector<Fib> fibs;
+    ucontext_t main_ctx;
+    int cur = -1;
     std::mt19937_64 rng;
-    std::vector<int> order;
+    std::vector<Barrier> cta_bar;
+    std::vector<std::vector<Barrier>> warp_bar;
+    std::vector<std::vector<std::array<uint32_t, 32>>> slot;
+    Barrier grid_bar;
+    std::function<void(int, int)> body;
+#if defined(EMU_ASAN)
+    const void *main_bottom = nullptr;
+    size_t main_size = 0;
+#endif
 
-    explicit Emu(uint64_t seed) : rng(seed), order(C::NT) { std::iota(order.begin(), order.end(), 0); }
-
-    template <class F> void phase(F f)
+    Sched(int nctas, int nt, uint64_t seed, std::function<void(int, int)> f) : rng(seed), body(std::move(f))
     {
+        const int nw = (nt + 31) / 32;
+        cta_bar.resize(nctas);
+        warp_bar.resize(nctas);
+        slot.resize(nctas);
+        for (int c = 0; c < nctas; c++) {
+            cta_bar[c].expected = nt;
+            warp_bar[c].resize(nw);
+            for (int w = 0; w < nw; w++)
+                warp_bar[c][w].expected = (w == nw - 1 && nt % 32) ? nt % 32 : 32;
+            slot[c].resize(nw);
+        }
+        grid_bar.expected = nctas * nt;
+        fibs.resize((size_t)nctas * nt);
+        for (int c = 0; c < nctas; c++)
+            for (int t = 0; t < nt; t++) {
+                Fib &f = fibs[(size_t)c * nt + t];
+                f.cta = c;
+                f.tid = t;
+            }
+    }
+
+    void to_main()
+    {
+#if defined(EMU_ASAN)
+        void *fake = nullptr;
+        __sanitizer_start_switch_fiber(&fake, main_bottom, main_size);
+#endif
+        swapcontext(&fibs[cur].ctx, &main_ctx);
+#if defined(EMU_ASAN)
+        __sanitizer_finish_switch_fiber(fake, nullptr, nullptr);
+#endif
+    }
+
+    void arrive(Barrier &b)
+    {
+        b.arrived++;
+        if (b.arrived == b.expected) {
+            for (int f : b.waiting)
+                fibs[f].runnable = true;
+            b.waiting.clear();
+            b.arrived = 0;
+            to_main();  // let the scheduler pick who goes on
+        } else {
+            b.waiting.push_back(cur);
+            fibs[cur].runnable = false;
+            to_main();
+        }
+    }
+
+    static void trampoline(int hi, int lo);
+
+    void run()
+    {
+        for (size_t i = 0; i < fibs.size(); i++) {
+            Fib &f = fibs[i];
+            f.stack.reset(new char[kStack]);
+            getcontext(&f.ctx);
+            f.ctx.uc_stack.ss_sp = f.stack.get();
+            f.ctx.uc_stack.ss_size = kStack;
+            f.ctx.uc_link = &main_ctx;
+            const uintptr_t self = reinterpret_cast<uintptr_t>(this);
+            makecontext(&f.ctx, (void (*)())trampoline, 2, (int)(self >> 32), (int)(self & 0xFFFFFFFFu));
+        }
+        std::vector<int> ready;
+        for (;;) {
+            ready.clear();
+            bool all_done = true;
+            for (size_t i = 0; i < fibs.size(); i++) {
+                if (!fibs[i].done) {
+                    all_done = false;
+                    if (fibs[i].runnable)
+                        ready.push_back((int)i);
+                }
+            }
+            if (all_done)
+                return;
+            if (ready.empty()) {
+                fprintf(stderr, "emulator deadlock: a barrier or warp collective not reached by every thread\n");
+                abort();
+            }
+            cur = ready[rng() % ready.size()];
+#if defined(EMU_ASAN)
+            void *fake = nullptr;
+            __sanitizer_start_switch_fiber(&fake, fibs[cur].stack.get(), kStack);
+#endif
+            swapcontext(&main_ctx, &fibs[cur].ctx);
+#if defined(EMU_ASAN)
+            __sanitizer_finish_switch_fiber(fake, &main_bottom, &main_size);
+#endif
+        }
+    }
+};
+
+Sched *g_sched = nullptr;
+
+void Sched::trampoline(int hi, int lo)
+{
+    Sched *s = reinterpret_cast<Sched *>(((uintptr_t)(uint32_t)hi << 32) | (uintptr_t)(uint32_t)lo);
+#if defined(EMU_ASAN)
+    __sanitizer_finish_switch_fiber(nullptr, &s->main_bottom, &s->main_size);
+#endif
+    const int me = s->cur;
+    s->body(s->fibs[me].cta, s->fibs[me].tid);
+    s->fibs[me].done = true;
+#if defined(EMU_ASAN)
+    void *fake = nullptr;
+    __sanitizer_start_switch_fiber(&fake, s->main_bottom, s->main_size);
+#endif
+    // returning resumes main_ctx through uc_link
+}
+
+Fib &me() { return g_sched->fibs[g_sched->cur]; }
+
+}  // namespace
+
+void emu_cta_sync() { g_sched->arrive(g_sched->cta_bar[me().cta]); }
+void emu_grid_sync() { g_sched->arrive(g_sched->grid_bar); }
+void emu_yield()
+{
+    if ((g_sched->rng() & 3) == 0)
+        g_sched->to_main();
+}
+int emu_lane() { return me().tid & 31; }
+
+static uint32_t *warp_slots() { return g_sched->slot[me().cta][me().tid / 32].data(); }
+static void warp_sync_emu() { g_sched->arrive(g_sched->warp_bar[me().cta][me().tid / 32]); }
+
+uint32_t emu_ballot(bool p)
+{
+    uint32_t *sl = warp_slots();
+    const int l = me().tid & 31;
+    sl[l] = p ? 1u : 0u;
+    warp_sync_emu();
+    uint32_t m = 0;
+    for (int i = 0; i < 32; i++)
+        m |= (sl[i] & 1u) << i;
+    warp_sync_emu();
+    return m;
+}
+int emu_shfl(int v, int src, int width)
+{
+    uint32_t *sl = warp_slots();
+    const int l = me().tid & 31;
+    sl[l] = (uint32_t)v;
+    warp_sync_emu();
+    const int r = (int)sl[(l & ~(width - 1)) + (src & (width - 1))];
+    warp_sync_emu();
+    return r;
+}
+int emu_shfl_up(int v, int delta, int width)
+{
+    uint32_t *sl = warp_slots();
+    const int l = me().tid & 31;
+    sl[l] = (uint32_t)v;
+    warp_sync_emu();
+    const int r = ((l & (width - 1)) >= delta) ? (int)sl[l - delta] : v;
+    warp_sync_emu();
+    return r;
+}
+
+namespace {
+
+template <class C> struct Emu {
+    uint64_t seed;
+    std::mt19937_64 rng;
+
+    explicit Emu(uint64_t s) : seed(s), rng(s) {}
+
+    // NT threads of one persistent CTA walk every tile (in a shuffled order)
+    template <class Smem, class Body> void run_tiles(int ntiles, Body body)
+    {
+        std::vector<int> order(ntiles);
+        std::iota(order.begin(), order.end(), 0);
         std::shuffle(order.begin(), order.end(), rng);
-        for (int t : order)
-            f(t);
+        auto smem = std::make_unique<Smem>();
+        Sched sch(1, C::NT, rng(), [&](int, int t) {
+            for (int tile : order) {
+                if (t == 0)
+                    memset(smem.get(), 0x7F, sizeof(Smem));
+                emu_cta_sync();
+                body(*smem, tile, t);
+                emu_cta_sync();
+            }
+        });
+        g_sched = &sch;
+        sch.run();
+        g_sched = nullptr;
+    }
+
+    // G CTAs of GNT threads, all running at once (cooperative launch)
+    void run_global(const Img &a, int G)
+    {
+        std::vector<ScanBuf> sbs(G);
+        std::vector<int> flags(G);
+        Sched sch(G, GNT, rng(), [&](int b, int t) { global_body<C>(a, sbs[b], flags[b], b, G, t); });
+        g_sched = &sch;
+        sch.run();
+        g_sched = nullptr;
     }
 
     int64_t run(const uint8_t *img, int H, int W, int64_t pitch, int32_t *labels, int32_t *status)
@@ -39,10 +277,11 @@ template <class C> struct Emu {
         if (H == 0 || W == 0)
             return 0;
         const Layout L = plan_layout<C>(H, W);
-        std::vector<unsigned char> ws((size_t)L.bytes + 64);
-        // poison the workspace: every value the kernels read must have been written
+        // header (K, status, grid state) + per-image arrays, poisoned
+        std::vector<unsigned char> ws((size_t)L.bytes + 256 + 64);
         memset(ws.data(), 0x7B, ws.size());
-        int K = -1;
+        char *hdr = (char *)ws.data();
+        char *b = hdr + 256;
         Img a;
         memset(&a, 0, sizeof(a));
         a.img = img;
@@ -52,9 +291,9 @@ template <class C> struct Emu {
         a.vec_in = ((uintptr_t)img % 16 == 0) && (pitch % 16 == 0);
         a.labels = labels;
         a.vec_out = ((uintptr_t)labels % 16 == 0) && (W % 4 == 0);
-        a.K = &K;
+        a.K = (int *)hdr;
         a.status = status;
-        char *b = (char *)ws.data();
+        a.gsync = (GridSync *)(hdr + 16);
         a.nTX = L.nTX;
         a.nTY = L.nTY;
         a.bitpack = (uint32_t *)(b + L.off_bitpack);
@@ -70,102 +309,13 @@ template <class C> struct Emu {
         a.nSeg = L.nSeg;
 
         const int ntiles = L.nTX * L.nTY;
-        std::vector<int> tiles(ntiles);
-        std::iota(tiles.begin(), tiles.end(), 0);
-        auto *s = new SmemL<C>;
-        auto *f = new SmemF<C>;
-        using T = Tile<C>;
-
-        // tile_local
-        std::shuffle(tiles.begin(), tiles.end(), rng);
-        for (int tile : tiles) {
-            const int ty = tile / a.nTX, tx = tile % a.nTX;
-            memset(s, 0x7F, sizeof(*s));
-            phase([&](int t) { T::load_image(a, *s, ty, tx, t); });
-            phase([&](int t) { T::store_bitpack(a, *s, ty, tx, t); T::strip_runs(*s, t); });
-            phase([&](int t) { T::strip_prefix(*s, t); });
-            phase([&](int t) { T::unions(a, *s, t); });
-            phase([&](int t) { T::roots(a, *s, t); });
-            phase([&](int t) { T::first_pixels(a, *s, t); });
-            phase([&](int t) { T::mark_roots(a, *s, t); });
-            phase([&](int t) { T::root_prefix(a, *s, ty, tx, t); });
-            phase([&](int t) { T::outputs(a, *s, ty, tx, t); });
-        }
-        // boundary merge, items in random order
-        {
-            const int64_t nh = (int64_t)(a.nTY - 1) * a.W, nv = (int64_t)(a.nTX - 1) * a.H;
-            std::vector<int64_t> items(nh + nv);
-            std::iota(items.begin(), items.end(), 0);
-            std::shuffle(items.begin(), items.end(), rng);
-            for (int64_t i : items) {
-                if (i < nh)
-                    merge_h<C>(a, 1 + (int)(i / a.W), (int)(i % a.W));
-                else
-                    merge_v<C>(a, 1 + (int)((i - nh) / a.H), (int)((i - nh) % a.H));
-            }
-        }
-        // flatten: rounds of pointer jumping over the segments (random order) until a
-        // round leaves every node at its root, as the cooperative kernel does
-        {
-            std::vector<int64_t> segs(L.nSeg);
-            std::iota(segs.begin(), segs.end(), 0);
-            for (int r = 0; r < MAX_ROUNDS; r++) {
-                std::shuffle(segs.begin(), segs.end(), rng);
-                bool more = false;
-                for (int64_t sg : segs)
-                    more |= jump_segment<C>(a, sg);
-                if (!more)
-                    break;
-                if (r == MAX_ROUNDS - 1)
-                    *a.status |= ST_LOOP_CAP;
-            }
-        }
-        // root count, scan and labels with a pseudo-grid of G CTAs of GNT threads
-        {
-            const int G = (int)std::min<int64_t>(3, (L.nSeg + GNT - 1) / GNT);
-            std::vector<int> tot(G), excl((size_t)G * GNT), cnt((size_t)G * GNT);
-            for (int bb = 0; bb < G; bb++) {
-                ScanBuf sb;
-                for (int t = 0; t < GNT; t++) {
-                    int64_t s0, s1;
-                    seg_range(L.nSeg, G, GNT, bb, t, &s0, &s1);
-                    cnt[(size_t)bb * GNT + t] = count_roots<C>(a, s0, s1);
-                    scan_put(sb, t, cnt[(size_t)bb * GNT + t]);
-                }
-                for (int k = 0; k < GNT_LOG; k++)
-                    for (int t = 0; t < GNT; t++)
-                        scan_step(sb, t, k);
-                for (int t = 0; t < GNT; t++)
-                    excl[(size_t)bb * GNT + t] = scan_incl(sb, t) - cnt[(size_t)bb * GNT + t];
-                tot[bb] = scan_incl(sb, GNT - 1);
-            }
-            int acc = 0;
-            for (int bb = 0; bb < G; bb++) {
-                const int t = tot[bb];
-                tot[bb] = acc;
-                acc += t;
-            }
-            *a.K = acc;
-            for (int bb = 0; bb < G; bb++)
-                for (int t = 0; t < GNT; t++) {
-                    int64_t s0, s1;
-                    seg_range(L.nSeg, G, GNT, bb, t, &s0, &s1);
-                    label_roots<C>(a, s0, s1, tot[bb] + excl[(size_t)bb * GNT + t]);
-                }
-        }
-        std::shuffle(tiles.begin(), tiles.end(), rng);
-        for (int tile : tiles) {
-            const int ty = tile / a.nTX, tx = tile % a.nTX;
-            memset(f, 0x7F, sizeof(*f));
-            phase([&](int t) { T::load_bitpack(a, *f, ty, tx, t); });
-            phase([&](int t) { T::strip_runs(*f, t); });
-            phase([&](int t) { T::strip_prefix(*f, t); });
-            phase([&](int t) { T::run_labels(a, *f, ty, tx, t); });
-            phase([&](int t) { T::write_labels(a, *f, ty, tx, t); });
-        }
-        delete s;
-        delete f;
-        return K;
+        run_tiles<SmemL<C>>(ntiles, [&](SmemL<C> &s, int tile, int t) { tile_local_body<C>(a, s, tile, t); });
+        const int64_t work = (int64_t)(L.nTY - 1) * W + (int64_t)(L.nTX - 1) * H;
+        const int64_t need = ((work > L.nSeg ? work : L.nSeg) + GNT - 1) / GNT;
+        const int G = (int)std::max<int64_t>(1, std::min<int64_t>(3, need));
+        run_global(a, G);
+        run_tiles<SmemF<C>>(ntiles, [&](SmemF<C> &s, int tile, int t) { final_body<C>(a, s, tile, t); });
+        return *a.K;
     }
 };
 
@@ -173,20 +323,18 @@ template <class C> struct Emu {
 
 extern "C" {
 
-// shapes: 0 = the library's main tile (64x256, 256 threads); 1 = small tile (4x32, 32 threads)
-int64_t emu_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t *labels,
-                  uint64_t seed, int32_t shape, int32_t *status)
+// shapes: 0 = 64x256 tiles (256 threads); 1 = 4x32 (32); 2 = 8x64 (64); 3 = 128x256 (256);
+// 4 = 64x512 (256)
+int64_t emu_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t *labels, uint64_t seed,
+                  int32_t shape, int32_t *status)
 {
     *status = 0;
-    if (shape == 0) {
-        Emu<Cfg<64, 256, 256>> e(seed);
-        return e.run(img, H, W, pitch, labels, status);
-    } else if (shape == 1) {
-        Emu<Cfg<4, 32, 32>> e(seed);
-        return e.run(img, H, W, pitch, labels, status);
-    } else {
-        Emu<Cfg<8, 64, 64>> e(seed);
-        return e.run(img, H, W, pitch, labels, status);
+    switch (shape) {
+    case 0: return Emu<Cfg<64, 256, 256>>(seed).run(img, H, W, pitch, labels, status);
+    case 1: return Emu<Cfg<4, 32, 32>>(seed).run(img, H, W, pitch, labels, status);
+    case 2: return Emu<Cfg<8, 64, 64>>(seed).run(img, H, W, pitch, labels, status);
+    case 3: return Emu<Cfg<128, 256, 256>>(seed).run(img, H, W, pitch, labels, status);
+    default: return Emu<Cfg<64, 512, 256>>(seed).run(img, H, W, pitch, labels, status);
     }
 }
 

@@ -31,7 +31,9 @@ def build(sanitize: bool = True) -> str:
     newest = max(os.path.getmtime(SRC), os.path.getmtime(CORE))
     if os.path.exists(so) and os.path.getmtime(so) >= newest:
         return so
-    cmd = ["g++", "-std=c++17", "-O1", "-g", "-DCCL_DEBUG", "-shared", "-fPIC", "-o", so, SRC]
+    # the global kernel's CTA size is reduced for the emulator (one OS thread per CUDA thread)
+    cmd = ["g++", "-std=c++20", "-O1", "-g", "-DCCL_DEBUG", "-DCCL_GLOBAL_NT=64", "-shared", "-fPIC",
+           "-o", so, SRC]
     if sanitize:
         cmd[1:1] = SAN
     subprocess.run(cmd, check=True)
