@@ -197,7 +197,7 @@ def label(img, connectivity: int = 8, out=None, stream=None, sync: bool = True):
     return out, kd
 
 
-def label_batch(imgs, connectivity: int = 8, outs=None, stream=None):
+def label_batch(imgs, connectivity: int = 8, outs=None, stream=None, k_out=None):
     """Label a list of 2-D uint8 CUDA tensors in one call.  Returns (labels list, K tensor)."""
     import torch
 
@@ -217,7 +217,7 @@ def label_batch(imgs, connectivity: int = 8, outs=None, stream=None):
         descs[i].W = W
         descs[i].pitch_bytes = im.stride(0) if H > 0 else W
         descs[i].labels = outs[i].data_ptr()
-    kd = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    kd = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if k_out is None else k_out
     _check(ccl_label_batch(descs, n, connectivity, kd.data_ptr(), _stream_ptr(stream)), "ccl_label_batch")
     return outs, kd[:n]
 

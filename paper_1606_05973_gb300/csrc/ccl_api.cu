@@ -26,6 +26,10 @@ struct Workspace {
     void *dev = nullptr;
     int64_t bytes = 0;
     int32_t *host_hdr = nullptr;  // pinned, 2 ints: K and status read back together
+    void *stage = nullptr;        // pinned staging of batch descriptors
+    int64_t stage_bytes = 0;
+    cudaEvent_t stage_done = nullptr;  // the last upload from `stage` has been read
+    bool stage_pending = false;
 };
 
 std::mutex g_ws_mu;
@@ -318,40 +322,131 @@ int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (n < 0 || (n > 0 && !imgs))
         return CCL_ERR_INVALID_ARGUMENT;
-    int64_t need = HDR;
+    std::vector<int32_t> keep;
+    keep.reserve(n);
     for (int32_t i = 0; i < n; i++) {
         const int32_t rc = check_args(imgs[i].img, imgs[i].H, imgs[i].W, imgs[i].pitch_bytes, connectivity,
                                       imgs[i].labels);
         if (rc != CCL_OK)
             return rc;
-        if (imgs[i].H > 0 && imgs[i].W > 0) {
-            const int64_t b = HDR + main_layout(imgs[i].H, imgs[i].W).bytes;
-            need = b > need ? b : need;
-        }
+        if (imgs[i].H > 0 && imgs[i].W > 0)
+            keep.push_back(i);
     }
-    if (n == 0)
-        return CCL_OK;
-    Workspace *w = nullptr;
-    int32_t rc = get_workspace(s, need, &w);
-    if (rc != CCL_OK)
-        return rc;
-    for (int32_t i = 0; i < n; i++) {
-        const ccl_image &im = imgs[i];
-        int32_t *k_dev = num_components_dev ? num_components_dev + i : static_cast<int32_t *>(w->dev);
-        if (im.H == 0 || im.W == 0) {
-            if (num_components_dev) {
-                cudaError_t e = cudaMemsetAsync(k_dev, 0, 4, s);
+    if (connectivity != 8)
+        return connectivity == 4 ? CCL_ERR_UNSUPPORTED : CCL_ERR_INVALID_ARGUMENT;
+    cudaError_t e = kernels_init();
+    if (e != cudaSuccess)
+        return map_cuda(e);
+    if (num_components_dev) {
+        for (int32_t i = 0; i < n; i++) {
+            if (imgs[i].H == 0 || imgs[i].W == 0) {
+                e = cudaMemsetAsync(num_components_dev + i, 0, 4, s);
                 if (e != cudaSuccess)
                     return map_cuda(e);
             }
-            continue;
         }
-        rc = enqueue_one(im.img, im.H, im.W, im.pitch_bytes, im.labels, k_dev, w,
-                         static_cast<char *>(w->dev) + HDR, s);
-        if (rc != CCL_OK)
-            return rc;
     }
-    return CCL_OK;
+    const int32_t m = (int32_t)keep.size();
+    if (m == 0)
+        return CCL_OK;
+
+    // workspace: header | descriptors | tile, item, segment prefixes | image rank offsets |
+    // per-CTA sums | one layout per image
+    std::vector<Layout> L(m);
+    std::vector<int64_t> loff(m);
+    int64_t o = 0;
+    const int64_t desc_bytes = align256((int64_t)m * (int64_t)sizeof(Img));
+    const int64_t pre_bytes = align256(3 * (int64_t)(m + 1) * 8);
+    const int64_t base_bytes = align256((int64_t)(m + 1) * 4);
+    const int64_t bsum_bytes = align256((int64_t)MAX_GLOBAL_CTAS * 4);
+    o = HDR + desc_bytes + pre_bytes + base_bytes + bsum_bytes;
+    for (int32_t k = 0; k < m; k++) {
+        L[k] = main_layout(imgs[keep[k]].H, imgs[keep[k]].W);
+        loff[k] = o;
+        o = align256(o + L[k].bytes);
+    }
+    Workspace *w = nullptr;
+    int32_t rc = get_workspace(s, o, &w);
+    if (rc != CCL_OK)
+        return rc;
+    const int64_t stage_need = desc_bytes + pre_bytes;
+    int capturing = 0;
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            capturing = 1;
+    }
+    if (w->stage_pending && !capturing) {
+        // the previous upload must have left the staging buffer before it is rewritten
+        e = cudaEventSynchronize(w->stage_done);
+        if (e != cudaSuccess)
+            return map_cuda(e);
+        w->stage_pending = false;
+    }
+    if (w->stage_bytes < stage_need) {
+        if (w->stage)
+            cudaFreeHost(w->stage);
+        w->stage = nullptr;
+        w->stage_bytes = 0;
+        e = cudaMallocHost(&w->stage, (size_t)stage_need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return CCL_ERR_OUT_OF_MEMORY;
+        }
+        w->stage_bytes = stage_need;
+    }
+    if (!w->stage_done) {
+        e = cudaEventCreateWithFlags(&w->stage_done, cudaEventDisableTiming);
+        if (e != cudaSuccess)
+            return map_cuda(e);
+    }
+    char *dev = static_cast<char *>(w->dev);
+    char *host = static_cast<char *>(w->stage);
+    Img *hd = reinterpret_cast<Img *>(host);
+    int64_t *hpre = reinterpret_cast<int64_t *>(host + desc_bytes);
+    int64_t *tileStart = hpre, *itemStart = hpre + (m + 1), *segStart = hpre + 2 * (m + 1);
+    tileStart[0] = itemStart[0] = segStart[0] = 0;
+    for (int32_t k = 0; k < m; k++) {
+        const ccl_image &im = imgs[keep[k]];
+        Img a;
+        memset(&a, 0, sizeof(a));
+        a.img = im.img;
+        a.pitch = im.pitch_bytes;
+        a.H = im.H;
+        a.W = im.W;
+        a.vec_in = ((reinterpret_cast<uintptr_t>(im.img) & 15) == 0) && (im.pitch_bytes % 16 == 0);
+        a.labels = im.labels;
+        a.vec_out = ((reinterpret_cast<uintptr_t>(im.labels) & 15) == 0) && (im.W % 4 == 0);
+        a.K = num_components_dev ? num_components_dev + keep[k] : nullptr;
+        a.status = reinterpret_cast<int *>(dev + 4);
+        a.gsync = nullptr;
+        bind_workspace(a, L[k], dev + loff[k]);
+        hd[k] = a;
+        tileStart[k + 1] = tileStart[k] + (int64_t)L[k].nTX * L[k].nTY;
+        itemStart[k + 1] = itemStart[k] + (int64_t)(L[k].nTY - 1) * im.W + (int64_t)(L[k].nTX - 1) * im.H;
+        segStart[k + 1] = segStart[k] + L[k].nSeg;
+    }
+    e = cudaMemcpyAsync(dev + HDR, host, (size_t)stage_need, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess)
+        return map_cuda(e);
+    if (!capturing) {
+        e = cudaEventRecord(w->stage_done, s);
+        if (e != cudaSuccess)
+            return map_cuda(e);
+        w->stage_pending = true;
+    }
+    Batch B;
+    B.n = m;
+    B.imgs = reinterpret_cast<const Img *>(dev + HDR);
+    const int64_t *dpre = reinterpret_cast<const int64_t *>(dev + HDR + desc_bytes);
+    B.tileStart = dpre;
+    B.itemStart = dpre + (m + 1);
+    B.segStart = dpre + 2 * (m + 1);
+    B.imgBase = reinterpret_cast<int *>(dev + HDR + desc_bytes + pre_bytes);
+    B.bsum = reinterpret_cast<int *>(dev + HDR + desc_bytes + pre_bytes + base_bytes);
+    B.gsync = reinterpret_cast<GridSync *>(dev + 16);
+    B.status = reinterpret_cast<int *>(dev + 4);
+    return map_cuda(launch_batch(B, tileStart[m], itemStart[m], segStart[m], s));
 }
 
 int32_t ccl_device_status(ccl_stream_t stream, int32_t *flags)
@@ -383,6 +478,10 @@ int32_t ccl_release(void)
             cudaFree(kv.second.dev);
         if (kv.second.host_hdr)
             cudaFreeHost(kv.second.host_hdr);
+        if (kv.second.stage)
+            cudaFreeHost(kv.second.stage);
+        if (kv.second.stage_done)
+            cudaEventDestroy(kv.second.stage_done);
     }
     g_ws.clear();
     return map_cuda(e);

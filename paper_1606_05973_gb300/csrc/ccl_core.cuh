@@ -349,6 +349,7 @@ struct Img {
     struct GridSync *gsync;  // grid barrier state of the global kernel (workspace header)
     int *labels;         // [H][W] int32 output
     int vec_out;         // labels 16-byte aligned and W % 4 == 0
+    int label_base;      // subtracted from the global rank labels (batch: ranks before this image)
     int *status;         // device status word (ST_* bits)
     int64_t nP, nSeg, nRunInfo;  // array sizes (for checked builds)
 };
@@ -845,7 +846,7 @@ template <class C> struct Tile {
                         v[k] = ld_ro(&a.P[CCL_CHK((int64_t)v[k], a.nP, a.status)]);
                 for (int k = 0; k < 4 && k0 + k < n; k++) {
                     if (fresh[k]) {
-                        prev_lab = -v[k];
+                        prev_lab = -v[k] - a.label_base;
 #if defined(CCL_DEBUG)
                         if (prev_lab <= 0) {
                             flag_status(a.status, ST_BAD_VALUE);
@@ -1001,8 +1002,9 @@ template <class C> CCL_HD bool jump_segment(const Img &a, int64_t seg, int *root
     return more;
 }
 
-// roots of segments [s0, s1) get -(label): labels continue from `off` in raster order
-template <class C> CCL_HD void label_roots(const Img &a, int64_t s0, int64_t s1, int off)
+// roots of segments [s0, s1) get -(label): labels continue from `off` in raster order;
+// returns the last label given (off if none)
+template <class C> CCL_HD int label_roots(const Img &a, int64_t s0, int64_t s1, int off)
 {
     for (int64_t seg = s0; seg < s1; seg++) {
         const int n = a.nseg[seg];
@@ -1019,6 +1021,7 @@ template <class C> CCL_HD void label_roots(const Img &a, int64_t s0, int64_t s1,
             }
         }
     }
+    return off;
 }
 
 // contiguous range of segments owned by thread (block b, thread t) for counting/labelling
@@ -1115,7 +1118,7 @@ template <class C> CCL_HD void tile_local_body(const Img &a, SmemL<C> &s, int ti
 {
     using T = Tile<C>;
     const int ty = tile / a.nTX, tx = tile % a.nTX;
-    if (tile == 0) {
+    if (tile == 0 && a.gsync) {
         // reset the grid barrier of the global kernel that follows on this stream
         unsigned *g = reinterpret_cast<unsigned *>(a.gsync);
         for (int i = tid; i < (int)(sizeof(GridSync) / 4); i += C::NT)
@@ -1274,6 +1277,179 @@ template <class C> CCL_HD void final_body(const Img &a, SmemF<C> &s, int tile, i
     cta_sync();
     CCL_TICK(2, 4);
 #endif
+}
+
+// ---- batches: many images, one launch per kernel ---------------------------------------
+// Tiles, boundary items and segments of all images are numbered consecutively; prefix
+// arrays (n+1 entries) map a number back to its image.  Ranks of global roots run over the
+// whole batch; imgBase[i] holds the ranks before image i, and the final pass subtracts it,
+// so every image is numbered 1..K_i on its own.  Images with no pixels are left out by the
+// host.
+struct Batch {
+    int n;
+    const Img *imgs;           // device array of n per-image descriptors
+    const int64_t *tileStart;  // n+1
+    const int64_t *itemStart;  // n+1 boundary-merge items
+    const int64_t *segStart;   // n+1 segments
+    int *imgBase;              // n+1 rank offsets (written by the global kernel)
+    GridSync *gsync;
+    int *bsum;
+    int *status;
+};
+
+// largest i in [0, n) with start[i] <= x (empty images share their start with the next)
+CCL_HD int find_img(const int64_t *start, int n, int64_t x)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (start[mid] <= x)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// per-CTA copy of the descriptor of the image a tile belongs to
+struct TileCtx {
+    Img img;
+    int tile;
+};
+
+template <class C> CCL_HD void batch_tile_local_body(const Batch &B, TileCtx &ctx, SmemL<C> &s, int bid, int tid)
+{
+    if (tid == 0) {
+        const int m = find_img(B.tileStart, B.n, bid);
+        ctx.img = B.imgs[m];
+        ctx.tile = (int)(bid - B.tileStart[m]);
+    }
+    if (bid == 0) {
+        unsigned *g = reinterpret_cast<unsigned *>(B.gsync);
+        for (int i = tid; i < (int)(sizeof(GridSync) / 4); i += C::NT)
+            g[i] = 0u;
+    }
+    cta_sync();
+    tile_local_body<C>(ctx.img, s, ctx.tile, tid);
+}
+
+template <class C> CCL_HD void batch_final_body(const Batch &B, TileCtx &ctx, SmemF<C> &s, int bid, int tid)
+{
+    if (tid == 0) {
+        const int m = find_img(B.tileStart, B.n, bid);
+        ctx.img = B.imgs[m];
+        ctx.tile = (int)(bid - B.tileStart[m]);
+        ctx.img.label_base = ld_g(&B.imgBase[m]);
+        if (ctx.tile == 0 && ctx.img.K)
+            *ctx.img.K = ld_g(&B.imgBase[m + 1]) - ctx.img.label_base;
+    }
+    cta_sync();
+    final_body<C>(ctx.img, s, ctx.tile, tid);
+}
+
+template <class C> CCL_HD void batch_global_body(const Batch &B, ScanBuf &sb, int &s_flag, int b, int G, int tid)
+{
+    unsigned epoch = 0;
+    GridSync *g = B.gsync;
+    const int64_t stride = (int64_t)G * GNT;
+    const int n = B.n;
+
+    // a3: boundary merge over the items of all images
+    const int64_t nitems = B.itemStart[n];
+    int m = 0;
+    for (int64_t i = (int64_t)b * GNT + tid; i < nitems; i += stride) {
+        if (i >= B.itemStart[m + 1] || i < B.itemStart[m])
+            m = find_img(B.itemStart, n, i);
+        const Img &a = B.imgs[m];
+        const int64_t nh = (int64_t)(a.nTY - 1) * a.W;
+        apply_edge_item(a, load_edge_item<C>(a, i - B.itemStart[m], nh));
+    }
+    grid_sync(g, (unsigned)G, epoch, B.status, tid);
+
+    // a4 + a5: first jump round and root count over a contiguous range of the batch's
+    // segments, then the scan across the CTA and across CTAs
+    const int64_t nsegs = B.segStart[n];
+    int64_t s0, s1;
+    seg_range(nsegs, G, GNT, b, tid, &s0, &s1);
+    const int m0 = (s0 < nsegs) ? find_img(B.segStart, n, s0) : n - 1;
+    int c = 0;
+    bool more = false;
+    m = m0;
+    for (int64_t seg = s0; seg < s1; seg++) {
+        while (seg >= B.segStart[m + 1])
+            m++;
+        more |= jump_segment<C>(B.imgs[m], seg - B.segStart[m], &c);
+    }
+    if (more)
+        flag_status(&g->round_more[0], 1);
+    scan_put(sb, tid, c);
+    cta_sync();
+    for (int k = 0; k < GNT_LOG; k++) {
+        scan_step(sb, tid, k);
+        cta_sync();
+    }
+    const int incl = scan_incl(sb, tid);
+    if (tid == GNT - 1)
+        st_g(&B.bsum[b], incl);
+    grid_sync(g, (unsigned)G, epoch, B.status, tid);
+    if (b == 0) {
+        const int per = (G + GNT - 1) / GNT;
+        const int lo = tid * per < G ? tid * per : G;
+        const int hi = lo + per < G ? lo + per : G;
+        int acc = 0;
+        for (int i = lo; i < hi; i++)
+            acc += ld_g(&B.bsum[i]);
+        scan_put(sb, tid, acc);
+        cta_sync();
+        for (int k = 0; k < GNT_LOG; k++) {
+            scan_step(sb, tid, k);
+            cta_sync();
+        }
+        int run = scan_incl(sb, tid) - acc;
+        for (int i = lo; i < hi; i++) {
+            const int t = ld_g(&B.bsum[i]);
+            st_g(&B.bsum[i], run);
+            run += t;
+        }
+        if (tid == GNT - 1)
+            st_g(&B.imgBase[n], scan_incl(sb, tid));
+    }
+    grid_sync(g, (unsigned)G, epoch, B.status, tid);
+    // roots get -(batch rank + 1); the thread that meets an image's first segment records
+    // the ranks before it
+    int run = ld_g(&B.bsum[b]) + incl - c;
+    m = m0;
+    for (int64_t seg = s0; seg < s1; seg++) {
+        while (seg >= B.segStart[m + 1])
+            m++;
+        if (seg == B.segStart[m])
+            st_g(&B.imgBase[m], run);
+        const int64_t ls = seg - B.segStart[m];
+        run = label_roots<C>(B.imgs[m], ls, ls + 1, run);
+    }
+
+    for (int r = 0; r < MAX_ROUNDS - 1; r++) {
+        if (tid == 0)
+            s_flag = ld_g(&g->round_more[r]);
+        cta_sync();
+        const int f = s_flag;
+        cta_sync();
+        if (!f)
+            break;
+        bool more_r = false;
+        int dummy = 0;
+        m = m0;
+        for (int64_t seg = s0; seg < s1; seg++) {
+            while (seg >= B.segStart[m + 1])
+                m++;
+            more_r |= jump_segment<C>(B.imgs[m], seg - B.segStart[m], &dummy);
+        }
+        if (more_r)
+            flag_status(&g->round_more[r + 1], 1);
+        grid_sync(g, (unsigned)G, epoch, B.status, tid);
+        if (r == MAX_ROUNDS - 2 && tid == 0 && b == 0 && ld_g(&g->round_more[r + 1]))
+            flag_status(B.status, ST_LOOP_CAP);
+    }
 }
 
 }  // namespace ccl

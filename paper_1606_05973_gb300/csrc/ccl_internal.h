@@ -42,6 +42,9 @@ void bind_workspace(Img &a, const Layout &L, void *ws);
 // Enqueue the whole labelling path for one image on `s`.  `a` must be fully bound.
 cudaError_t launch_label(const Img &a, const Layout &L, cudaStream_t s);
 
+// Enqueue the batched path: tiles, boundary items and segments summed over the batch.
+cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, cudaStream_t s);
+
 // One-time per-process setup of kernel attributes (dynamic shared memory).
 cudaError_t kernels_init();
 

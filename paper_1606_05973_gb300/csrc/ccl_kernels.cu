@@ -43,6 +43,27 @@ template <class C> __global__ void __launch_bounds__(C::NT, 2048 / C::NT) k_fina
     final_body<C>(a, *reinterpret_cast<SmemF<C> *>(smem_raw), blockIdx.x, threadIdx.x);
 }
 
+template <class C> __global__ void __launch_bounds__(C::NT, 2048 / C::NT) k_tile_local_batch(Batch B)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ TileCtx ctx;
+    batch_tile_local_body<C>(B, ctx, *reinterpret_cast<SmemL<C> *>(smem_raw), blockIdx.x, threadIdx.x);
+}
+
+template <class C> __global__ void __launch_bounds__(GNT, CCL_GLOBAL_MIN_CTAS) k_global_batch(Batch B)
+{
+    __shared__ ScanBuf sb;
+    __shared__ int s_flag;
+    batch_global_body<C>(B, sb, s_flag, blockIdx.x, gridDim.x, threadIdx.x);
+}
+
+template <class C> __global__ void __launch_bounds__(C::NT, 2048 / C::NT) k_final_batch(Batch B)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ TileCtx ctx;
+    batch_final_body<C>(B, ctx, *reinterpret_cast<SmemF<C> *>(smem_raw), blockIdx.x, threadIdx.x);
+}
+
 Layout main_layout(int H, int W) { return plan_layout<MainCfg>(H, W); }
 
 void bind_workspace(Img &a, const Layout &L, void *ws)
@@ -65,6 +86,7 @@ void bind_workspace(Img &a, const Layout &L, void *ws)
 
 static int g_num_sms = 0;
 static int g_global_ctas = 0;
+static int g_global_batch_ctas = 0;
 
 cudaError_t kernels_init()
 {
@@ -76,6 +98,12 @@ cudaError_t kernels_init()
                                    (int)sizeof(SmemL<C>));
         if (err == cudaSuccess)
             err = cudaFuncSetAttribute(k_final<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(SmemF<C>));
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(k_tile_local_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(SmemL<C>));
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(k_final_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(SmemF<C>));
         int dev = 0, coop = 0, occ = 0;
         if (err == cudaSuccess)
@@ -93,6 +121,16 @@ cudaError_t kernels_init()
             if (g_global_ctas > MAX_GLOBAL_CTAS)
                 g_global_ctas = MAX_GLOBAL_CTAS;
             if (g_global_ctas < 1)
+                err = cudaErrorInvalidConfiguration;
+        }
+        int occb = 0;
+        if (err == cudaSuccess)
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, k_global_batch<C>, GNT, 0);
+        if (err == cudaSuccess) {
+            g_global_batch_ctas = g_num_sms * occb;
+            if (g_global_batch_ctas > MAX_GLOBAL_CTAS)
+                g_global_batch_ctas = MAX_GLOBAL_CTAS;
+            if (g_global_batch_ctas < 1)
                 err = cudaErrorInvalidConfiguration;
         }
     });
@@ -117,6 +155,13 @@ template <class K> static cudaError_t launch_tiles(K kern, int ntiles, int nt, s
     return cudaSuccess;
 }
 
+template <class K> static cudaError_t launch_tiles_b(K kern, int ntiles, int nt, size_t smem, cudaStream_t s,
+                                                     const Batch &b)
+{
+    kern<<<ntiles, nt, smem, s>>>(b);
+    return cudaSuccess;
+}
+
 cudaError_t launch_label(const Img &a, const Layout &L, cudaStream_t s)
 {
     using C = MainCfg;
@@ -132,6 +177,26 @@ cudaError_t launch_label(const Img &a, const Layout &L, cudaStream_t s)
     void *args[] = {&arg};
     CCL_LAUNCH(KID_GLOBAL, cudaLaunchCooperativeKernel((const void *)k_global<C>, dim3(grid), dim3(GNT), args, 0, s));
     CCL_LAUNCH(KID_FINAL, launch_tiles(k_final<C>, ntiles, C::NT, sizeof(SmemF<C>), s, a));
+    return cudaSuccess;
+}
+
+cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, cudaStream_t s)
+{
+    using C = MainCfg;
+    if (tiles <= 0)
+        return cudaSuccess;
+    if (tiles > 0x7FFFFFFF)
+        return cudaErrorInvalidValue;
+    CCL_LAUNCH(KID_TILE_LOCAL, launch_tiles_b(k_tile_local_batch<C>, (int)tiles, C::NT, sizeof(SmemL<C>), s, B));
+    const int64_t need = ((items > segs ? items : segs) + GNT - 1) / GNT;
+    int grid = (int)(need < g_global_batch_ctas ? need : g_global_batch_ctas);
+    if (grid < 1)
+        grid = 1;
+    Batch arg = B;
+    void *args[] = {&arg};
+    CCL_LAUNCH(KID_GLOBAL,
+               cudaLaunchCooperativeKernel((const void *)k_global_batch<C>, dim3(grid), dim3(GNT), args, 0, s));
+    CCL_LAUNCH(KID_FINAL, launch_tiles_b(k_final_batch<C>, (int)tiles, C::NT, sizeof(SmemF<C>), s, B));
     return cudaSuccess;
 }
 

@@ -272,6 +272,80 @@ template <class C> struct Emu {
         g_sched = nullptr;
     }
 
+    // the batched kernels over n images (all with H, W > 0), as ccl_label_batch runs them
+    void run_batch(int n, const uint8_t *const *imgs, const int32_t *Hs, const int32_t *Ws, const int64_t *pitches,
+                   int32_t *const *labels, int32_t *Ks, int32_t *status)
+    {
+        std::vector<Layout> L(n);
+        std::vector<std::vector<unsigned char>> ws(n);
+        std::vector<Img> descs(n);
+        std::vector<int64_t> tileStart(n + 1), itemStart(n + 1), segStart(n + 1);
+        std::vector<int> imgBase(n + 1, 0x7B7B7B7B), bsum(MAX_GLOBAL_CTAS, 0x7B7B7B7B);
+        std::vector<unsigned char> hdr(256, 0x7B);
+        for (int i = 0; i < n; i++) {
+            L[i] = plan_layout<C>(Hs[i], Ws[i]);
+            ws[i].assign((size_t)L[i].bytes + 64, 0x7B);
+            Img &a = descs[i];
+            memset(&a, 0, sizeof(a));
+            a.img = imgs[i];
+            a.pitch = pitches[i];
+            a.H = Hs[i];
+            a.W = Ws[i];
+            a.vec_in = ((uintptr_t)imgs[i] % 16 == 0) && (pitches[i] % 16 == 0);
+            a.labels = labels[i];
+            a.vec_out = ((uintptr_t)labels[i] % 16 == 0) && (Ws[i] % 4 == 0);
+            a.K = Ks + i;
+            a.status = status;
+            a.gsync = nullptr;
+            char *b = (char *)ws[i].data();
+            a.nTX = L[i].nTX;
+            a.nTY = L[i].nTY;
+            a.bitpack = (uint32_t *)(b + L[i].off_bitpack);
+            a.runinfo = (uint16_t *)(b + L[i].off_runinfo);
+            a.nRunInfo = L[i].nRunInfo;
+            a.P = (int *)(b + L[i].off_P);
+            a.nseg = (int *)(b + L[i].off_nseg);
+            a.cnt = (int *)(b + L[i].off_cnt);
+            a.edgeRow = (int *)(b + L[i].off_edgeRow);
+            a.edgeCol = (int *)(b + L[i].off_edgeCol);
+            a.bsum = (int *)(b + L[i].off_bsum);
+            a.nP = L[i].nP;
+            a.nSeg = L[i].nSeg;
+            tileStart[i + 1] = tileStart[i] + (int64_t)L[i].nTX * L[i].nTY;
+            itemStart[i + 1] = itemStart[i] + (int64_t)(L[i].nTY - 1) * Ws[i] + (int64_t)(L[i].nTX - 1) * Hs[i];
+            segStart[i + 1] = segStart[i] + L[i].nSeg;
+        }
+        Batch B;
+        B.n = n;
+        B.imgs = descs.data();
+        B.tileStart = tileStart.data();
+        B.itemStart = itemStart.data();
+        B.segStart = segStart.data();
+        B.imgBase = imgBase.data();
+        B.gsync = (GridSync *)(hdr.data() + 16);
+        B.bsum = bsum.data();
+        B.status = status;
+        struct SL2 {
+            SmemL<C> s;
+            TileCtx ctx;
+        };
+        struct SF2 {
+            SmemF<C> s;
+            TileCtx ctx;
+        };
+        const int ntiles = (int)tileStart[n];
+        run_tiles<SL2>(ntiles, [&](SL2 &sm, int tile, int t) { batch_tile_local_body<C>(B, sm.ctx, sm.s, tile, t); });
+        const int64_t need = ((itemStart[n] > segStart[n] ? itemStart[n] : segStart[n]) + GNT - 1) / GNT;
+        const int G = (int)std::max<int64_t>(1, std::min<int64_t>(3, need));
+        std::vector<ScanBuf> sbs(G);
+        std::vector<int> flags(G);
+        Sched sch(G, GNT, rng(), [&](int b, int t) { batch_global_body<C>(B, sbs[b], flags[b], b, G, t); });
+        g_sched = &sch;
+        sch.run();
+        g_sched = nullptr;
+        run_tiles<SF2>(ntiles, [&](SF2 &sm, int tile, int t) { batch_final_body<C>(B, sm.ctx, sm.s, tile, t); });
+    }
+
     int64_t run(const uint8_t *img, int H, int W, int64_t pitch, int32_t *labels, int32_t *status)
     {
         if (H == 0 || W == 0)
@@ -335,6 +409,18 @@ int64_t emu_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32
     case 2: return Emu<Cfg<8, 64, 64>>(seed).run(img, H, W, pitch, labels, status);
     case 3: return Emu<Cfg<128, 256, 256>>(seed).run(img, H, W, pitch, labels, status);
     default: return Emu<Cfg<64, 512, 256>>(seed).run(img, H, W, pitch, labels, status);
+    }
+}
+
+// the batched path; every image must have H, W > 0
+void emu_label_batch(int32_t n, const uint8_t *const *imgs, const int32_t *H, const int32_t *W, const int64_t *pitch,
+                     int32_t *const *labels, int32_t *K, uint64_t seed, int32_t shape, int32_t *status)
+{
+    *status = 0;
+    switch (shape) {
+    case 0: Emu<Cfg<64, 256, 256>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
+    case 1: Emu<Cfg<4, 32, 32>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
+    default: Emu<Cfg<8, 64, 64>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
     }
 }
 

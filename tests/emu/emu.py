@@ -47,6 +47,10 @@ class Emu:
         f.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                       ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p]
         f.restype = ctypes.c_int64
+        fb = self.lib.emu_label_batch
+        fb.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p]
+        fb.restype = None
 
     def label(self, img: np.ndarray, seed: int = 1, shape: int = 0, pitch: int | None = None, fill: int = 7):
         import synth
@@ -61,3 +65,20 @@ class Emu:
         st = np.zeros(1, np.int32)
         k = self.lib.emu_label(src.ctypes.data, h, w, pitch, lab.ctypes.data, seed, shape, st.ctypes.data)
         return lab, int(k), int(st[0])
+
+    def label_batch(self, imgs, seed: int = 1, shape: int = 1):
+        """Batched path on a list of non-empty images; returns (labels list, K list, status)."""
+        n = len(imgs)
+        srcs = [np.ascontiguousarray(im) for im in imgs]
+        labs = [np.full(im.shape, -7, np.int32) for im in srcs]
+        P = ctypes.c_void_p * n
+        ip = P(*[im.ctypes.data for im in srcs])
+        lp = P(*[lb.ctypes.data for lb in labs])
+        H = np.array([im.shape[0] for im in srcs], np.int32)
+        W = np.array([im.shape[1] for im in srcs], np.int32)
+        pitch = np.array([im.shape[1] for im in srcs], np.int64)
+        K = np.full(n, -1, np.int32)
+        st = np.zeros(1, np.int32)
+        self.lib.emu_label_batch(n, ip, H.ctypes.data, W.ctypes.data, pitch.ctypes.data, lp, K.ctypes.data,
+                                 seed, shape, st.ctypes.data)
+        return labs, [int(k) for k in K], int(st[0])

@@ -45,6 +45,20 @@ def main(path, n_random):
         if not (k == rk and st == 0 and np.array_equal(lab, ref)):
             bad += 1
             print("random mismatch", h, w, k, rk, st)
+    # batches of uneven images (the batched kernels), every image checked on its own
+    for trial in range(6):
+        k = int(rng.integers(1, 7))
+        batch = []
+        for _ in range(k):
+            h = int(rng.integers(1, 40))
+            w = int(rng.integers(1, 150))
+            batch.append((rng.random((h, w)) < rng.uniform(0.1, 0.9)).astype(np.uint8))
+        labs, ks, st = emu.label_batch(batch, seed=trial, shape=1 + trial % 2)
+        for img, lab, kk in zip(batch, labs, ks):
+            ref, rk = oracle.cclremsp(img)
+            if not (kk == rk and st == 0 and np.array_equal(lab, ref)):
+                bad += 1
+                print("batch mismatch", img.shape, kk, rk, st)
     for img in (np.zeros((0, 3), np.uint8), np.zeros((3, 0), np.uint8)):
         lab, k, st = emu.label(img)
         if k != 0:

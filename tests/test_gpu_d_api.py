@@ -86,3 +86,46 @@ def test_profile_counts_launches(ccl):
     assert kt["tile_local"][0] == 2 and kt["final_labels"][0] == 2
     assert kt["final_labels"][1] > 0.0
     ccl.ccl_profile_reset()
+
+
+def test_batch_uneven_with_empty_images_matches_single_calls(ccl):
+    import torch
+
+    specs = synth.batch_specs(n=120, seed=7, lo=1, hi=1500)
+    imgs = [synth.make_batch_image(s) if s["h"] > 1 else np.zeros((s["h"], s["w"]), np.uint8) for s in specs]
+    imgs[5] = np.zeros((0, 17), np.uint8)
+    imgs[50] = np.zeros((9, 0), np.uint8)
+    dev = [torch.from_numpy(im).cuda() for im in imgs]
+    outs, ks = ccl.label_batch(dev)
+    ks = ks.cpu().numpy()
+    for i, (im, o, k) in enumerate(zip(imgs, outs, ks)):
+        ref, rk = oracle.cclremsp(im)
+        assert k == rk, i
+        assert np.array_equal(o.cpu().numpy(), ref), i
+        lab1, k1 = ccl.label(dev[i])
+        assert k1 == rk and np.array_equal(lab1.cpu().numpy(), ref), i
+    flags = ctypes.c_int32(0)
+    assert ccl.lib().ccl_device_status(stream_handle(), ctypes.byref(flags)) == 0 and flags.value == 0
+
+
+def test_batch_graph_replay(ccl):
+    import torch
+
+    specs = synth.batch_specs(n=30, seed=9, lo=32, hi=600)
+    imgs = [synth.make_batch_image(s) for s in specs]
+    dev = [torch.from_numpy(im).cuda() for im in imgs]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        outs, ks = ccl.label_batch(dev, stream=s)  # warm-up: sizes the workspace
+        s.synchronize()
+        for o in outs:
+            o.fill_(-1)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            outs2, ks2 = ccl.label_batch(dev, outs=outs, stream=s)
+        g.replay()
+        s.synchronize()
+    for im, o, k in zip(imgs, outs2, ks2.cpu().numpy()):
+        ref, rk = oracle.cclremsp(im)
+        assert k == rk and np.array_equal(o.cpu().numpy(), ref)
