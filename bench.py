@@ -332,7 +332,156 @@ def run_ours(args, rank, world, local_rank):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline([t for _, t in imgs], args)
+    if args.batch_images > 0 or args.served:
+        del imgs, labels, host_imgs, host_labs
+        torch.cuda.empty_cache()
+    if args.batch_images > 0:
+        line["batched"] = measure_batched(args, dev, lib, stream)
+        torch.cuda.empty_cache()
+    if args.served:
+        line["served"] = measure_served(args, dev)
     return line
+
+
+def measure_served(args, dev):
+    """Serving workload: a Poisson stream of square requests (side log-uniform in
+    [256, 8192], mixed Bernoulli / blob content, seed 200) through the continuous-batching
+    server (16 GiB workspace cap, 3 lanes, batches of up to 64).  Capacity is measured with
+    every request submitted at once; then offered loads of 0.2 .. 1.0 x capacity, latency
+    from submission to completion as the server records it."""
+    import threading
+
+    import torch
+
+    import paper_1606_05973_gb300 as ccl
+
+    sys.setswitchinterval(0.0005)
+    specs = synth.served_specs(32, seed=200)
+    pool = synth.batch_device(specs, dev)
+    outs = [torch.empty(tuple(t.shape), dtype=torch.int32, device=dev) for t in pool for _ in range(2)]
+    ref_k = [ccl.label(t)[1] for t in pool]
+    torch.cuda.synchronize()
+    mean_px = sum(t.numel() for t in pool) / len(pool)
+    res = {"workload": "Poisson requests of square uint8 images, side log-uniform in [256, 8192], "
+                       "p ~ U(0.2, 0.8), alternating Bernoulli / sigma in {2,4,8} blobs (32 distinct, seed 200)",
+           "server": {"mem_cap_bytes": 16 << 30, "lanes": 3, "max_batch": 64}, "loads": []}
+    rng = np.random.Generator(np.random.PCG64(200))
+    with ccl.Server(mem_cap_bytes=16 << 30, lanes=3, max_batch=64) as srv:
+        def run(arrivals):
+            n = len(arrivals)
+            ids = [0] * n
+            bad = []
+
+            def waiter():
+                for i in range(n):
+                    while ids[i] == 0:
+                        time.sleep(0)
+                    k = srv.wait(ids[i], timeout_ms=60000)
+                    if k != ref_k[i % len(pool)]:
+                        bad.append(i)
+
+            th = threading.Thread(target=waiter, daemon=True)
+            th.start()
+            t0 = time.perf_counter()
+            for i, at in enumerate(arrivals):
+                while time.perf_counter() - t0 < at:
+                    pass
+                img = pool[i % len(pool)]
+                out = outs[2 * (i % len(pool)) + (i // len(pool)) % 2]  # one of this image's two buffers
+                assert out.shape == img.shape
+                ids[i] = srv.submit(img, out)
+            th.join(timeout=120)
+            if th.is_alive():
+                raise RuntimeError("served requests did not complete")
+            if bad:
+                raise RuntimeError(f"served component counts differ for requests {bad[:5]}")
+            return srv.stats()
+
+        # capacity: everything submitted at once
+        run([0.0] * (4 * len(pool)))
+        srv.reset_stats()
+        st = run([0.0] * (8 * len(pool)))
+        cap = st["completed"] / st["elapsed_s"]
+        res["capacity_img_s"] = round(cap, 1)
+        res["capacity_gpx_s"] = round(st["gpx_per_s"], 2)
+        for load in (0.2, 0.4, 0.6, 0.8, 1.0):
+            rate = load * cap
+            n = int(min(600, max(120, rate * 0.5)))
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n)).tolist()
+            srv.reset_stats()
+            st = run(arrivals)
+            res["loads"].append({"load": load, "rate_img_s": round(rate, 1), "requests": n,
+                                 "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                                 "max_ms": round(st["max_ms"], 3), "gpx_s": round(st["gpx_per_s"], 2),
+                                 "mean_batch": round(st["mean_batch"], 2)})
+    res["mean_request_mpx"] = round(mean_px / 1e6, 2)
+    return res
+
+
+def measure_batched(args, dev, lib, stream):
+    """The uneven-batch workload (sides log-uniform in [64, 2048], p ~ U(0.2, 0.8), half
+    Bernoulli, half sigma in {2,4,8} blobs, seed 100) labelled three ways on one stream:
+    one ccl_label_async call per image, one ccl_label_batch call, and that call replayed
+    from a CUDA graph.  Inputs resident in HBM; CUDA-event timing."""
+    import torch
+
+    import paper_1606_05973_gb300 as ccl
+
+    specs = synth.batch_specs(args.batch_images, seed=100)
+    imgs = synth.batch_device(specs, dev)
+    labs = [torch.empty(tuple(t.shape), dtype=torch.int32, device=dev) for t in imgs]
+    kd_single = torch.zeros(len(imgs), dtype=torch.int32, device=dev)
+    kd_batch = torch.zeros(len(imgs), dtype=torch.int32, device=dev)
+    px = sum(t.numel() for t in imgs)
+    # a side stream for all three (graph capture needs a non-default stream)
+    stream = torch.cuda.Stream(device=dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))
+    torch.cuda.synchronize()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+
+    def per_image():
+        for i, t in enumerate(imgs):
+            H, W = t.shape
+            rc = lib.ccl_label_async(t.data_ptr(), H, W, t.stride(0), 8, labs[i].data_ptr(),
+                                     kd_single.data_ptr() + 4 * i, sptr)
+            if rc != 0:
+                raise RuntimeError("ccl_label_async failed")
+
+    def batched():
+        ccl.label_batch(imgs, outs=labs, stream=stream, k_out=kd_batch)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(2, min(args.steps, 5))
+    with torch.cuda.stream(stream):
+        ms_single = timed(per_image, reps)
+        ms_batch = timed(batched, reps)
+        ref_k = kd_single.clone()
+        # CUDA graph of the batch call (the workspace is already sized); replayed on `stream`
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            batched()
+        kd_batch.fill_(-1)
+        ms_graph = timed(g.replay, reps)
+    if not torch.equal(kd_batch, ref_k):
+        raise RuntimeError("batched and per-image component counts differ")
+    return {"workload": f"{len(imgs)} uint8 images, H and W each log-uniform in [64, 2048], "
+                        "p ~ U(0.2, 0.8), half Bernoulli / half sigma in {2,4,8} blobs, seed 100",
+            "images": len(imgs), "pixels": int(px),
+            "per_image_ms": round(ms_single, 3), "batched_ms": round(ms_batch, 3),
+            "batched_graph_ms": round(ms_graph, 3),
+            "gpx_s_per_image": round(px / ms_single / 1e6, 2), "gpx_s_batched": round(px / ms_batch / 1e6, 2),
+            "gpx_s_batched_graph": round(px / ms_graph / 1e6, 2),
+            "speedup_batched_graph_vs_per_image": round(ms_single / ms_graph, 2)}
 
 
 # ---- CPU oracle ---------------------------------------------------------------------------
@@ -421,6 +570,9 @@ def main():
     ap.add_argument("--workload", choices=["sweep8192", "big21568", "small1024"], default="sweep8192")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None, help="keep one image of the workload (profiling)")
+    ap.add_argument("--batch-images", type=int, default=4096,
+                    help="size of the uneven-batch comparison (0 skips it)")
+    ap.add_argument("--no-served", dest="served", action="store_false", help="skip the serving measurement")
     ap.add_argument("--cpu-budget-s", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3:

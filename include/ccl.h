@@ -147,6 +147,53 @@ int32_t ccl_label_static(const uint8_t *img, int32_t H, int32_t W, int64_t pitch
                          int32_t connectivity, int32_t *labels, int32_t *num_components_dev,
                          ccl_stream_t stream);
 
+/*
+ * Continuous-batching server (the serving form of the batched path; the paper's method is
+ * unchanged underneath).  Requests are admitted while others run: a scheduler thread packs
+ * waiting requests, first come first served, into one batched launch per idle lane (a CUDA
+ * stream with its own resident workspace), so launches on different lanes overlap on the
+ * device and new requests join the next launch as soon as a lane frees up.  Each result is
+ * bit-identical to labelling the image alone.
+ *
+ * Memory: mem_cap_bytes of device workspace, split evenly between the lanes and allocated
+ * at creation (it stays resident).  A request whose workspace alone exceeds a lane's share
+ * completes with CCL_ERR_TOO_LARGE.  Images and label buffers stay the caller's and must
+ * stay valid until ccl_server_wait returns for that request.
+ */
+typedef struct ccl_server ccl_server;
+
+typedef struct {
+    int64_t mem_cap_bytes; /* total device workspace of all lanes, > 0 */
+    int32_t lanes;         /* concurrent batched launches (CUDA streams), >= 1 */
+    int32_t max_batch;     /* most requests in one launch, >= 1 */
+    int32_t max_pending;   /* queued requests before submit returns CCL_ERR_BUSY (0: no limit) */
+} ccl_server_config;
+
+typedef struct {
+    int64_t completed;      /* requests finished since the last reset */
+    int64_t pixels;         /* their pixels */
+    double elapsed_s;       /* first submit to last completion */
+    double gpx_per_s;       /* pixels / elapsed */
+    double p50_ms, p99_ms, max_ms, mean_ms; /* latency: submit to completion */
+    int64_t launches;       /* batched launches */
+    double mean_batch;      /* requests per launch */
+    int64_t peak_inflight_bytes; /* workspace bytes of requests on the device at once */
+    int32_t peak_queue;     /* most requests waiting for admission */
+} ccl_server_stats;
+
+/* Create a server on the current CUDA device.  *out receives the handle. */
+int32_t ccl_server_create(const ccl_server_config *cfg, ccl_server **out);
+/* Queue one image (device pointers, 8-connectivity); *request_id receives its id.  Does not
+ * wait for the GPU.  CCL_ERR_BUSY if max_pending requests are already waiting. */
+int32_t ccl_server_submit(ccl_server *srv, const ccl_image *img, uint64_t *request_id);
+/* Wait up to timeout_ms (< 0: forever) for a request; on success *num_components receives K
+ * and the request is forgotten.  CCL_ERR_TIMEOUT if it is still running (wait again). */
+int32_t ccl_server_wait(ccl_server *srv, uint64_t request_id, int32_t *num_components, int32_t timeout_ms);
+int32_t ccl_server_get_stats(ccl_server *srv, ccl_server_stats *out);
+int32_t ccl_server_reset_stats(ccl_server *srv);
+/* Finish every admitted and queued request, then free the server. */
+int32_t ccl_server_destroy(ccl_server *srv);
+
 /* Bytes of workspace one image of H x W needs (for capacity planning). */
 int32_t ccl_workspace_bytes(int32_t H, int32_t W, int64_t *bytes);
 

@@ -20,7 +20,9 @@ __all__ = [
     "CCLError", "CCLUnavailable", "load", "lib", "ccl_label", "ccl_label_async", "ccl_label_static",
     "ccl_label_host", "ccl_label_batch", "ccl_workspace_bytes", "ccl_device_status", "ccl_release",
     "ccl_profile_enable", "ccl_profile_reset", "ccl_profile_read", "ccl_status_string",
-    "ccl_version", "label", "label_batch", "label_host", "kernel_times", "CCL_OK",
+    "ccl_version", "label", "label_batch", "label_host", "kernel_times", "CCL_OK", "Server",
+    "ccl_server_create", "ccl_server_submit", "ccl_server_wait", "ccl_server_get_stats",
+    "ccl_server_reset_stats", "ccl_server_destroy",
 ]
 
 CCL_OK = 0
@@ -42,6 +44,19 @@ class CCLUnavailable(RuntimeError):
 class ImageDesc(ctypes.Structure):
     _fields_ = [("img", ctypes.c_void_p), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
                 ("pitch_bytes", ctypes.c_int64), ("labels", ctypes.c_void_p)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("mem_cap_bytes", ctypes.c_int64), ("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("max_pending", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("pixels", ctypes.c_int64), ("elapsed_s", ctypes.c_double),
+                ("gpx_per_s", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("mean_batch", ctypes.c_double), ("peak_inflight_bytes", ctypes.c_int64),
+                ("peak_queue", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -66,6 +81,12 @@ _SIGS = {
     "ccl_profile_enable": ([_I32], _I32),
     "ccl_profile_reset": ([], _I32),
     "ccl_profile_read": ([_P, _I32, _P], _I32),
+    "ccl_server_create": ([_P, _P], _I32),
+    "ccl_server_submit": ([_P, _P, _P], _I32),
+    "ccl_server_wait": ([_P, ctypes.c_uint64, _P, _I32], _I32),
+    "ccl_server_get_stats": ([_P, _P], _I32),
+    "ccl_server_reset_stats": ([_P], _I32),
+    "ccl_server_destroy": ([_P], _I32),
 }
 
 
@@ -150,6 +171,72 @@ def ccl_profile_reset() -> int:
 
 def ccl_profile_read(out, max_entries, count_ptr) -> int:
     return lib().ccl_profile_read(out, max_entries, count_ptr)
+
+
+def ccl_server_create(cfg, out_ptr) -> int:
+    return lib().ccl_server_create(cfg, out_ptr)
+
+
+def ccl_server_submit(srv, img_desc, id_ptr) -> int:
+    return lib().ccl_server_submit(srv, img_desc, id_ptr)
+
+
+def ccl_server_wait(srv, request_id, k_ptr, timeout_ms) -> int:
+    return lib().ccl_server_wait(srv, request_id, k_ptr, timeout_ms)
+
+
+def ccl_server_get_stats(srv, out) -> int:
+    return lib().ccl_server_get_stats(srv, out)
+
+
+def ccl_server_reset_stats(srv) -> int:
+    return lib().ccl_server_reset_stats(srv)
+
+
+def ccl_server_destroy(srv) -> int:
+    return lib().ccl_server_destroy(srv)
+
+
+class Server:
+    """Continuous-batching server (ccl_server_*): submit device images, wait for K."""
+
+    def __init__(self, mem_cap_bytes: int = 16 << 30, lanes: int = 3, max_batch: int = 64, max_pending: int = 0):
+        cfg = ServerConfig(mem_cap_bytes, lanes, max_batch, max_pending)
+        h = ctypes.c_void_p()
+        _check(ccl_server_create(ctypes.byref(cfg), ctypes.byref(h)), "ccl_server_create")
+        self.h = h
+
+    def submit(self, img, labels) -> int:
+        """img: 2-D uint8 CUDA tensor (stride(1) == 1); labels: contiguous int32 (H, W)."""
+        H, W = img.shape
+        d = ImageDesc(img.data_ptr(), H, W, img.stride(0) if H > 0 else W, labels.data_ptr())
+        rid = ctypes.c_uint64(0)
+        _check(ccl_server_submit(self.h, ctypes.byref(d), ctypes.byref(rid)), "ccl_server_submit")
+        return int(rid.value)
+
+    def wait(self, request_id: int, timeout_ms: int = -1) -> int:
+        k = ctypes.c_int32(-1)
+        _check(ccl_server_wait(self.h, request_id, ctypes.byref(k), timeout_ms), "ccl_server_wait")
+        return int(k.value)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(ccl_server_get_stats(self.h, ctypes.byref(st)), "ccl_server_get_stats")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def reset_stats(self):
+        _check(ccl_server_reset_stats(self.h), "ccl_server_reset_stats")
+
+    def close(self):
+        if self.h:
+            _check(ccl_server_destroy(self.h), "ccl_server_destroy")
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 # ---- torch conveniences (marshalling only) ------------------------------------------------

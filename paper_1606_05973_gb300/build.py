@@ -16,7 +16,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
-SOURCES = ["ccl_kernels.cu", "ccl_api.cu", "ccl_static.cu"]
+SOURCES = ["ccl_kernels.cu", "ccl_api.cu", "ccl_static.cu", "ccl_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

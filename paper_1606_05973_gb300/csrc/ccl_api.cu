@@ -11,27 +11,15 @@
 #include "../../include/ccl.h"
 #include "ccl_internal.h"
 
-namespace {
-
 using namespace ccl;
+
+namespace ccl {
 
 // ---- workspace cache -----------------------------------------------------------------------
 // One workspace per (device, stream).  Layout: a 256-byte header {K, status, grid barrier
 // state of the global kernel at byte 16} followed
 // by the per-image arrays (and, for host-buffer calls, a device copy of the image and of
 // the labels).  Work on one stream is ordered, so reusing its workspace is safe.
-constexpr int64_t HDR = 256;
-
-struct Workspace {
-    void *dev = nullptr;
-    int64_t bytes = 0;
-    int32_t *host_hdr = nullptr;  // pinned, 2 ints: K and status read back together
-    void *stage = nullptr;        // pinned staging of batch descriptors
-    int64_t stage_bytes = 0;
-    cudaEvent_t stage_done = nullptr;  // the last upload from `stage` has been read
-    bool stage_pending = false;
-};
-
 std::mutex g_ws_mu;
 std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
 
@@ -170,7 +158,7 @@ int32_t read_k_and_status(Workspace *w, const int32_t *k_dev, int32_t *num_compo
     return CCL_OK;
 }
 
-}  // namespace
+}  // namespace ccl
 
 namespace ccl {
 
@@ -316,59 +304,44 @@ int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pi
     return rc;
 }
 
-int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, int32_t *num_components_dev,
-                        ccl_stream_t stream)
+}  // extern "C"
+
+namespace ccl {
+
+// Workspace bytes of a batch of m non-empty images (header, descriptors, prefixes, rank
+// offsets, CTA sums, one layout per image).
+int64_t batch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m)
 {
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (n < 0 || (n > 0 && !imgs))
-        return CCL_ERR_INVALID_ARGUMENT;
-    std::vector<int32_t> keep;
-    keep.reserve(n);
-    for (int32_t i = 0; i < n; i++) {
-        const int32_t rc = check_args(imgs[i].img, imgs[i].H, imgs[i].W, imgs[i].pitch_bytes, connectivity,
-                                      imgs[i].labels);
-        if (rc != CCL_OK)
-            return rc;
-        if (imgs[i].H > 0 && imgs[i].W > 0)
-            keep.push_back(i);
-    }
-    if (connectivity != 8)
-        return connectivity == 4 ? CCL_ERR_UNSUPPORTED : CCL_ERR_INVALID_ARGUMENT;
+    int64_t o = HDR + align256((int64_t)m * (int64_t)sizeof(Img)) + align256(3 * (int64_t)(m + 1) * 8) +
+                align256((int64_t)(m + 1) * 4) + align256((int64_t)MAX_GLOBAL_CTAS * 4);
+    for (int32_t k = 0; k < m; k++)
+        o = align256(o + main_layout(imgs[keep[k]].H, imgs[keep[k]].W).bytes);
+    return o;
+}
+
+// Enqueue the batched path for images imgs[keep[0..m)] (all checked, non-empty) on `s`
+// using workspace `w` (at least batch_bytes large).  K of image keep[k] goes to
+// k_dev[keep[k]] when k_dev is not NULL.
+int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int32_t *k_dev, Workspace *w,
+                      cudaStream_t s)
+{
     cudaError_t e = kernels_init();
     if (e != cudaSuccess)
         return map_cuda(e);
-    if (num_components_dev) {
-        for (int32_t i = 0; i < n; i++) {
-            if (imgs[i].H == 0 || imgs[i].W == 0) {
-                e = cudaMemsetAsync(num_components_dev + i, 0, 4, s);
-                if (e != cudaSuccess)
-                    return map_cuda(e);
-            }
-        }
-    }
-    const int32_t m = (int32_t)keep.size();
-    if (m == 0)
-        return CCL_OK;
-
-    // workspace: header | descriptors | tile, item, segment prefixes | image rank offsets |
-    // per-CTA sums | one layout per image
     std::vector<Layout> L(m);
     std::vector<int64_t> loff(m);
-    int64_t o = 0;
     const int64_t desc_bytes = align256((int64_t)m * (int64_t)sizeof(Img));
     const int64_t pre_bytes = align256(3 * (int64_t)(m + 1) * 8);
     const int64_t base_bytes = align256((int64_t)(m + 1) * 4);
     const int64_t bsum_bytes = align256((int64_t)MAX_GLOBAL_CTAS * 4);
-    o = HDR + desc_bytes + pre_bytes + base_bytes + bsum_bytes;
+    int64_t o = HDR + desc_bytes + pre_bytes + base_bytes + bsum_bytes;
     for (int32_t k = 0; k < m; k++) {
         L[k] = main_layout(imgs[keep[k]].H, imgs[keep[k]].W);
         loff[k] = o;
         o = align256(o + L[k].bytes);
     }
-    Workspace *w = nullptr;
-    int32_t rc = get_workspace(s, o, &w);
-    if (rc != CCL_OK)
-        return rc;
+    if (o > w->bytes)
+        return CCL_ERR_OUT_OF_MEMORY;
     const int64_t stage_need = desc_bytes + pre_bytes;
     int capturing = 0;
     {
@@ -417,7 +390,7 @@ int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, 
         a.vec_in = ((reinterpret_cast<uintptr_t>(im.img) & 15) == 0) && (im.pitch_bytes % 16 == 0);
         a.labels = im.labels;
         a.vec_out = ((reinterpret_cast<uintptr_t>(im.labels) & 15) == 0) && (im.W % 4 == 0);
-        a.K = num_components_dev ? num_components_dev + keep[k] : nullptr;
+        a.K = k_dev ? k_dev + keep[k] : nullptr;
         a.status = reinterpret_cast<int *>(dev + 4);
         a.gsync = nullptr;
         bind_workspace(a, L[k], dev + loff[k]);
@@ -447,6 +420,47 @@ int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, 
     B.gsync = reinterpret_cast<GridSync *>(dev + 16);
     B.status = reinterpret_cast<int *>(dev + 4);
     return map_cuda(launch_batch(B, tileStart[m], itemStart[m], segStart[m], s));
+}
+
+}  // namespace ccl
+
+extern "C" {
+
+int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, int32_t *num_components_dev,
+                        ccl_stream_t stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (n < 0 || (n > 0 && !imgs))
+        return CCL_ERR_INVALID_ARGUMENT;
+    std::vector<int32_t> keep;
+    keep.reserve(n);
+    for (int32_t i = 0; i < n; i++) {
+        const int32_t rc = check_args(imgs[i].img, imgs[i].H, imgs[i].W, imgs[i].pitch_bytes, connectivity,
+                                      imgs[i].labels);
+        if (rc != CCL_OK)
+            return rc;
+        if (imgs[i].H > 0 && imgs[i].W > 0)
+            keep.push_back(i);
+    }
+    if (connectivity != 8)
+        return connectivity == 4 ? CCL_ERR_UNSUPPORTED : CCL_ERR_INVALID_ARGUMENT;
+    if (num_components_dev) {
+        for (int32_t i = 0; i < n; i++) {
+            if (imgs[i].H == 0 || imgs[i].W == 0) {
+                cudaError_t e = cudaMemsetAsync(num_components_dev + i, 0, 4, s);
+                if (e != cudaSuccess)
+                    return map_cuda(e);
+            }
+        }
+    }
+    const int32_t m = (int32_t)keep.size();
+    if (m == 0)
+        return CCL_OK;
+    Workspace *w = nullptr;
+    int32_t rc = get_workspace(s, batch_bytes(imgs, keep.data(), m), &w);
+    if (rc != CCL_OK)
+        return rc;
+    return enqueue_batch(imgs, keep.data(), m, num_components_dev, w, s);
 }
 
 int32_t ccl_device_status(ccl_stream_t stream, int32_t *flags)

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/ccl.h"
+
 #include "ccl_core.cuh"
 
 namespace ccl {
@@ -47,5 +49,29 @@ cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t s
 
 // One-time per-process setup of kernel attributes (dynamic shared memory).
 cudaError_t kernels_init();
+
+// ---- host-side workspace (ccl_api.cu) ------------------------------------------------
+// A device workspace starts with a 256-byte header {K at 0, status word at 4, grid state
+// of the global kernel at 16}; the per-image or per-batch arrays follow.
+constexpr int64_t HDR = 256;
+
+struct Workspace {
+    void *dev = nullptr;
+    int64_t bytes = 0;
+    int32_t *host_hdr = nullptr;  // pinned, 2 ints: K and status read back together
+    void *stage = nullptr;        // pinned staging of batch descriptors
+    int64_t stage_bytes = 0;
+    cudaEvent_t stage_done = nullptr;  // the last upload from `stage` has been read
+    bool stage_pending = false;
+};
+
+
+int32_t map_cuda(cudaError_t e);
+int32_t check_args(const void *img, int32_t H, int32_t W, int64_t pitch, int32_t conn, const void *labels);
+// the batched path on imgs[keep[0..m)] (checked, non-empty); workspace `w` must hold
+// batch_bytes(); K of image keep[k] goes to k_dev[keep[k]] (k_dev may be NULL)
+int64_t batch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m);
+int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int32_t *k_dev, Workspace *w,
+                      cudaStream_t s);
 
 }  // namespace ccl

@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "bernoulli", "blobs", "serpentine", "checkerboard", "dot_lattice", "striped_rows",
-    "batch_specs", "make_batch_image", "sha256", "sweep_8192", "pad_pitch", "blobs_device",
+    "batch_specs", "make_batch_image", "sha256", "sweep_8192", "pad_pitch", "blobs_device", "batch_device", "served_specs",
 ]
 
 
@@ -102,6 +102,46 @@ def blobs(h: int, w: int, sigma: float, seed: int, chunk_rows: int = 2048) -> np
         x1 = min(w, x0 + chunk_rows)
         col = np.fft.irfft(np.fft.rfft(noise[:, x0:x1], axis=0) * fk[:, None], n=h, axis=0)
         out[:, x0:x1] = col > 0
+    return out
+
+
+def _smooth_torch(noise, sigma: float):
+    import torch
+
+    device = noise.device
+    k = _gauss_kernel(sigma)
+    r = (k.size - 1) // 2
+    for axis in (0, 1):
+        n = noise.shape[axis]
+        kk = np.zeros(n, dtype=np.float32)
+        for i, v in enumerate(k):
+            kk[(i - r) % n] += v
+        fk = torch.fft.rfft(torch.from_numpy(kk).to(device))
+        shape = [1, 1]
+        shape[axis] = fk.numel()
+        noise = torch.fft.irfft(torch.fft.rfft(noise, dim=axis) * fk.reshape(shape), n=n, dim=axis)
+    return noise
+
+
+def batch_device(specs, device):
+    """The images of ``batch_specs`` as uint8 torch tensors on ``device`` (same recipe as
+    ``make_batch_image``: Bernoulli items drawn on the host; blob items from host noise,
+    smoothed and thresholded at their (1-p)-quantile on the device)."""
+    import torch
+
+    out = []
+    for spec in specs:
+        h, w = spec["h"], spec["w"]
+        if spec["kind"] == "bernoulli":
+            out.append(torch.from_numpy(bernoulli(h, w, spec["p"], spec["seed"])).to(device))
+        else:
+            rng = _rng(spec["seed"])
+            noise = torch.from_numpy(rng.standard_normal((h, w), dtype=np.float32)).to(device)
+            f = _smooth_torch(noise, spec["sigma"])
+            v = f.reshape(-1)
+            k = int(round((1.0 - spec["p"]) * (v.numel() - 1)))
+            thr = torch.sort(v).values[k]
+            out.append((f > thr).to(torch.uint8))
     return out
 
 
@@ -201,6 +241,19 @@ def batch_specs(n: int = 4096, seed: int = 100, lo: int = 64, hi: int = 2048):
         sigma = float(rng.choice([2.0, 4.0, 8.0]))
         specs.append({"h": h, "w": w, "p": p, "kind": "bernoulli" if i % 2 == 0 else "blobs",
                       "sigma": sigma, "seed": seed * 100003 + i})
+    return specs
+
+
+def served_specs(n: int = 32, seed: int = 200, lo: int = 256, hi: int = 8192):
+    """Request images for the serving workload: square, side floor(exp(U(ln lo, ln hi))),
+    density p ~ U(0.2, 0.8), alternating Bernoulli(p) and sigma in {2,4,8} blobs."""
+    rng = _rng(seed)
+    specs = []
+    for i in range(n):
+        side = int(math.floor(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        specs.append({"h": side, "w": side, "p": float(rng.uniform(0.2, 0.8)),
+                      "kind": "bernoulli" if i % 2 == 0 else "blobs",
+                      "sigma": float(rng.choice([2.0, 4.0, 8.0])), "seed": seed * 100003 + i})
     return specs
 
 
