@@ -52,6 +52,26 @@ def env_int(name, default):
         return default
 
 
+# ---- multi-rank helpers (independent replicas; a collective only for timing) ------------
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Max of a per-rank float over all ranks (NCCL with a CUDA device, gloo on CPU)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gpx_s(px_per_rank: int, world: int, seconds_max: float) -> float:
+    """Whole-job throughput: every rank labels the same amount of work (weak scaling),
+    the job lasts as long as its slowest rank."""
+    return world * px_per_rank / seconds_max / 1e9
+
+
 # ---- workloads ---------------------------------------------------------------------------
 
 def make_workload(name, device, only=None):
@@ -250,13 +270,7 @@ def run_ours(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     kt = ccl.kernel_times()
     launches = sum(v[0] for v in kt.values())
-    ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
 
     # correctness spot check outside the timed region: K must match a fresh labelling
     ks = kdev.cpu().tolist()
@@ -281,13 +295,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
     for i, hl in enumerate(host_labs):
         if int(hl.max()) != ks[i]:
             raise RuntimeError("host-buffer labels disagree with the device run")
@@ -295,7 +303,7 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return None
     step_ms = ms_max / args.steps
-    value = world * px_per_step / (step_ms * 1e-3) / 1e9
+    value = aggregate_gpx_s(px_per_step, world, step_ms * 1e-3)
     peak, peak_kind = hbm_peak()
     # dominant kernel by summed device time (among those with an algorithmic byte model)
     overall = max(kt.items(), key=lambda kv: kv[1][1])[0]
@@ -324,7 +332,7 @@ def run_ours(args, rank, world, local_rank):
         "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 4)} for k, v in kt.items() if v[0]},
         "gpu_launches": int(launches),
         "components": {name: int(k) for (name, _), k in zip(imgs, ks)},
-        "e2e": {"value": round(world * px_per_step / e2e_s / 1e9, 3), "unit": UNIT,
+        "e2e": {"value": round(aggregate_gpx_s(px_per_step, world, e2e_s), 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(t.numel() for t in host_imgs)),
                 "d2h_bytes_per_step": int(sum(4 * t.numel() + 4 for t in host_labs)),
                 "api": "ccl_label_host (pinned host buffers, copies inside the timed region)"},
