@@ -211,6 +211,13 @@ def ncu_traffic(kernel, workload):
 
 # ---- our arm ------------------------------------------------------------------------------
 
+def conn_desc(desc, conn):
+    """The workload description under `conn`-connectivity (the workloads are stated for 8)."""
+    if conn == 8:
+        return desc
+    return {**desc, "workload": desc["workload"].replace("8-connectivity", f"{conn}-connectivity")}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -220,6 +227,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     lib = ccl.lib()
     imgs, desc = make_workload(args.workload, dev, args.only)
+    desc = conn_desc(desc, args.connectivity)
     if args.only:
         imgs = [(n, t) for n, t in imgs if n == args.only]
         if not imgs:
@@ -234,7 +242,7 @@ def run_ours(args, rank, world, local_rank):
     def step():
         for i, (_, t) in enumerate(imgs):
             H, W = t.shape
-            rc = lib.ccl_label_async(t.data_ptr(), H, W, t.stride(0), 8, labels[i].data_ptr(),
+            rc = lib.ccl_label_async(t.data_ptr(), H, W, t.stride(0), args.connectivity, labels[i].data_ptr(),
                                      kdev.data_ptr() + 4 * i, sptr)
             if rc != 0:
                 raise RuntimeError(f"ccl_label_async: {ccl.ccl_status_string(rc)}")
@@ -283,7 +291,8 @@ def run_ours(args, rank, world, local_rank):
     def e2e_step():
         for hi, hl in zip(host_imgs, host_labs):
             H, W = hi.shape
-            rc = lib.ccl_label_host(hi.data_ptr(), H, W, hi.stride(0), 8, hl.data_ptr(), ctypes.byref(kk), sptr)
+            rc = lib.ccl_label_host(hi.data_ptr(), H, W, hi.stride(0), args.connectivity, hl.data_ptr(),
+                                    ctypes.byref(kk), sptr)
             if rc != 0:
                 raise RuntimeError(f"ccl_label_host: {ccl.ccl_status_string(rc)}")
 
@@ -313,7 +322,7 @@ def run_ours(args, rank, world, local_rank):
     roof = None
     if dname in KERNEL_BYTES_PER_PX and dl > 0:
         achieved = KERNEL_BYTES_PER_PX[dname] * per_launch_px / (dms / dl * 1e-3) / 1e9
-        tr = ncu_traffic(dname, args.workload)
+        tr = ncu_traffic(dname, args.workload if args.connectivity == 8 else f"{args.workload}_conn{args.connectivity}")
         roof = {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                 "traffic": tr, "algorithmic_bytes_per_launch": KERNEL_BYTES_PER_PX[dname] * per_launch_px,
@@ -367,14 +376,14 @@ def measure_served(args, dev):
     specs = synth.served_specs(32, seed=200)
     pool = synth.batch_device(specs, dev)
     outs = [torch.empty(tuple(t.shape), dtype=torch.int32, device=dev) for t in pool for _ in range(2)]
-    ref_k = [ccl.label(t)[1] for t in pool]
+    ref_k = [ccl.label(t, connectivity=args.connectivity)[1] for t in pool]
     torch.cuda.synchronize()
     mean_px = sum(t.numel() for t in pool) / len(pool)
     res = {"workload": "Poisson requests of square uint8 images, side log-uniform in [256, 8192], "
                        "p ~ U(0.2, 0.8), alternating Bernoulli / sigma in {2,4,8} blobs (32 distinct, seed 200)",
            "server": {"mem_cap_bytes": 16 << 30, "lanes": 3, "max_batch": 64}, "loads": []}
     rng = np.random.Generator(np.random.PCG64(200))
-    with ccl.Server(mem_cap_bytes=16 << 30, lanes=3, max_batch=64) as srv:
+    with ccl.Server(mem_cap_bytes=16 << 30, lanes=3, max_batch=64, connectivity=args.connectivity) as srv:
         def run(arrivals):
             n = len(arrivals)
             ids = [0] * n
@@ -384,9 +393,13 @@ def measure_served(args, dev):
                 for i in range(n):
                     while ids[i] == 0:
                         time.sleep(0)
-                    k = srv.wait(ids[i], timeout_ms=60000)
+                    try:
+                        k = srv.wait(ids[i], timeout_ms=60000)
+                    except Exception as e:  # noqa: BLE001 - reported by the submitting thread
+                        bad.append((i, repr(e)))
+                        continue
                     if k != ref_k[i % len(pool)]:
-                        bad.append(i)
+                        bad.append((i, f"K {k} != {ref_k[i % len(pool)]}"))
 
             th = threading.Thread(target=waiter, daemon=True)
             th.start()
@@ -450,13 +463,13 @@ def measure_batched(args, dev, lib, stream):
     def per_image():
         for i, t in enumerate(imgs):
             H, W = t.shape
-            rc = lib.ccl_label_async(t.data_ptr(), H, W, t.stride(0), 8, labs[i].data_ptr(),
+            rc = lib.ccl_label_async(t.data_ptr(), H, W, t.stride(0), args.connectivity, labs[i].data_ptr(),
                                      kd_single.data_ptr() + 4 * i, sptr)
             if rc != 0:
                 raise RuntimeError("ccl_label_async failed")
 
     def batched():
-        ccl.label_batch(imgs, outs=labs, stream=stream, k_out=kd_batch)
+        ccl.label_batch(imgs, connectivity=args.connectivity, outs=labs, stream=stream, k_out=kd_batch)
 
     def timed(fn, reps):
         fn()
@@ -510,8 +523,13 @@ def cpu_baseline(dev_imgs, args):
     host = [t.cpu().numpy() for t in dev_imgs]
     nthr = cpu_threads()
     res = {}
-    for key, fn, cores in (("paremsp", lambda im: orc.paremsp(im, nthr, remap=False), nthr),
-                           ("cclremsp", lambda im: orc.cclremsp(im), 1)):
+    conn = args.connectivity
+    if conn != 8:  # PARemSP (Algorithm 7) is stated for 8-connectivity only
+        legs = (("cclremsp", lambda im: orc.cclremsp(im, conn), 1),)
+    else:
+        legs = (("paremsp", lambda im: orc.paremsp(im, nthr, remap=False), nthr),
+                ("cclremsp", lambda im: orc.cclremsp(im), 1))
+    for key, fn, cores in legs:
         px, secs, used = 0, 0.0, 0
         for im in host:
             t0 = time.perf_counter()
@@ -522,6 +540,11 @@ def cpu_baseline(dev_imgs, args):
             if secs > args.cpu_budget_s:
                 break
         res[key] = {"value": round(px / secs / 1e9, 4), "cores": cores, "images": used, "seconds": round(secs, 2)}
+    if conn != 8:
+        p = res["cclremsp"]
+        return {"value": p["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                "algorithm": f"CCLRemSP (Algorithm 1) with {conn}-connectivity, canonical labels",
+                "sample": f"first {p['images']} image(s) of the workload, labelled once each"}
     p = res["paremsp"]
     return {"value": p["value"], "unit": UNIT, "cores": p["cores"], "kind": "oracle",
             "algorithm": "PARemSP (Algorithm 7) on OpenMP threads, canonical renumbering excluded",
@@ -534,6 +557,8 @@ def run_reference(args, rank, world):
     (one image of the workload, round robin) per step."""
     if rank != 0:
         return None
+    if args.connectivity != 8:
+        return {"impl": "reference", "unavailable": "PARemSP (Algorithm 7) is stated for 8-connectivity only"}
     import oracle
 
     orc = oracle.default()
@@ -577,6 +602,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["sweep8192", "big21568", "small1024"], default="sweep8192")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--connectivity", type=int, choices=[8, 4], default=8,
+                    help="8 (the paper's) or 4; the reference arm supports 8 only")
     ap.add_argument("--only", default=None, help="keep one image of the workload (profiling)")
     ap.add_argument("--batch-images", type=int, default=4096,
                     help="size of the uneven-batch comparison (0 skips it)")

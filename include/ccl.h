@@ -5,8 +5,9 @@
  *
  * Problem (Section III of the paper): every object pixel of a binary image receives a
  * label so that connected object pixels share one.  An object pixel is any non-zero
- * byte; pixels outside the image are background.  Connectivity is 8 (Section III: the
- * paper uses 8-connectedness only).
+ * byte; pixels outside the image are background.  Connectivity is 8, the paper's (Section
+ * III), or 4 (edge neighbours only), an extension that runs the same passes with one-row
+ * strips in place of the two-row ones.
  *
  * Output numbering (the paper's flatten, Algorithm 3, yields consecutive labels starting
  * at the smallest equivalent label; this library fixes the order): background 0, and
@@ -35,8 +36,10 @@ typedef struct CUstream_st *ccl_stream_t;
 
 typedef enum {
     CCL_OK = 0,
-    CCL_ERR_INVALID_ARGUMENT = 1, /* NULL pointer, negative size, pitch < W, H*W >= 2^31 */
-    CCL_ERR_UNSUPPORTED = 2,      /* connectivity other than 8 */
+    CCL_ERR_INVALID_ARGUMENT = 1, /* NULL pointer, negative size, pitch < W, H*W >= 2^31,
+                                     connectivity not 4 or 8 */
+    CCL_ERR_UNSUPPORTED = 2,      /* more tile runs than 32-bit node ids can number, or a device
+                                     index above 63 (ccl_label_static) */
     CCL_ERR_OUT_OF_MEMORY = 3,    /* workspace allocation failed */
     CCL_ERR_CUDA = 4,             /* a CUDA runtime call failed */
     CCL_ERR_TIMEOUT = 5,          /* a device loop hit its iteration cap (see status bits) */
@@ -69,7 +72,7 @@ int32_t ccl_version(void);
  *                  are read); 16-byte alignment of img and pitch enables vector loads
  *   H, W           image size, H >= 0, W >= 0, H*W < 2^31
  *   pitch_bytes    row stride of img in bytes, >= W
- *   connectivity   8 (4 returns CCL_ERR_UNSUPPORTED)
+ *   connectivity   8 or 4 (anything else: CCL_ERR_INVALID_ARGUMENT, also when H or W is 0)
  *   labels         device, H*W int32, row stride W (dense); fully overwritten
  *   num_components HOST int32 or NULL.  Non-NULL: the call waits for `stream` and
  *                  stores K; it also checks the device status word and returns
@@ -167,6 +170,7 @@ typedef struct {
     int32_t lanes;         /* concurrent batched launches (CUDA streams), >= 1 */
     int32_t max_batch;     /* most requests in one launch, >= 1 */
     int32_t max_pending;   /* queued requests before submit returns CCL_ERR_BUSY (0: no limit) */
+    int32_t connectivity;  /* 4 or 8 for every request of this server; 0 means 8 */
 } ccl_server_config;
 
 typedef struct {
@@ -183,7 +187,7 @@ typedef struct {
 
 /* Create a server on the current CUDA device.  *out receives the handle. */
 int32_t ccl_server_create(const ccl_server_config *cfg, ccl_server **out);
-/* Queue one image (device pointers, 8-connectivity); *request_id receives its id.  Does not
+/* Queue one image (device pointers, the server's connectivity); *request_id receives its id.  Does not
  * wait for the GPU.  CCL_ERR_BUSY if max_pending requests are already waiting. */
 int32_t ccl_server_submit(ccl_server *srv, const ccl_image *img, uint64_t *request_id);
 /* Wait up to timeout_ms (< 0: forever) for a request; on success *num_components receives K
@@ -194,7 +198,7 @@ int32_t ccl_server_reset_stats(ccl_server *srv);
 /* Finish every admitted and queued request, then free the server. */
 int32_t ccl_server_destroy(ccl_server *srv);
 
-/* Bytes of workspace one image of H x W needs (for capacity planning). */
+/* Bytes of workspace one image of H x W needs under either connectivity (capacity planning). */
 int32_t ccl_workspace_bytes(int32_t H, int32_t W, int64_t *bytes);
 
 /* Read and clear the device status word of `stream`'s workspace (waits for the stream).

@@ -48,7 +48,7 @@ class ImageDesc(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("mem_cap_bytes", ctypes.c_int64), ("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("max_pending", ctypes.c_int32)]
+                ("max_pending", ctypes.c_int32), ("connectivity", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -200,8 +200,9 @@ def ccl_server_destroy(srv) -> int:
 class Server:
     """Continuous-batching server (ccl_server_*): submit device images, wait for K."""
 
-    def __init__(self, mem_cap_bytes: int = 16 << 30, lanes: int = 3, max_batch: int = 64, max_pending: int = 0):
-        cfg = ServerConfig(mem_cap_bytes, lanes, max_batch, max_pending)
+    def __init__(self, mem_cap_bytes: int = 16 << 30, lanes: int = 3, max_batch: int = 64, max_pending: int = 0,
+                 connectivity: int = 8):
+        cfg = ServerConfig(mem_cap_bytes, lanes, max_batch, max_pending, connectivity)
         h = ctypes.c_void_p()
         _check(ccl_server_create(ctypes.byref(cfg), ctypes.byref(h)), "ccl_server_create")
         self.h = h

@@ -97,17 +97,15 @@ int32_t check_args(const void *img, int32_t H, int32_t W, int64_t pitch, int32_t
 {
     if (H < 0 || W < 0)
         return CCL_ERR_INVALID_ARGUMENT;
+    if (conn != 4 && conn != 8)
+        return CCL_ERR_INVALID_ARGUMENT;
     if (H == 0 || W == 0)
-        return conn == 8 ? CCL_OK : (conn == 4 ? CCL_ERR_UNSUPPORTED : CCL_ERR_INVALID_ARGUMENT);
+        return CCL_OK;
     if (!img || !labels || pitch < W)
         return CCL_ERR_INVALID_ARGUMENT;
     if ((int64_t)H * (int64_t)W >= ((int64_t)1 << 31) - 1)
         return CCL_ERR_INVALID_ARGUMENT;
-    if (conn == 4)
-        return CCL_ERR_UNSUPPORTED;
-    if (conn != 8)
-        return CCL_ERR_INVALID_ARGUMENT;
-    const Layout L = main_layout(H, W);
+    const Layout L = main_layout(H, W, conn);
     if (L.nP >= ((int64_t)1 << 31) - 1)  // global node ids are int32
         return CCL_ERR_UNSUPPORTED;
     return CCL_OK;
@@ -115,13 +113,13 @@ int32_t check_args(const void *img, int32_t H, int32_t W, int64_t pitch, int32_t
 
 // Enqueue the path for one image whose K goes to k_dev (device) and whose status bits go
 // to the workspace header.  `layout_base` is the workspace area for the per-image arrays.
-int32_t enqueue_one(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t *labels,
+int32_t enqueue_one(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t conn, int32_t *labels,
                     int32_t *k_dev, Workspace *w, char *layout_base, cudaStream_t s)
 {
     cudaError_t e = kernels_init();
     if (e != cudaSuccess)
         return map_cuda(e);
-    const Layout L = main_layout(H, W);
+    const Layout L = main_layout(H, W, conn);
     Img a;
     memset(&a, 0, sizeof(a));
     a.img = img;
@@ -135,7 +133,7 @@ int32_t enqueue_one(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int
     a.status = reinterpret_cast<int *>(static_cast<char *>(w->dev) + 4);
     a.gsync = reinterpret_cast<GridSync *>(static_cast<char *>(w->dev) + 16);
     bind_workspace(a, L, layout_base);
-    return map_cuda(launch_label(a, L, s));
+    return map_cuda(launch_label(a, L, conn, s));
 }
 
 int32_t read_k_and_status(Workspace *w, const int32_t *k_dev, int32_t *num_components, cudaStream_t s)
@@ -214,7 +212,8 @@ int32_t ccl_workspace_bytes(int32_t H, int32_t W, int64_t *bytes)
         *bytes = HDR;
         return CCL_OK;
     }
-    *bytes = HDR + main_layout(H, W).bytes;
+    const int64_t b8 = main_layout(H, W, 8).bytes, b4 = main_layout(H, W, 4).bytes;
+    *bytes = HDR + (b8 > b4 ? b8 : b4);
     return CCL_OK;
 }
 
@@ -232,11 +231,12 @@ int32_t ccl_label_async(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_
         return CCL_OK;
     }
     Workspace *w = nullptr;
-    rc = get_workspace(s, HDR + main_layout(H, W).bytes, &w);
+    rc = get_workspace(s, HDR + main_layout(H, W, connectivity).bytes, &w);
     if (rc != CCL_OK)
         return rc;
     int32_t *k_dev = num_components_dev ? num_components_dev : static_cast<int32_t *>(w->dev);
-    return enqueue_one(img, H, W, pitch_bytes, labels, k_dev, w, static_cast<char *>(w->dev) + HDR, s);
+    return enqueue_one(img, H, W, pitch_bytes, connectivity, labels, k_dev, w, static_cast<char *>(w->dev) + HDR,
+                       s);
 }
 
 int32_t ccl_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes, int32_t connectivity,
@@ -252,11 +252,11 @@ int32_t ccl_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes,
         return CCL_OK;
     }
     Workspace *w = nullptr;
-    rc = get_workspace(s, HDR + main_layout(H, W).bytes, &w);
+    rc = get_workspace(s, HDR + main_layout(H, W, connectivity).bytes, &w);
     if (rc != CCL_OK)
         return rc;
     int32_t *k_dev = static_cast<int32_t *>(w->dev);
-    rc = enqueue_one(img, H, W, pitch_bytes, labels, k_dev, w, static_cast<char *>(w->dev) + HDR, s);
+    rc = enqueue_one(img, H, W, pitch_bytes, connectivity, labels, k_dev, w, static_cast<char *>(w->dev) + HDR, s);
     if (rc != CCL_OK || !num_components)
         return rc;
     return read_k_and_status(w, k_dev, num_components, s);
@@ -275,7 +275,7 @@ int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pi
             *num_components = 0;
         return CCL_OK;
     }
-    const Layout L = main_layout(H, W);
+    const Layout L = main_layout(H, W, connectivity);
     const int64_t dpitch = (W + 15) & ~(int64_t)15;
     const int64_t img_bytes = align256((int64_t)H * dpitch);
     const int64_t lab_bytes = align256((int64_t)H * W * 4);
@@ -291,7 +291,7 @@ int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pi
     if (e != cudaSuccess)
         return map_cuda(e);
     int32_t *k_dev = reinterpret_cast<int32_t *>(base);
-    rc = enqueue_one(d_img, H, W, dpitch, d_lab, k_dev, w, base + HDR, s);
+    rc = enqueue_one(d_img, H, W, dpitch, connectivity, d_lab, k_dev, w, base + HDR, s);
     if (rc != CCL_OK)
         return rc;
     e = cudaMemcpyAsync(labels_host, d_lab, (size_t)H * W * 4, cudaMemcpyDeviceToHost, s);
@@ -310,19 +310,19 @@ namespace ccl {
 
 // Workspace bytes of a batch of m non-empty images (header, descriptors, prefixes, rank
 // offsets, CTA sums, one layout per image).
-int64_t batch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m)
+int64_t batch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn)
 {
     int64_t o = HDR + align256((int64_t)m * (int64_t)sizeof(Img)) + align256(3 * (int64_t)(m + 1) * 8) +
                 align256((int64_t)(m + 1) * 4) + align256((int64_t)MAX_GLOBAL_CTAS * 4);
     for (int32_t k = 0; k < m; k++)
-        o = align256(o + main_layout(imgs[keep[k]].H, imgs[keep[k]].W).bytes);
+        o = align256(o + main_layout(imgs[keep[k]].H, imgs[keep[k]].W, conn).bytes);
     return o;
 }
 
 // Enqueue the batched path for images imgs[keep[0..m)] (all checked, non-empty) on `s`
 // using workspace `w` (at least batch_bytes large).  K of image keep[k] goes to
 // k_dev[keep[k]] when k_dev is not NULL.
-int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int32_t *k_dev, Workspace *w,
+int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int32_t *k_dev, Workspace *w,
                       cudaStream_t s)
 {
     cudaError_t e = kernels_init();
@@ -336,7 +336,7 @@ int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int
     const int64_t bsum_bytes = align256((int64_t)MAX_GLOBAL_CTAS * 4);
     int64_t o = HDR + desc_bytes + pre_bytes + base_bytes + bsum_bytes;
     for (int32_t k = 0; k < m; k++) {
-        L[k] = main_layout(imgs[keep[k]].H, imgs[keep[k]].W);
+        L[k] = main_layout(imgs[keep[k]].H, imgs[keep[k]].W, conn);
         loff[k] = o;
         o = align256(o + L[k].bytes);
     }
@@ -419,7 +419,7 @@ int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int
     B.bsum = reinterpret_cast<int *>(dev + HDR + desc_bytes + pre_bytes + base_bytes);
     B.gsync = reinterpret_cast<GridSync *>(dev + 16);
     B.status = reinterpret_cast<int *>(dev + 4);
-    return map_cuda(launch_batch(B, tileStart[m], itemStart[m], segStart[m], s));
+    return map_cuda(launch_batch(B, tileStart[m], itemStart[m], segStart[m], conn, s));
 }
 
 }  // namespace ccl
@@ -442,8 +442,8 @@ int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, 
         if (imgs[i].H > 0 && imgs[i].W > 0)
             keep.push_back(i);
     }
-    if (connectivity != 8)
-        return connectivity == 4 ? CCL_ERR_UNSUPPORTED : CCL_ERR_INVALID_ARGUMENT;
+    if (connectivity != 4 && connectivity != 8)
+        return CCL_ERR_INVALID_ARGUMENT;
     if (num_components_dev) {
         for (int32_t i = 0; i < n; i++) {
             if (imgs[i].H == 0 || imgs[i].W == 0) {
@@ -457,10 +457,10 @@ int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, 
     if (m == 0)
         return CCL_OK;
     Workspace *w = nullptr;
-    int32_t rc = get_workspace(s, batch_bytes(imgs, keep.data(), m), &w);
+    int32_t rc = get_workspace(s, batch_bytes(imgs, keep.data(), m, connectivity), &w);
     if (rc != CCL_OK)
         return rc;
-    return enqueue_batch(imgs, keep.data(), m, num_components_dev, w, s);
+    return enqueue_batch(imgs, keep.data(), m, connectivity, num_components_dev, w, s);
 }
 
 int32_t ccl_device_status(ccl_stream_t stream, int32_t *flags)

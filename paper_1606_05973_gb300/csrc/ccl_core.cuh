@@ -314,17 +314,22 @@ CCL_HD void store4(int *dst, const int v[4])
 }
 
 // ---- tile configuration ----------------------------------------------------------------
-template <int TH_, int TW_, int NT_> struct Cfg {
+// CONN = 8: a strip is two rows (under 8-connectivity every run of row 2s | row 2s+1 is
+// connected).  CONN = 4: a strip is one row (diagonal contacts do not connect).
+template <int TH_, int TW_, int NT_, int CONN_ = 8> struct Cfg {
     static constexpr int TH = TH_;        // tile rows (even: whole strips)
     static constexpr int TW = TW_;        // tile columns (multiple of 32)
     static constexpr int NT = NT_;        // threads per CTA
+    static constexpr int CONN = CONN_;    // 8 or 4
+    static constexpr int RPS = CONN == 8 ? 2 : 1;  // rows per strip
     static constexpr int NW = TW / 32;    // 32-bit words per tile row
-    static constexpr int NS = TH / 2;     // two-row strips per tile
+    static constexpr int NS = TH / RPS;   // strips per tile
     static constexpr int CH = TW / 16;    // 16-byte chunks per tile row
     static constexpr int ROWCAP = TW / 2; // max components whose first pixel is in one tile row
     static constexpr int RC = TW / 2;     // max strip runs in one strip
     static constexpr int RMAX = NS * RC;  // max strip runs in one tile
     static_assert(TW % 32 == 0 && TH % 2 == 0, "tile shape");
+    static_assert(CONN == 8 || CONN == 4, "connectivity");
     static_assert(TH * ROWCAP <= 65536, "root codes must fit 16 bits");
     static_assert(TH * TW < 65535 && RMAX <= 65536, "positions and run numbers must fit 16 bits");
     static_assert(ROWCAP % 4 == 0, "segments are read four parents at a time");
@@ -396,7 +401,7 @@ template <class C> CCL_HD Layout plan_layout(int H, int W)
 // which needs only a popcount and a per-word prefix of start counts.
 template <class C> struct SmemRuns {
     uint32_t bits[C::TH][C::NW];     // object bits of the tile (rows beyond H are 0)
-    uint32_t starts[C::NS][C::NW];   // run starts of (row 2s | row 2s+1)
+    uint32_t starts[C::NS][C::NW];   // run starts of strip s (row 2s | row 2s+1, or row s)
     int rpre[C::NS][C::NW];          // run starts of strip s before word w
 };
 // A parent word holds the parent's run number in its low 16 bits.  The high 16 bits are
@@ -582,13 +587,24 @@ template <class C> struct Tile {
 
     CCL_HD static uint32_t strip_word(const SR &s, int st, int w)
     {
-        return s.bits[2 * st][w] | s.bits[2 * st + 1][w];
+        if constexpr (C::CONN == 4)
+            return s.bits[st][w];
+        else
+            return s.bits[2 * st][w] | s.bits[2 * st + 1][w];
     }
 
     // Tile raster position of the first pixel (raster order) of the strip run that starts
     // at bit b of word w: the first object pixel of the upper row inside the run if any,
     // else the run's first column in the lower row.
     CCL_HD static int first_pixel(const SR &s, int st, int w, int b)
+    {
+        if constexpr (C::CONN == 4)
+            return st * C::TW + w * 32 + b;  // a one-row run starts at its first pixel
+        else
+            return first_pixel2(s, st, w, b);
+    }
+
+    CCL_HD static int first_pixel2(const SR &s, int st, int w, int b)
     {
         const uint32_t R0 = s.bits[2 * st][w];
         const uint32_t M = R0 | s.bits[2 * st + 1][w];
@@ -658,12 +674,19 @@ template <class C> struct Tile {
             const int st = u / C::NW, w = u % C::NW;
             if (st == 0)
                 continue;
-            const uint32_t A = s.bits[2 * st - 1][w], B = s.bits[2 * st][w];
-            const uint32_t Ap = (w > 0) ? (s.bits[2 * st - 1][w - 1] >> 31) : 0u;
-            const uint32_t Bp = (w > 0) ? (s.bits[2 * st][w - 1] >> 31) : 0u;
+            // A: last row of strip st-1, B: first row of strip st
+            const int ra = C::RPS * st - 1, rb = C::RPS * st;
+            const uint32_t A = s.bits[ra][w], B = s.bits[rb][w];
+            const uint32_t Ap = (w > 0) ? (s.bits[ra][w - 1] >> 31) : 0u;
+            const uint32_t Bp = (w > 0) ? (s.bits[rb][w - 1] >> 31) : 0u;
             const uint32_t Ash = (A << 1) | Ap, Bsh = (B << 1) | Bp;
-            const uint32_t ev1 = (B & ~Bsh) & (A | Ash);
-            const uint32_t ev2 = (A & ~Ash) & Bsh;
+            const uint32_t sBr = B & ~Bsh, sAr = A & ~Ash;  // single-row run starts
+            // 8: the B run starts where A has a pixel at that column or one to the left, or
+            //    the A run starts one column right of a B pixel
+            // 4: the B run starts under an A pixel, or the A run starts over a B pixel that
+            //    does not start a B run
+            const uint32_t ev1 = (C::CONN == 8) ? (sBr & (A | Ash)) : (sBr & A);
+            const uint32_t ev2 = (C::CONN == 8) ? (sAr & Bsh) : (sAr & B & ~sBr);
             uint32_t evs = ev1 | ev2;
             if (!evs)
                 continue;
@@ -677,7 +700,7 @@ template <class C> struct Tile {
                 const int b = ctz32(evs);
                 evs &= evs - 1u;
                 if ((ev1 >> b) & 1u) {
-                    const int ba = ((A >> b) & 1u) ? b : b - 1;
+                    const int ba = (C::CONN == 4 || ((A >> b) & 1u)) ? b : b - 1;
                     const int na = baseA + popc32(sA & mask_upto(ba)), nb = baseB + popc32(sB & mask_upto(b));
                     if (na != last_a || nb != last_b) {
                         rem_unite_s(s.par, C::RMAX, nb, na, a.status);
@@ -686,7 +709,8 @@ template <class C> struct Tile {
                     }
                 }
                 if ((ev2 >> b) & 1u) {
-                    const int na = baseA + popc32(sA & mask_upto(b)), nb = baseB + popc32(sB & mask_upto(b - 1));
+                    const int bb = (C::CONN == 4) ? b : b - 1;
+                    const int na = baseA + popc32(sA & mask_upto(b)), nb = baseB + popc32(sB & mask_upto(bb));
                     if (na != last_a || nb != last_b) {
                         rem_unite_s(s.par, C::RMAX, na, nb, a.status);
                         last_a = na;
@@ -816,7 +840,7 @@ template <class C> struct Tile {
     {
         if (!((s.bits[r][x >> 5] >> (x & 31)) & 1u))
             return -1;
-        return (int)gid_of_code(a, ty, tx, code_of(s, comp_pos(a, s, node(s, r >> 1, x))));
+        return (int)gid_of_code(a, ty, tx, code_of(s, comp_pos(a, s, node(s, r / C::RPS, x))));
     }
 
     // -- final pass: the label of every strip run, from its code and the global table ------
@@ -870,7 +894,7 @@ template <class C> struct Tile {
             const int y = y0 + r, gx = x0 + x;
             if (y >= a.H || gx >= a.W)
                 continue;
-            const int st = r >> 1, w = x >> 5;
+            const int st = r / C::RPS, w = x >> 5;
             const uint32_t row = s.bits[r][w];
             const uint32_t starts = s.starts[st][w];
             const int base = st * C::RC + s.rpre[st][w] - 1;
@@ -932,10 +956,17 @@ template <class C> CCL_HD EdgeItem load_edge_item(const Img &a, int64_t i, int64
     return it;
 }
 
-CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it)
+template <class C> CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it)
 {
     if (it.e < 0)
         return;
+    if constexpr (C::CONN == 4) {
+        // 4-connectivity: only the facing pixel; the previous edge pixel (same node) has
+        // already joined through its own facing pixel if that one is an object pixel
+        if (it.b >= 0 && !(it.same_prev && it.aa >= 0))
+            rem_unite_g(a.P, a.nP, it.e, it.b, a.status);
+        return;
+    }
     if (it.b >= 0) {
         if (!it.same_prev)
             rem_unite_g(a.P, a.nP, it.e, it.b, a.status);
@@ -1179,7 +1210,7 @@ template <class C> CCL_HD void global_body(const Img &a, ScanBuf &sb, int &s_fla
         }
         CCL_UNROLL
         for (int k = 0; k < MB; k++)
-            apply_edge_item(a, it[k]);
+            apply_edge_item<C>(a, it[k]);
     }
     grid_sync(g, (unsigned)G, epoch, a.status, tid);
     CCL_TICK(1, 1);
@@ -1362,7 +1393,7 @@ template <class C> CCL_HD void batch_global_body(const Batch &B, ScanBuf &sb, in
             m = find_img(B.itemStart, n, i);
         const Img &a = B.imgs[m];
         const int64_t nh = (int64_t)(a.nTY - 1) * a.W;
-        apply_edge_item(a, load_edge_item<C>(a, i - B.itemStart[m], nh));
+        apply_edge_item<C>(a, load_edge_item<C>(a, i - B.itemStart[m], nh));
     }
     grid_sync(g, (unsigned)G, epoch, B.status, tid);
 

@@ -33,19 +33,21 @@ void prof_end(int kid, cudaStream_t s);
 #ifndef CCL_TILE_NT
 #define CCL_TILE_NT 256
 #endif
-using MainCfg = Cfg<CCL_TILE_H, CCL_TILE_W, CCL_TILE_NT>;
+using MainCfg = Cfg<CCL_TILE_H, CCL_TILE_W, CCL_TILE_NT, 8>;
+// 4-connectivity: one-row strips, so half the tile height keeps the same shared memory
+using MainCfg4 = Cfg<CCL_TILE_H / 2, CCL_TILE_W, CCL_TILE_NT, 4>;
 
-Layout main_layout(int H, int W);
+Layout main_layout(int H, int W, int conn);
 
 // Fill the workspace pointers of `a` (everything but img, labels, K and status) from the
 // base of the image's part of a workspace.
 void bind_workspace(Img &a, const Layout &L, void *ws);
 
 // Enqueue the whole labelling path for one image on `s`.  `a` must be fully bound.
-cudaError_t launch_label(const Img &a, const Layout &L, cudaStream_t s);
+cudaError_t launch_label(const Img &a, const Layout &L, int conn, cudaStream_t s);
 
 // Enqueue the batched path: tiles, boundary items and segments summed over the batch.
-cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, cudaStream_t s);
+cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, int conn, cudaStream_t s);
 
 // One-time per-process setup of kernel attributes (dynamic shared memory).
 cudaError_t kernels_init();
@@ -70,8 +72,8 @@ int32_t map_cuda(cudaError_t e);
 int32_t check_args(const void *img, int32_t H, int32_t W, int64_t pitch, int32_t conn, const void *labels);
 // the batched path on imgs[keep[0..m)] (checked, non-empty); workspace `w` must hold
 // batch_bytes(); K of image keep[k] goes to k_dev[keep[k]] (k_dev may be NULL)
-int64_t batch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m);
-int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int32_t *k_dev, Workspace *w,
+int64_t batch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn);
+int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int32_t *k_dev, Workspace *w,
                       cudaStream_t s);
 
 }  // namespace ccl

@@ -5,6 +5,7 @@
 //                 root count, scan and labels of the global roots    (rows a3, a4, a5)
 //   k_final       one CTA per tile: label of every strip run, int32 labels (row a5)
 // The per-tile and per-segment phases live in ccl_core.cuh.
+#include <algorithm>
 #include <mutex>
 
 #include "ccl_internal.h"
@@ -64,7 +65,10 @@ template <class C> __global__ void __launch_bounds__(C::NT, 2048 / C::NT) k_fina
     batch_final_body<C>(B, ctx, *reinterpret_cast<SmemF<C> *>(smem_raw), blockIdx.x, threadIdx.x);
 }
 
-Layout main_layout(int H, int W) { return plan_layout<MainCfg>(H, W); }
+Layout main_layout(int H, int W, int conn)
+{
+    return conn == 4 ? plan_layout<MainCfg4>(H, W) : plan_layout<MainCfg>(H, W);
+}
 
 void bind_workspace(Img &a, const Layout &L, void *ws)
 {
@@ -85,29 +89,46 @@ void bind_workspace(Img &a, const Layout &L, void *ws)
 }
 
 static int g_num_sms = 0;
-static int g_global_ctas = 0;
-static int g_global_batch_ctas = 0;
+
+template <class C> struct KernState {
+    static int global_ctas, global_batch_ctas;
+};
+template <class C> int KernState<C>::global_ctas = 0;
+template <class C> int KernState<C>::global_batch_ctas = 0;
+
+template <class C> static cudaError_t init_cfg()
+{
+    cudaError_t err = cudaFuncSetAttribute(k_tile_local<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(SmemL<C>));
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_final<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmemF<C>));
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_tile_local_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(SmemL<C>));
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_final_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(SmemF<C>));
+    int occ = 0, occb = 0;
+    if (err == cudaSuccess)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_global<C>, GNT, 0);
+    if (err == cudaSuccess)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, k_global_batch<C>, GNT, 0);
+    if (err == cudaSuccess) {
+        KernState<C>::global_ctas = std::min(g_num_sms * occ, MAX_GLOBAL_CTAS);
+        KernState<C>::global_batch_ctas = std::min(g_num_sms * occb, MAX_GLOBAL_CTAS);
+        if (KernState<C>::global_ctas < 1 || KernState<C>::global_batch_ctas < 1)
+            err = cudaErrorInvalidConfiguration;
+    }
+    return err;
+}
 
 cudaError_t kernels_init()
 {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
-        using C = MainCfg;
-        err = cudaFuncSetAttribute(k_tile_local<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)sizeof(SmemL<C>));
-        if (err == cudaSuccess)
-            err = cudaFuncSetAttribute(k_final<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(SmemF<C>));
-        if (err == cudaSuccess)
-            err = cudaFuncSetAttribute(k_tile_local_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(SmemL<C>));
-        if (err == cudaSuccess)
-            err = cudaFuncSetAttribute(k_final_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(SmemF<C>));
-        int dev = 0, coop = 0, occ = 0;
-        if (err == cudaSuccess)
-            err = cudaGetDevice(&dev);
+        int dev = 0, coop = 0;
+        err = cudaGetDevice(&dev);
         if (err == cudaSuccess)
             err = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (err == cudaSuccess)
@@ -115,24 +136,9 @@ cudaError_t kernels_init()
         if (err == cudaSuccess && !coop)
             err = cudaErrorNotSupported;
         if (err == cudaSuccess)
-            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_global<C>, GNT, 0);
-        if (err == cudaSuccess) {
-            g_global_ctas = g_num_sms * occ;
-            if (g_global_ctas > MAX_GLOBAL_CTAS)
-                g_global_ctas = MAX_GLOBAL_CTAS;
-            if (g_global_ctas < 1)
-                err = cudaErrorInvalidConfiguration;
-        }
-        int occb = 0;
+            err = init_cfg<MainCfg>();
         if (err == cudaSuccess)
-            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, k_global_batch<C>, GNT, 0);
-        if (err == cudaSuccess) {
-            g_global_batch_ctas = g_num_sms * occb;
-            if (g_global_batch_ctas > MAX_GLOBAL_CTAS)
-                g_global_batch_ctas = MAX_GLOBAL_CTAS;
-            if (g_global_batch_ctas < 1)
-                err = cudaErrorInvalidConfiguration;
-        }
+            err = init_cfg<MainCfg4>();
     });
     return err;
 }
@@ -162,15 +168,14 @@ template <class K> static cudaError_t launch_tiles_b(K kern, int ntiles, int nt,
     return cudaSuccess;
 }
 
-cudaError_t launch_label(const Img &a, const Layout &L, cudaStream_t s)
+template <class C> static cudaError_t launch_label_t(const Img &a, const Layout &L, cudaStream_t s)
 {
-    using C = MainCfg;
     const int ntiles = L.nTX * L.nTY;
     CCL_LAUNCH(KID_TILE_LOCAL, launch_tiles(k_tile_local<C>, ntiles, C::NT, sizeof(SmemL<C>), s, a));
     // the global kernel needs enough threads for its largest phase, and every CTA resident
     const int64_t work = (int64_t)(L.nTY - 1) * a.W + (int64_t)(L.nTX - 1) * a.H;
     const int64_t need = ((work > L.nSeg ? work : L.nSeg) + GNT - 1) / GNT;
-    int grid = (int)(need < g_global_ctas ? need : g_global_ctas);
+    int grid = (int)(need < KernState<C>::global_ctas ? need : KernState<C>::global_ctas);
     if (grid < 1)
         grid = 1;
     Img arg = a;
@@ -180,16 +185,16 @@ cudaError_t launch_label(const Img &a, const Layout &L, cudaStream_t s)
     return cudaSuccess;
 }
 
-cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, cudaStream_t s)
+template <class C>
+static cudaError_t launch_batch_t(const Batch &B, int64_t tiles, int64_t items, int64_t segs, cudaStream_t s)
 {
-    using C = MainCfg;
     if (tiles <= 0)
         return cudaSuccess;
     if (tiles > 0x7FFFFFFF)
         return cudaErrorInvalidValue;
     CCL_LAUNCH(KID_TILE_LOCAL, launch_tiles_b(k_tile_local_batch<C>, (int)tiles, C::NT, sizeof(SmemL<C>), s, B));
     const int64_t need = ((items > segs ? items : segs) + GNT - 1) / GNT;
-    int grid = (int)(need < g_global_batch_ctas ? need : g_global_batch_ctas);
+    int grid = (int)(need < KernState<C>::global_batch_ctas ? need : KernState<C>::global_batch_ctas);
     if (grid < 1)
         grid = 1;
     Batch arg = B;
@@ -198,6 +203,17 @@ cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t s
                cudaLaunchCooperativeKernel((const void *)k_global_batch<C>, dim3(grid), dim3(GNT), args, 0, s));
     CCL_LAUNCH(KID_FINAL, launch_tiles_b(k_final_batch<C>, (int)tiles, C::NT, sizeof(SmemF<C>), s, B));
     return cudaSuccess;
+}
+
+cudaError_t launch_label(const Img &a, const Layout &L, int conn, cudaStream_t s)
+{
+    return conn == 4 ? launch_label_t<MainCfg4>(a, L, s) : launch_label_t<MainCfg>(a, L, s);
+}
+
+cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, int conn, cudaStream_t s)
+{
+    return conn == 4 ? launch_batch_t<MainCfg4>(B, tiles, items, segs, s)
+                     : launch_batch_t<MainCfg>(B, tiles, items, segs, s);
 }
 
 }  // namespace ccl

@@ -118,7 +118,7 @@ bool try_launch_locked(ccl_server *s, Lane &L)
         Request &r = s->reqs[id];
         L.imgs.push_back(r.img);
         L.keep.push_back((int32_t)L.keep.size());
-        const int64_t need = batch_bytes(L.imgs.data(), L.keep.data(), (int32_t)L.keep.size());
+        const int64_t need = batch_bytes(L.imgs.data(), L.keep.data(), (int32_t)L.keep.size(), s->cfg.connectivity);
         if (need > L.ws.bytes) {
             L.imgs.pop_back();
             L.keep.pop_back();
@@ -136,8 +136,8 @@ bool try_launch_locked(ccl_server *s, Lane &L)
     const int32_t m = (int32_t)L.ids.size();
     if (m == 0)
         return false;
-    L.bytes = batch_bytes(L.imgs.data(), L.keep.data(), m);
-    int32_t rc = enqueue_batch(L.imgs.data(), L.keep.data(), m, L.k_dev, &L.ws, L.stream);
+    L.bytes = batch_bytes(L.imgs.data(), L.keep.data(), m, s->cfg.connectivity);
+    int32_t rc = enqueue_batch(L.imgs.data(), L.keep.data(), m, s->cfg.connectivity, L.k_dev, &L.ws, L.stream);
     cudaError_t e = cudaSuccess;
     if (rc == CCL_OK) {
         // K values and the status word back to the host, then clear the status word
@@ -213,7 +213,8 @@ extern "C" {
 
 int32_t ccl_server_create(const ccl_server_config *cfg, ccl_server **out)
 {
-    if (!cfg || !out || cfg->mem_cap_bytes <= 0 || cfg->lanes < 1 || cfg->max_batch < 1 || cfg->max_pending < 0)
+    if (!cfg || !out || cfg->mem_cap_bytes <= 0 || cfg->lanes < 1 || cfg->max_batch < 1 || cfg->max_pending < 0 ||
+        (cfg->connectivity != 0 && cfg->connectivity != 4 && cfg->connectivity != 8))
         return CCL_ERR_INVALID_ARGUMENT;
     *out = nullptr;
     cudaError_t e = kernels_init();
@@ -221,6 +222,8 @@ int32_t ccl_server_create(const ccl_server_config *cfg, ccl_server **out)
         return map_cuda(e);
     std::unique_ptr<ccl_server> s(new ccl_server);
     s->cfg = *cfg;
+    if (s->cfg.connectivity == 0)
+        s->cfg.connectivity = 8;
     e = cudaGetDevice(&s->device);
     if (e != cudaSuccess)
         return map_cuda(e);
@@ -269,7 +272,7 @@ int32_t ccl_server_submit(ccl_server *s, const ccl_image *img, uint64_t *request
 {
     if (!s || !img || !request_id)
         return CCL_ERR_INVALID_ARGUMENT;
-    const int32_t rc = check_args(img->img, img->H, img->W, img->pitch_bytes, 8, img->labels);
+    const int32_t rc = check_args(img->img, img->H, img->W, img->pitch_bytes, s->cfg.connectivity, img->labels);
     if (rc != CCL_OK)
         return rc;
     std::unique_lock<std::mutex> lk(s->mu);

@@ -61,8 +61,8 @@ extern "C" int32_t ccl_label_static(const uint8_t *img, int32_t H, int32_t W, in
 {
     using namespace ccl;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (H < 0 || W < 0 || connectivity != 8)
-        return (connectivity == 4) ? CCL_ERR_UNSUPPORTED : CCL_ERR_INVALID_ARGUMENT;
+    if (H < 0 || W < 0 || (connectivity != 4 && connectivity != 8))
+        return CCL_ERR_INVALID_ARGUMENT;
     if (H == 0 || W == 0) {
         if (num_components_dev)
             return cudaMemsetAsync(num_components_dev, 0, 4, s) == cudaSuccess ? CCL_OK : CCL_ERR_CUDA;
@@ -70,7 +70,7 @@ extern "C" int32_t ccl_label_static(const uint8_t *img, int32_t H, int32_t W, in
     }
     if (!img || !labels || pitch_bytes < W || (int64_t)H * (int64_t)W >= ((int64_t)1 << 31) - 1)
         return CCL_ERR_INVALID_ARGUMENT;
-    const Layout L = main_layout(H, W);
+    const Layout L = main_layout(H, W, connectivity);
     if (L.nP >= ((int64_t)1 << 31) - 1)
         return CCL_ERR_UNSUPPORTED;
     const int64_t hdr = 256;
@@ -101,5 +101,5 @@ extern "C" int32_t ccl_label_static(const uint8_t *img, int32_t H, int32_t W, in
     a.status = reinterpret_cast<int *>(b + 4);
     a.gsync = reinterpret_cast<GridSync *>(b + 16);
     bind_workspace(a, L, b + hdr);
-    return launch_label(a, L, s) == cudaSuccess ? CCL_OK : CCL_ERR_CUDA;
+    return launch_label(a, L, connectivity, s) == cudaSuccess ? CCL_OK : CCL_ERR_CUDA;
 }

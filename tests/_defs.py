@@ -147,10 +147,24 @@ def closed_forms():
             for j in range(cw):
                 exp[2 * i, 2 * j] = i * cw + j + 1
         cases.append((f"dots_{h}x{w}", dl, 8, ((h + 1) // 2) * cw, exp))
+        cases.append((f"dots4_{h}x{w}", dl, 4, ((h + 1) // 2) * cw, exp))
+        # 4-connectivity: a checkerboard's object pixels touch only diagonally, so each is
+        # its own component, numbered in raster order
+        exp = np.zeros((h, w), np.int32)
+        exp[cb != 0] = np.arange(1, int((cb != 0).sum()) + 1)
+        cases.append((f"checker4_{h}x{w}", cb, 4, int((cb != 0).sum()), exp))
+        # the main diagonal: one component under 8-connectivity, min(h, w) under 4
+        dg = np.eye(h, w, dtype=np.uint8)
+        n = min(h, w)
+        cases.append((f"diag_{h}x{w}", dg, 8, 1, dg.astype(np.int32)))
+        exp = np.zeros((h, w), np.int32)
+        exp[np.arange(n), np.arange(n)] = np.arange(1, n + 1)
+        cases.append((f"diag4_{h}x{w}", dg, 4, n, exp))
         sr = synth.striped_rows(h, w)
         exp = np.zeros((h, w), np.int32)
         exp[0::2, :] = (np.arange(0, h, 2) // 2 + 1)[:, None]
         cases.append((f"rows_{h}x{w}", sr, 8, (h + 1) // 2, exp))
+        cases.append((f"rows4_{h}x{w}", sr, 4, (h + 1) // 2, exp))
         sp = synth.serpentine(h, w)
         if w >= 2:
             cases.append((f"serpentine_{h}x{w}", sp, 8, 1, sp.astype(np.int32)))

@@ -397,8 +397,9 @@ template <class C> struct Emu {
 
 extern "C" {
 
-// shapes: 0 = 64x256 tiles (256 threads); 1 = 4x32 (32); 2 = 8x64 (64); 3 = 128x256 (256);
-// 4 = 64x512 (256)
+// shapes, 8-connectivity: 0 = 64x256 tiles (256 threads); 1 = 4x32 (32); 2 = 8x64 (64);
+// 3 = 128x256 (256); 4 = 64x512 (256).  4-connectivity: 5 = 32x256 (256); 6 = 4x32 (32);
+// 7 = 8x64 (64); 8 = 2x32 (32)
 int64_t emu_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t *labels, uint64_t seed,
                   int32_t shape, int32_t *status)
 {
@@ -408,7 +409,11 @@ int64_t emu_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32
     case 1: return Emu<Cfg<4, 32, 32>>(seed).run(img, H, W, pitch, labels, status);
     case 2: return Emu<Cfg<8, 64, 64>>(seed).run(img, H, W, pitch, labels, status);
     case 3: return Emu<Cfg<128, 256, 256>>(seed).run(img, H, W, pitch, labels, status);
-    default: return Emu<Cfg<64, 512, 256>>(seed).run(img, H, W, pitch, labels, status);
+    case 4: return Emu<Cfg<64, 512, 256>>(seed).run(img, H, W, pitch, labels, status);
+    case 5: return Emu<Cfg<32, 256, 256, 4>>(seed).run(img, H, W, pitch, labels, status);
+    case 6: return Emu<Cfg<4, 32, 32, 4>>(seed).run(img, H, W, pitch, labels, status);
+    case 7: return Emu<Cfg<8, 64, 64, 4>>(seed).run(img, H, W, pitch, labels, status);
+    default: return Emu<Cfg<2, 32, 32, 4>>(seed).run(img, H, W, pitch, labels, status);
     }
 }
 
@@ -420,7 +425,9 @@ void emu_label_batch(int32_t n, const uint8_t *const *imgs, const int32_t *H, co
     switch (shape) {
     case 0: Emu<Cfg<64, 256, 256>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
     case 1: Emu<Cfg<4, 32, 32>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
-    default: Emu<Cfg<8, 64, 64>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
+    case 2: Emu<Cfg<8, 64, 64>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
+    case 6: Emu<Cfg<4, 32, 32, 4>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
+    default: Emu<Cfg<8, 64, 64, 4>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
     }
 }
 

@@ -24,38 +24,42 @@ def main(path, n_random):
         for p in (0.2, 0.41, 0.6, 0.8):
             imgs.append(synth.bernoulli(h, w, p, int(p * 1000) + h))
     for i, img in enumerate(imgs):
-        ref, rk = oracle.cclremsp(img)
-        # one- and two-warp tiles for every pattern; the 256-thread tile shapes (one OS
-        # thread per CUDA thread) on every fourth pattern only, to keep the run short
-        shapes = (1, 2, 0, 3, 4) if i % 4 == 0 else (1, 2)
-        for shape in shapes:
-            for seed in range(2 if shape in (1, 2) else 1):
-                pitch = None if seed == 0 else img.shape[1] + 3 + (i % 16)
-                lab, k, st = emu.label(img, seed=i * 7 + seed, shape=shape, pitch=pitch)
-                if not (k == rk and st == 0 and np.array_equal(lab, ref)):
-                    bad += 1
-                    print("mismatch", img.shape, shape, seed, k, rk, st)
+        for conn, small, large in ((8, (1, 2), (0, 3, 4)), (4, (6, 7, 8), (5,))):
+            ref, rk = oracle.cclremsp(img, conn)
+            # small tiles (one or two warps) for every pattern; the 256-thread tile shapes
+            # on every fourth pattern only, to keep the run short
+            shapes = small + large if i % 4 == 0 else small
+            for shape in shapes:
+                for seed in range(2 if shape in small else 1):
+                    pitch = None if seed == 0 else img.shape[1] + 3 + (i % 16)
+                    lab, k, st = emu.label(img, seed=i * 7 + seed, shape=shape, pitch=pitch)
+                    if not (k == rk and st == 0 and np.array_equal(lab, ref)):
+                        bad += 1
+                        print("mismatch", conn, img.shape, shape, seed, k, rk, st)
     rng = np.random.default_rng(5)
     for i in range(n_random):
         h = int(rng.integers(1, 20))
         w = int(rng.integers(1, 140))
         img = (rng.random((h, w)) < rng.uniform(0.15, 0.9)).astype(np.uint8)
-        ref, rk = oracle.cclremsp(img)
-        lab, k, st = emu.label(img, seed=i, shape=1 + (i % 2))
+        conn = 8 if i % 2 == 0 else 4
+        ref, rk = oracle.cclremsp(img, conn)
+        shape = (1, 2)[(i // 2) % 2] if conn == 8 else (6, 7, 8)[(i // 2) % 3]
+        lab, k, st = emu.label(img, seed=i, shape=shape)
         if not (k == rk and st == 0 and np.array_equal(lab, ref)):
             bad += 1
-            print("random mismatch", h, w, k, rk, st)
+            print("random mismatch", conn, shape, h, w, k, rk, st)
     # batches of uneven images (the batched kernels), every image checked on its own
-    for trial in range(6):
+    for trial in range(8):
         k = int(rng.integers(1, 7))
         batch = []
         for _ in range(k):
             h = int(rng.integers(1, 40))
             w = int(rng.integers(1, 150))
             batch.append((rng.random((h, w)) < rng.uniform(0.1, 0.9)).astype(np.uint8))
-        labs, ks, st = emu.label_batch(batch, seed=trial, shape=1 + trial % 2)
+        shape, conn = ((1, 8), (2, 8), (6, 4), (7, 4))[trial % 4]
+        labs, ks, st = emu.label_batch(batch, seed=trial, shape=shape)
         for img, lab, kk in zip(batch, labs, ks):
-            ref, rk = oracle.cclremsp(img)
+            ref, rk = oracle.cclremsp(img, conn)
             if not (kk == rk and st == 0 and np.array_equal(lab, ref)):
                 bad += 1
                 print("batch mismatch", img.shape, kk, rk, st)

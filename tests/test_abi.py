@@ -60,12 +60,16 @@ def test_argument_checks_need_no_gpu(lib):
     assert lib.ccl_label(p, -1, 4, 4, 8, p, ctypes.byref(k), None) == 1
     assert lib.ccl_label(p, 4, 4, 3, 8, p, ctypes.byref(k), None) == 1
     assert lib.ccl_label(None, 4, 4, 4, 8, p, ctypes.byref(k), None) == 1
-    assert lib.ccl_label(p, 4, 4, 4, 4, p, ctypes.byref(k), None) == 2
+    assert lib.ccl_label(p, 4, 4, 3, 4, p, ctypes.byref(k), None) == 1  # 4-connectivity: same checks
     assert lib.ccl_label(p, 4, 4, 4, 5, p, ctypes.byref(k), None) == 1
-    k.value = 7
-    assert lib.ccl_label(p, 0, 9, 9, 8, p, ctypes.byref(k), None) == 0 and k.value == 0
+    assert lib.ccl_label(p, 0, 9, 9, 5, p, ctypes.byref(k), None) == 1  # connectivity checked first
+    for conn in (8, 4):
+        k.value = 7
+        assert lib.ccl_label(p, 0, 9, 9, conn, p, ctypes.byref(k), None) == 0 and k.value == 0
     nb = ctypes.c_int64(0)
     assert lib.ccl_workspace_bytes(8192, 8192, ctypes.byref(nb)) == 0
-    # bit pack 1/8 B/px + run codes 1/2 B/px + parents (row segments) 2 B/px + edge ids
-    # + segment counts
-    assert 2.5 * 8192 * 8192 < nb.value < 3.0 * 8192 * 8192
+    # the larger of the two connectivities' layouts.  8-connectivity: bit pack 1/8 B/px +
+    # run codes 1/2 B/px + parents (row segments) 2 B/px + edge ids + segment counts, under
+    # 3 B/px; 4-connectivity: one-row strips double the run-code slots (1 B/px) and the
+    # 32-row tiles double the row-edge ids
+    assert 3.3 * 8192 * 8192 < nb.value < 3.6 * 8192 * 8192

@@ -25,22 +25,24 @@ SHAPES = [(1, 1), (2, 3), (1, 300), (300, 1), (63, 255), (64, 256), (65, 257), (
           (130, 700), (200, 31), (7, 1000)]
 
 
+@pytest.mark.parametrize("conn", [8, 4])
 @pytest.mark.parametrize("h,w", SHAPES)
-def test_checked_random(dbg, h, w):
+def test_checked_random(dbg, h, w, conn):
     for p in (0.1, 0.45, 0.7, 0.95):
         img = synth.bernoulli(h, w, p, 1000 * h + w + int(100 * p))
-        ref, rk = oracle.cclremsp(img)
-        rc, lab, k, flags = run_label(img, lib=dbg)
+        ref, rk = oracle.cclremsp(img, conn)
+        rc, lab, k, flags = run_label(img, lib=dbg, conn=conn)
         assert rc == 0 and flags == 0, (rc, flags)
         assert k == rk and np.array_equal(lab, ref)
 
 
+@pytest.mark.parametrize("conn", [8, 4])
 @pytest.mark.parametrize("maker", ["serpentine", "checkerboard", "dot_lattice", "striped_rows"])
-def test_checked_patterns(dbg, maker):
+def test_checked_patterns(dbg, maker, conn):
     for h, w in [(64, 256), (129, 511), (200, 300)]:
         img = getattr(synth, maker)(h, w)
-        ref, rk = oracle.cclremsp(img)
-        rc, lab, k, flags = run_label(img, lib=dbg)
+        ref, rk = oracle.cclremsp(img, conn)
+        rc, lab, k, flags = run_label(img, lib=dbg, conn=conn)
         assert rc == 0 and flags == 0
         assert k == rk and np.array_equal(lab, ref)
 
