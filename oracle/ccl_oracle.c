@@ -32,8 +32,8 @@
  *     chunks are an even number of rows, the last chunk takes the remainder; rows above a
  *     chunk are background during its local scan; flatten walks each chunk's used label
  *     range in chunk order with one shared k; the labelling pass is parallel.
- *   - Algorithm 8: the locked root link is a compare-and-swap on p[root]; splices are an
- *     atomic minimum so p[x] never increases.
+ *   - Algorithm 8: the locked root link is a compare-and-swap on p[root]; the unlocked
+ *     splice is a compare-and-swap from the parent value read, retried when it fails.
  *   - Object pixel = any non-zero byte; pixels outside the image are background.
  */
 #include <stdint.h>
@@ -352,16 +352,15 @@ int64_t oracle_aremsp(const uint8_t *img, int64_t h, int64_t w, int64_t pitch, i
 /* ---------------------------------------------------------------------------------- */
 /* Algorithm 8 (merger): Rem's union for concurrent threads.  The paper takes a lock on the
  * root, re-checks that it is still a root and links it; here that is one compare-and-swap
- * of p[root] from root to the other parent.  Splices (the unlocked writes of the paper)
- * only lower p[v], through an atomic minimum. */
+ * of p[root] from root to the other parent.  The paper's splice p[rootx] <- p[rooty] is an
+ * unlocked write; here it too is a compare-and-swap from the parent value this thread read
+ * (a failed one re-reads and retries).  An unconditional splice can overwrite a parent that
+ * another thread has just set, detaching a subtree that no thread then reconnects. */
 static inline lab_t ld(lab_t *p, lab_t i) { return __atomic_load_n(&p[i], __ATOMIC_ACQUIRE); }
 
-static inline void atomic_min_lab(lab_t *addr, lab_t val)
+static inline int cas_lab(lab_t *addr, lab_t expect, lab_t val)
 {
-    lab_t cur = __atomic_load_n(addr, __ATOMIC_ACQUIRE);
-    while (val < cur &&
-           !__atomic_compare_exchange_n(addr, &cur, val, 0, __ATOMIC_ACQ_REL, __ATOMIC_ACQUIRE)) {
-    }
+    return __atomic_compare_exchange_n(addr, &expect, val, 0, __ATOMIC_ACQ_REL, __ATOMIC_ACQUIRE);
 }
 
 static void rem_merger(lab_t *p, lab_t x, lab_t y)
@@ -374,24 +373,16 @@ static void rem_merger(lab_t *p, lab_t x, lab_t y)
         if (px == py)
             return;
         if (px > py) {
-            if (rootx == px) {
-                lab_t expect = rootx;
-                if (__atomic_compare_exchange_n(&p[rootx], &expect, py, 0, __ATOMIC_ACQ_REL,
-                                                __ATOMIC_ACQUIRE))
-                    return;
-                continue; /* no longer a root: carry on from the current position */
-            }
-            atomic_min_lab(&p[rootx], py);
+            if (!cas_lab(&p[rootx], px, py))
+                continue; /* p[rootx] changed since it was read: read again */
+            if (rootx == px)
+                return; /* a root was linked */
             rootx = px;
         } else {
-            if (rooty == py) {
-                lab_t expect = rooty;
-                if (__atomic_compare_exchange_n(&p[rooty], &expect, px, 0, __ATOMIC_ACQ_REL,
-                                                __ATOMIC_ACQUIRE))
-                    return;
+            if (!cas_lab(&p[rooty], py, px))
                 continue;
-            }
-            atomic_min_lab(&p[rooty], px);
+            if (rooty == py)
+                return;
             rooty = py;
         }
     }

@@ -162,17 +162,6 @@ CCL_HD int at_cas(int *a, int cmp, int val)
     return cmp;
 #endif
 }
-CCL_HD void at_min(int *a, int v)
-{
-#if defined(__CUDA_ARCH__)
-    atomicMin(a, v);
-#else
-    emu_yield();
-    int cur = __atomic_load_n(a, __ATOMIC_SEQ_CST);
-    while (v < cur && !__atomic_compare_exchange_n(a, &cur, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {
-    }
-#endif
-}
 CCL_HD void at_or(uint32_t *a, uint32_t v)
 {
 #if defined(__CUDA_ARCH__)
@@ -236,24 +225,31 @@ CCL_HD int ld_s(const int *a)
     return __atomic_load_n(a, __ATOMIC_RELAXED);
 #endif
 }
-// global memory written by other CTAs in the same launch: read through L2, not L1
+// Global memory that other CTAs of the same launch write (union-find parents, CTA sums,
+// round flags).  These are strong relaxed accesses at GPU scope, not weak ones: a weak
+// load of a parent word may return a value older than a link another CTA made before the
+// last grid barrier (observed on GB300 for about 2% of labellings of large near-critical
+// images as a root whose link was then overwritten by its label), whereas a strong load
+// returns the coherent value, and the grid barrier's fences order them.
 CCL_HD int ld_g(const int *a)
 {
 #if defined(__CUDA_ARCH__)
-    return __ldcg(a);
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
 #else
     return __atomic_load_n(a, __ATOMIC_RELAXED);
 #endif
 }
-// four consecutive ints from a 16-byte aligned address, through L2
+// four consecutive ints from a 16-byte aligned address (one strong vector load; each
+// element is read atomically, the four together are not)
 CCL_HD void ld_g4(const int *a, int v[4])
 {
 #if defined(__CUDA_ARCH__)
-    const int4 q = __ldcg(reinterpret_cast<const int4 *>(a));
-    v[0] = q.x;
-    v[1] = q.y;
-    v[2] = q.z;
-    v[3] = q.w;
+    asm volatile("ld.relaxed.gpu.global.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "l"(a)
+                 : "memory");
 #else
     for (int k = 0; k < 4; k++)
         v[k] = __atomic_load_n(a + k, __ATOMIC_RELAXED);
@@ -262,7 +258,7 @@ CCL_HD void ld_g4(const int *a, int v[4])
 CCL_HD void st_g(int *a, int v)
 {
 #if defined(__CUDA_ARCH__)
-    *a = v;
+    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
 #else
     __atomic_store_n(a, v, __ATOMIC_RELAXED);
 #endif
@@ -419,9 +415,13 @@ template <class C> struct SmemF : SmemRuns<C> {
 constexpr uint32_t PAR_HI = 0xFFFF0000u;
 constexpr uint32_t PAR_LO = 0x0000FFFFu;
 
-// Rem's union with splicing (Algorithm 2) made safe for concurrent threads (Algorithm 8):
-// the locked "still a root? then link" step is one compare-and-swap, and a splice
-// p[r] <- p[other] is an atomic minimum so that parents never grow.
+// Rem's union with splicing (Algorithm 2) made safe for concurrent threads (Algorithm 8).
+// Both writes are compare-and-swaps of exactly the parent value this thread read: the
+// locked "still a root? then link" step of Algorithm 8, and also its unlocked splice
+// p[r] <- p[other].  A splice that overwrote a parent it had not read would detach r from
+// a tree that another thread had just attached it to, and no thread would reconnect that
+// tree (a lost union; seen on GB300 and reproduced by an interleaving search).  A failed
+// compare-and-swap re-reads and retries from the same node.
 CCL_HD void rem_unite_s(uint32_t *par, int n, int x, int y, int *st)
 {
     int rx = CCL_CHK(x, n, st), ry = CCL_CHK(y, n, st);
@@ -432,26 +432,25 @@ CCL_HD void rem_unite_s(uint32_t *par, int n, int x, int y, int *st)
         if (px == py)
             return;
         if (px > py) {
-            if ((int)(px & PAR_LO) == rx) {
-                if (at_cas_u(&par[rx], px, py) == px)
-                    return;
+            const bool root = (int)(px & PAR_LO) == rx;
+            if (at_cas_u(&par[rx], px, py) != px)
                 continue;
-            }
-            at_min_u(&par[rx], py);
+            if (root)
+                return;
             rx = CCL_CHK((int)(px & PAR_LO), n, st);
         } else {
-            if ((int)(py & PAR_LO) == ry) {
-                if (at_cas_u(&par[ry], py, px) == py)
-                    return;
+            const bool root = (int)(py & PAR_LO) == ry;
+            if (at_cas_u(&par[ry], py, px) != py)
                 continue;
-            }
-            at_min_u(&par[ry], px);
+            if (root)
+                return;
             ry = CCL_CHK((int)(py & PAR_LO), n, st);
         }
     }
     flag_status(st, ST_LOOP_CAP);
 }
 
+// The same union over the global parent table (ids are raster-ordered node ids).
 CCL_HD void rem_unite_g(int *P, int64_t n, int x, int y, int *st)
 {
     int rx = (int)CCL_CHK((int64_t)x, n, st), ry = (int)CCL_CHK((int64_t)y, n, st);
@@ -462,20 +461,16 @@ CCL_HD void rem_unite_g(int *P, int64_t n, int x, int y, int *st)
         if (px == py)
             return;
         if (px > py) {
-            if (px == rx) {
-                if (at_cas(&P[rx], rx, py) == rx)
-                    return;
+            if (at_cas(&P[rx], px, py) != px)
                 continue;
-            }
-            at_min(&P[rx], py);
+            if (px == rx)
+                return;
             rx = px;
         } else {
-            if (py == ry) {
-                if (at_cas(&P[ry], ry, px) == ry)
-                    return;
+            if (at_cas(&P[ry], py, px) != py)
                 continue;
-            }
-            at_min(&P[ry], px);
+            if (py == ry)
+                return;
             ry = py;
         }
     }

@@ -309,15 +309,17 @@ int32_t ccl_server_wait(ccl_server *s, uint64_t id, int32_t *num_components, int
     auto it = s->reqs.find(id);
     if (it == s->reqs.end())
         return CCL_ERR_INVALID_ARGUMENT;
-    auto ready = [&] { return it->second.done; };
+    // the map may rehash while the lock is released (iterators die, element addresses do not)
+    const Request *r = &it->second;
+    auto ready = [&] { return r->done; };
     if (timeout_ms < 0)
         s->cv_done.wait(lk, ready);
     else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
         return CCL_ERR_TIMEOUT;
-    const int32_t status = it->second.status;
+    const int32_t status = r->status;
     if (num_components)
-        *num_components = it->second.K;
-    s->reqs.erase(it);
+        *num_components = r->K;
+    s->reqs.erase(id);
     return status;
 }
 

@@ -65,3 +65,30 @@ def test_465mb_image(variant):
     _check_full(img, t)
     del t
     torch.cuda.empty_cache()
+
+
+def test_repeated_near_critical_blobs():
+    """Thresholded Gaussian fields at density 0.5 are at the percolation threshold: giant
+    tortuous components cross thousands of tile edges, so many boundary unions run on the
+    same trees at once.  Before splices became compare-and-swaps of the parent read, about
+    1% of these labellings lost a union (K + 1, one component split); 300 repetitions of
+    each image would have shown it with high probability."""
+    import torch
+
+    import paper_1606_05973_gb300 as ccl
+
+    images = [synth.batch_device([{"h": 8192, "w": 8192, "kind": "blobs", "p": 0.5, "sigma": 2.0,
+                                   "seed": 991}], "cuda")[0],
+              synth.blobs_device(8192, 8192, 4.0, 7, "cuda")]
+    for t in images:
+        ref, rk = oracle.cclremsp(t.cpu().numpy())
+        ref = torch.from_numpy(ref).cuda()
+        out = torch.empty_like(ref)
+        bad = 0
+        for _ in range(300):
+            _, k = ccl.label(t, out=out)
+            if k != rk or not torch.equal(out, ref):
+                bad += 1
+        assert bad == 0, bad
+        del ref, out
+        torch.cuda.empty_cache()

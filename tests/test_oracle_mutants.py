@@ -34,8 +34,8 @@ MUTANTS = [
      "if (x + 1 < w && LAB(i - 1, x + 1) != 0 && 0)", 0),
     ("paremsp_first_label_zero", "lab_t count = (lab_t)(start[t] * w + 1);",
      "lab_t count = (lab_t)(start[t] * w);", 0),
-    ("merger_link_no_op", "if (__atomic_compare_exchange_n(&p[rootx], &expect, py,",
-     "if (__atomic_compare_exchange_n(&p[rootx], &expect, px,", 0),
+    ("merger_link_no_op", "if (!cas_lab(&p[rootx], px, py))",
+     "if (!cas_lab(&p[rootx], px, px))", 0),
     ("bfs_lost_direction", "static const int dy8[8] = {-1, -1, -1, 0, 0, 1, 1, 1};",
      "static const int dy8[8] = {-1, -1, -1, 0, 0, 1, 1, 0};", 0),
     ("view_reads_past_row_end", "x >= v->w", "x > v->w", 0),
