@@ -421,36 +421,9 @@ constexpr uint32_t PAR_LO = 0x0000FFFFu;
 // p[r] <- p[other].  A splice that overwrote a parent it had not read would detach r from
 // a tree that another thread had just attached it to, and no thread would reconnect that
 // tree (a lost union; seen on GB300 and reproduced by an interleaving search).  A failed
-// compare-and-swap re-reads and retries from the same node.
-CCL_HD void rem_unite_s(uint32_t *par, int n, int x, int y, int *st)
-{
-    int rx = CCL_CHK(x, n, st), ry = CCL_CHK(y, n, st);
-    (void)n;
-    for (int it = 0; it < SMEM_LOOP_CAP; it++) {
-        const uint32_t px = ld_su(&par[rx]);
-        const uint32_t py = ld_su(&par[ry]);
-        if (px == py)
-            return;
-        if (px > py) {
-            const bool root = (int)(px & PAR_LO) == rx;
-            if (at_cas_u(&par[rx], px, py) != px)
-                continue;
-            if (root)
-                return;
-            rx = CCL_CHK((int)(px & PAR_LO), n, st);
-        } else {
-            const bool root = (int)(py & PAR_LO) == ry;
-            if (at_cas_u(&par[ry], py, px) != py)
-                continue;
-            if (root)
-                return;
-            ry = CCL_CHK((int)(py & PAR_LO), n, st);
-        }
-    }
-    flag_status(st, ST_LOOP_CAP);
-}
-
-// The same union over the global parent table (ids are raster-ordered node ids).
+// compare-and-swap re-reads and retries from the same node.  The tile pass runs the same
+// steps on packed shared-memory words (Tile::unions); this is the global parent table
+// (ids are raster-ordered node ids).
 CCL_HD void rem_unite_g(int *P, int64_t n, int x, int y, int *st)
 {
     int rx = (int)CCL_CHK((int64_t)x, n, st), ry = (int)CCL_CHK((int64_t)y, n, st);
@@ -665,52 +638,89 @@ template <class C> struct Tile {
     // the A run starts one column right of a B pixel.
     CCL_HD static void unions(const Img &a, SL &s, int tid)
     {
-        for (int u = tid; u < C::NS * C::NW; u += C::NT) {
-            const int st = u / C::NW, w = u % C::NW;
-            if (st == 0)
-                continue;
-            // A: last row of strip st-1, B: first row of strip st
-            const int ra = C::RPS * st - 1, rb = C::RPS * st;
-            const uint32_t A = s.bits[ra][w], B = s.bits[rb][w];
-            const uint32_t Ap = (w > 0) ? (s.bits[ra][w - 1] >> 31) : 0u;
-            const uint32_t Bp = (w > 0) ? (s.bits[rb][w - 1] >> 31) : 0u;
-            const uint32_t Ash = (A << 1) | Ap, Bsh = (B << 1) | Bp;
-            const uint32_t sBr = B & ~Bsh, sAr = A & ~Ash;  // single-row run starts
-            // 8: the B run starts where A has a pixel at that column or one to the left, or
-            //    the A run starts one column right of a B pixel
-            // 4: the B run starts under an A pixel, or the A run starts over a B pixel that
-            //    does not start a B run
-            const uint32_t ev1 = (C::CONN == 8) ? (sBr & (A | Ash)) : (sBr & A);
-            const uint32_t ev2 = (C::CONN == 8) ? (sAr & Bsh) : (sAr & B & ~sBr);
-            uint32_t evs = ev1 | ev2;
-            if (!evs)
-                continue;
-            // run of strip s covering bit b of this word (b = -1: the last bit of the word to
-            // the left) is base + popcount(starts & bits 0..b)
-            const uint32_t sA = s.starts[st - 1][w], sB = s.starts[st][w];
-            const int baseA = (st - 1) * C::RC + s.rpre[st - 1][w] - 1;
-            const int baseB = st * C::RC + s.rpre[st][w] - 1;
-            int last_a = -1, last_b = -1;
-            while (evs) {
-                const int b = ctz32(evs);
-                evs &= evs - 1u;
-                if ((ev1 >> b) & 1u) {
-                    const int ba = (C::CONN == 4 || ((A >> b) & 1u)) ? b : b - 1;
-                    const int na = baseA + popc32(sA & mask_upto(ba)), nb = baseB + popc32(sB & mask_upto(b));
+        // every thread runs the same number of outer passes (NT is a multiple of 32), so
+        // whole warps reach the votes below
+        for (int u0 = 0; u0 < C::NS * C::NW; u0 += C::NT) {
+            const int u = u0 + tid, st = u / C::NW, w = u % C::NW;
+            uint32_t ev1 = 0, ev2 = 0, A = 0, sA = 0, sB = 0;
+            int baseA = 0, baseB = 0;
+            if (u < C::NS * C::NW && st > 0) {
+                // A: last row of strip st-1, B: first row of strip st
+                const int ra = C::RPS * st - 1, rb = C::RPS * st;
+                A = s.bits[ra][w];
+                const uint32_t B = s.bits[rb][w];
+                const uint32_t Ap = (w > 0) ? (s.bits[ra][w - 1] >> 31) : 0u;
+                const uint32_t Bp = (w > 0) ? (s.bits[rb][w - 1] >> 31) : 0u;
+                const uint32_t Ash = (A << 1) | Ap, Bsh = (B << 1) | Bp;
+                const uint32_t sBr = B & ~Bsh, sAr = A & ~Ash;  // single-row run starts
+                // 8: the B run starts where A has a pixel at that column or one to the left,
+                //    or the A run starts one column right of a B pixel
+                // 4: the B run starts under an A pixel, or the A run starts over a B pixel
+                //    that does not start a B run
+                ev1 = (C::CONN == 8) ? (sBr & (A | Ash)) : (sBr & A);
+                ev2 = (C::CONN == 8) ? (sAr & Bsh) : (sAr & B & ~sBr);
+                // run of strip s covering bit b of this word (b = -1: the last bit of the
+                // word to the left) is base + popcount(starts & bits 0..b)
+                sA = s.starts[st - 1][w];
+                sB = s.starts[st][w];
+                baseA = (st - 1) * C::RC + s.rpre[st - 1][w] - 1;
+                baseB = st * C::RC + s.rpre[st][w] - 1;
+            }
+            // One loop for all of this thread's joins, run in step by the whole warp: each
+            // pass takes the thread's next event if it has no join in progress, then runs
+            // one step of Rem's union (Algorithm 2 with Algorithm 8's compare-and-swap
+            // writes, as in rem_unite_g).  A warp vote ends the loop, so the lanes stay
+            // converged and each pass is one short predicated block per part.
+            int last_a = -1, last_b = -1, rx = -1, ry = -1;
+            for (int it = 0;; it++) {
+                if (rx < 0 && (ev1 | ev2)) {
+                    const int b = ctz32(ev1 | ev2);
+                    int na, nb, x, y;
+                    if ((ev1 >> b) & 1u) {
+                        ev1 &= ev1 - 1u;
+                        const int ba = (C::CONN == 4 || ((A >> b) & 1u)) ? b : b - 1;
+                        na = baseA + popc32(sA & mask_upto(ba));
+                        nb = baseB + popc32(sB & mask_upto(b));
+                        x = nb;
+                        y = na;
+                    } else {
+                        ev2 &= ev2 - 1u;
+                        const int bb = (C::CONN == 4) ? b : b - 1;
+                        na = baseA + popc32(sA & mask_upto(b));
+                        nb = baseB + popc32(sB & mask_upto(bb));
+                        x = na;
+                        y = nb;
+                    }
                     if (na != last_a || nb != last_b) {
-                        rem_unite_s(s.par, C::RMAX, nb, na, a.status);
                         last_a = na;
                         last_b = nb;
+                        rx = CCL_CHK(x, C::RMAX, a.status);
+                        ry = CCL_CHK(y, C::RMAX, a.status);
                     }
                 }
-                if ((ev2 >> b) & 1u) {
-                    const int bb = (C::CONN == 4) ? b : b - 1;
-                    const int na = baseA + popc32(sA & mask_upto(b)), nb = baseB + popc32(sB & mask_upto(bb));
-                    if (na != last_a || nb != last_b) {
-                        rem_unite_s(s.par, C::RMAX, na, nb, a.status);
-                        last_a = na;
-                        last_b = nb;
-                    }
+                if (!warp_ballot(rx >= 0 || (ev1 | ev2) != 0u))
+                    break;
+                if (it == SMEM_LOOP_CAP) {
+                    flag_status(a.status, ST_LOOP_CAP);
+                    break;
+                }
+                if (rx >= 0) {
+                    const uint32_t px = ld_su(&s.par[rx]);
+                    const uint32_t py = ld_su(&s.par[ry]);
+                    const bool xs = px > py;  // write the larger parent's entry
+                    const int r = xs ? rx : ry;
+                    const uint32_t pr = xs ? px : py, po = xs ? py : px;
+                    if (px == py) {
+                        rx = -1;  // same parent: already joined
+                    } else if (at_cas_u(&s.par[r], pr, po) == pr) {
+                        const int up = CCL_CHK((int)(pr & PAR_LO), C::RMAX, a.status);
+                        if (up == r)
+                            rx = -1;  // a root was linked: this join is done
+                        else if (xs)
+                            rx = up;
+                        else
+                            ry = up;
+                    }  // else: changed since read, read again in the next pass
                 }
             }
         }

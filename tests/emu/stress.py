@@ -13,11 +13,12 @@ import synth  # noqa: E402
 from emu.emu import Emu  # noqa: E402
 
 
-def main(path, n_random):
+def main(path, n_random, sizes=None):
     emu = Emu(path)
     bad = 0
     imgs = []
-    for h, w in [(8, 64), (9, 65), (7, 63), (16, 128), (33, 97), (66, 300), (129, 257)]:
+    all_sizes = [(8, 64), (9, 65), (7, 63), (16, 128), (33, 97), (66, 300), (129, 257)]
+    for h, w in (all_sizes if sizes is None else all_sizes[:sizes]):
         imgs += [synth.serpentine(h, w), synth.checkerboard(h, w), synth.dot_lattice(h, w),
                  synth.striped_rows(h, w), synth.blobs(h, w, 2.0, h + w), np.ones((h, w), np.uint8),
                  np.ascontiguousarray(synth.serpentine(w, h).T)]
@@ -27,8 +28,8 @@ def main(path, n_random):
         for conn, small, large in ((8, (1, 2), (0, 3, 4)), (4, (6, 7, 8), (5,))):
             ref, rk = oracle.cclremsp(img, conn)
             # small tiles (one or two warps) for every pattern; the 256-thread tile shapes
-            # on every fourth pattern only, to keep the run short
-            shapes = small + large if i % 4 == 0 else small
+            # on every sixth pattern only, to keep the run short
+            shapes = small + large if i % 6 == 0 else small
             for shape in shapes:
                 for seed in range(2 if shape in small else 1):
                     pitch = None if seed == 0 else img.shape[1] + 3 + (i % 16)
@@ -72,4 +73,5 @@ def main(path, n_random):
 
 
 if __name__ == "__main__":
-    sys.exit(1 if main(sys.argv[1], int(sys.argv[2])) else 0)
+    sizes = int(sys.argv[3]) if len(sys.argv) > 3 else None
+    sys.exit(1 if main(sys.argv[1], int(sys.argv[2]), sizes) else 0)

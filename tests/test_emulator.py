@@ -16,19 +16,31 @@ import pytest
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def test_emulated_path_matches_oracle_under_sanitizers():
+def _stress(sanitize, n_random, sizes=None):
     sys.path.insert(0, HERE)
     from emu import emu
 
-    rt = emu.asan_runtime()
+    rt = emu.asan_runtime() if sanitize else None
     so = emu.build(sanitize=rt is not None)
     env = dict(os.environ)
     if rt:
         env["LD_PRELOAD"] = rt
         env["ASAN_OPTIONS"] = "detect_leaks=0"
-    r = subprocess.run([sys.executable, os.path.join(HERE, "emu", "stress.py"), so, "400"],
-                       capture_output=True, text=True, env=env, timeout=600)
+    args = [sys.executable, os.path.join(HERE, "emu", "stress.py"), so, str(n_random)]
+    if sizes is not None:
+        args.append(str(sizes))
+    r = subprocess.run(args, capture_output=True, text=True, env=env, timeout=600)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
+
+
+def test_emulated_path_matches_oracle():
+    """Every pattern size, 400 random images and the batches, without the sanitizer."""
+    _stress(False, 400)
+
+
+def test_emulated_path_matches_oracle_under_sanitizers():
+    """The same checks on the smaller sizes with AddressSanitizer preloaded."""
+    _stress(True, 120, sizes=5)
 
 
 def test_emulated_path_tile_variants_quick():

@@ -1,5 +1,5 @@
 """Interleaving check of the concurrent Rem union (Algorithm 2 with Algorithm 8's
-concurrency), step for step as the GPU kernels (rem_unite_g, rem_unite_s) and the
+concurrency), step for step as the GPU kernels (rem_unite_g and the tile pass) and the
 oracle's PARemSP merger run it: two loads of the parents, then one compare-and-swap that
 either links a root or splices a non-root, each from exactly the value read; a failed
 compare-and-swap re-reads.  Every interleaving of single memory accesses of a few
