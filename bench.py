@@ -357,7 +357,53 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
     if args.served:
         line["served"] = measure_served(args, dev)
+    if args.fused:
+        line["fused_binarisation"] = measure_fused(args, dev, lib, stream)
+        torch.cuda.empty_cache()
     return line
+
+
+def measure_fused(args, dev, lib, stream):
+    """Fused binarisation: an 8192x8192 8-bit grayscale field (sigma 4, seed 12) labelled
+    as byte > 127 (Section V's im2bw(0.5)) by ccl_label_threshold in one pass, against a
+    separate binarisation pass (torch) followed by ccl_label.  Inputs resident in HBM;
+    CUDA-event timing over 20 repetitions after 3 warm-ups."""
+    import torch
+
+    g = synth.gray_field_device(8192, 8192, 4.0, 12, dev)
+    H, W = g.shape
+    lab = torch.empty((H, W), dtype=torch.int32, device=dev)
+    binary = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    kd = torch.zeros(1, dtype=torch.int32, device=dev)
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+
+    def fused():
+        rc = lib.ccl_label_threshold(g.data_ptr(), H, W, g.stride(0), args.connectivity, 127, lab.data_ptr(),
+                                     None, sptr)
+        if rc != 0:
+            raise RuntimeError("ccl_label_threshold failed")
+
+    def two_pass():
+        torch.gt(g, 127, out=binary)
+        rc = lib.ccl_label_async(binary.data_ptr(), H, W, W, args.connectivity, lab.data_ptr(), kd.data_ptr(), sptr)
+        if rc != 0:
+            raise RuntimeError("ccl_label_async failed")
+
+    res = {"workload": "8192x8192 uint8 grayscale field (sigma 4, seed 12), object = byte > 127"}
+    for name, fn in (("fused", fused), ("binarise_then_label", two_pass)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        res[name] = {"ms": round(ms, 4), "gpx_s": round(H * W / (ms * 1e-3) / 1e9, 2)}
+    res["speedup"] = round(res["binarise_then_label"]["ms"] / res["fused"]["ms"], 3)
+    return res
 
 
 def measure_served(args, dev):
@@ -608,6 +654,7 @@ def main():
     ap.add_argument("--batch-images", type=int, default=4096,
                     help="size of the uneven-batch comparison (0 skips it)")
     ap.add_argument("--no-served", dest="served", action="store_false", help="skip the serving measurement")
+    ap.add_argument("--no-fused", dest="fused", action="store_false", help="skip the fused-binarisation measurement")
     ap.add_argument("--cpu-budget-s", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -87,6 +87,21 @@ int32_t ccl_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes,
                   ccl_stream_t stream);
 
 /*
+ * ccl_label_threshold - label the binarisation of an 8-bit grayscale image in the same
+ * pass: a pixel is an object pixel when its byte is greater than `threshold`.
+ *
+ * The paper binarises its land-cover rasters with im2bw(0.5) before labelling (Section V);
+ * on 8-bit data that is byte > 127.5, i.e. threshold = 127 here.  Fusing the test into the
+ * load removes the separate binarisation pass and its bytes.
+ *
+ *   threshold      0..255 (else CCL_ERR_INVALID_ARGUMENT); 0 is exactly ccl_label
+ *   other arguments, return values and numbering as ccl_label
+ */
+int32_t ccl_label_threshold(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes,
+                            int32_t connectivity, int32_t threshold, int32_t *labels,
+                            int32_t *num_components, ccl_stream_t stream);
+
+/*
  * ccl_label_async - as ccl_label, fully asynchronous: K is written to the DEVICE int32
  * num_components_dev (may be NULL).  Safe to capture in a CUDA graph once the stream's
  * workspace is large enough (make one uncaptured call of the same or larger size first).
@@ -124,6 +139,11 @@ typedef struct {
  */
 int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity,
                         int32_t *num_components_dev, ccl_stream_t stream);
+
+/* ccl_label_batch with object = byte > threshold for every image (see ccl_label_threshold). */
+int32_t ccl_label_batch_threshold(const ccl_image *imgs, int32_t n, int32_t connectivity,
+                                  int32_t threshold, int32_t *num_components_dev,
+                                  ccl_stream_t stream);
 
 /*
  * ccl_label_static - as ccl_label_async, but it allocates nothing.  The paper has no

@@ -123,6 +123,12 @@ def default() -> Oracle:
     return Oracle(_get())
 
 
+def binarize(img, threshold: int) -> np.ndarray:
+    """Fused binarisation's input, written out: object = byte > threshold (Section V
+    binarises with im2bw(0.5), i.e. byte > 127.5 on 8-bit data: threshold 127)."""
+    return (np.asarray(img, dtype=np.uint8) > int(threshold)).astype(np.uint8)
+
+
 def cclremsp(img, conn: int = 8):
     """CCLRemSP (Algorithm 1): canonical labels of ``img`` under ``conn``-connectivity."""
     return default().cclremsp(img, conn)

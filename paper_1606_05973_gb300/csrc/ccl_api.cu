@@ -113,8 +113,8 @@ int32_t check_args(const void *img, int32_t H, int32_t W, int64_t pitch, int32_t
 
 // Enqueue the path for one image whose K goes to k_dev (device) and whose status bits go
 // to the workspace header.  `layout_base` is the workspace area for the per-image arrays.
-int32_t enqueue_one(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t conn, int32_t *labels,
-                    int32_t *k_dev, Workspace *w, char *layout_base, cudaStream_t s)
+int32_t enqueue_one(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t conn, int32_t thr,
+                    int32_t *labels, int32_t *k_dev, Workspace *w, char *layout_base, cudaStream_t s)
 {
     cudaError_t e = kernels_init();
     if (e != cudaSuccess)
@@ -126,6 +126,7 @@ int32_t enqueue_one(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int
     a.pitch = pitch;
     a.H = H;
     a.W = W;
+    a.thr = thr;
     a.vec_in = ((reinterpret_cast<uintptr_t>(img) & 15) == 0) && (pitch % 16 == 0);
     a.labels = labels;
     a.vec_out = ((reinterpret_cast<uintptr_t>(labels) & 15) == 0) && (W % 4 == 0);
@@ -235,14 +236,18 @@ int32_t ccl_label_async(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_
     if (rc != CCL_OK)
         return rc;
     int32_t *k_dev = num_components_dev ? num_components_dev : static_cast<int32_t *>(w->dev);
-    return enqueue_one(img, H, W, pitch_bytes, connectivity, labels, k_dev, w, static_cast<char *>(w->dev) + HDR,
-                       s);
+    return enqueue_one(img, H, W, pitch_bytes, connectivity, 0, labels, k_dev, w,
+                       static_cast<char *>(w->dev) + HDR, s);
 }
 
-int32_t ccl_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes, int32_t connectivity,
-                  int32_t *labels, int32_t *num_components, ccl_stream_t stream)
+namespace {
+
+int32_t label_sync(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes, int32_t connectivity,
+                   int32_t thr, int32_t *labels, int32_t *num_components, ccl_stream_t stream)
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (thr < 0 || thr > 255)
+        return CCL_ERR_INVALID_ARGUMENT;
     int32_t rc = check_args(img, H, W, pitch_bytes, connectivity, labels);
     if (rc != CCL_OK)
         return rc;
@@ -256,10 +261,25 @@ int32_t ccl_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes,
     if (rc != CCL_OK)
         return rc;
     int32_t *k_dev = static_cast<int32_t *>(w->dev);
-    rc = enqueue_one(img, H, W, pitch_bytes, connectivity, labels, k_dev, w, static_cast<char *>(w->dev) + HDR, s);
+    rc = enqueue_one(img, H, W, pitch_bytes, connectivity, thr, labels, k_dev, w, static_cast<char *>(w->dev) + HDR,
+                     s);
     if (rc != CCL_OK || !num_components)
         return rc;
     return read_k_and_status(w, k_dev, num_components, s);
+}
+
+}  // namespace
+
+int32_t ccl_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes, int32_t connectivity,
+                  int32_t *labels, int32_t *num_components, ccl_stream_t stream)
+{
+    return label_sync(img, H, W, pitch_bytes, connectivity, 0, labels, num_components, stream);
+}
+
+int32_t ccl_label_threshold(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes, int32_t connectivity,
+                            int32_t threshold, int32_t *labels, int32_t *num_components, ccl_stream_t stream)
+{
+    return label_sync(img, H, W, pitch_bytes, connectivity, threshold, labels, num_components, stream);
 }
 
 int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch_bytes,
@@ -291,7 +311,7 @@ int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pi
     if (e != cudaSuccess)
         return map_cuda(e);
     int32_t *k_dev = reinterpret_cast<int32_t *>(base);
-    rc = enqueue_one(d_img, H, W, dpitch, connectivity, d_lab, k_dev, w, base + HDR, s);
+    rc = enqueue_one(d_img, H, W, dpitch, connectivity, 0, d_lab, k_dev, w, base + HDR, s);
     if (rc != CCL_OK)
         return rc;
     e = cudaMemcpyAsync(labels_host, d_lab, (size_t)H * W * 4, cudaMemcpyDeviceToHost, s);
@@ -322,8 +342,8 @@ int64_t batch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int c
 // Enqueue the batched path for images imgs[keep[0..m)] (all checked, non-empty) on `s`
 // using workspace `w` (at least batch_bytes large).  K of image keep[k] goes to
 // k_dev[keep[k]] when k_dev is not NULL.
-int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int32_t *k_dev, Workspace *w,
-                      cudaStream_t s)
+int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
+                      Workspace *w, cudaStream_t s)
 {
     cudaError_t e = kernels_init();
     if (e != cudaSuccess)
@@ -387,6 +407,7 @@ int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int
         a.pitch = im.pitch_bytes;
         a.H = im.H;
         a.W = im.W;
+        a.thr = thr;
         a.vec_in = ((reinterpret_cast<uintptr_t>(im.img) & 15) == 0) && (im.pitch_bytes % 16 == 0);
         a.labels = im.labels;
         a.vec_out = ((reinterpret_cast<uintptr_t>(im.labels) & 15) == 0) && (im.W % 4 == 0);
@@ -426,11 +447,13 @@ int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int
 
 extern "C" {
 
-int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, int32_t *num_components_dev,
-                        ccl_stream_t stream)
+namespace {
+
+int32_t label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, int32_t thr, int32_t *num_components_dev,
+                    ccl_stream_t stream)
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (n < 0 || (n > 0 && !imgs))
+    if (n < 0 || (n > 0 && !imgs) || thr < 0 || thr > 255)
         return CCL_ERR_INVALID_ARGUMENT;
     std::vector<int32_t> keep;
     keep.reserve(n);
@@ -460,7 +483,21 @@ int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, 
     int32_t rc = get_workspace(s, batch_bytes(imgs, keep.data(), m, connectivity), &w);
     if (rc != CCL_OK)
         return rc;
-    return enqueue_batch(imgs, keep.data(), m, connectivity, num_components_dev, w, s);
+    return enqueue_batch(imgs, keep.data(), m, connectivity, thr, num_components_dev, w, s);
+}
+
+}  // namespace
+
+int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, int32_t *num_components_dev,
+                        ccl_stream_t stream)
+{
+    return label_batch(imgs, n, connectivity, 0, num_components_dev, stream);
+}
+
+int32_t ccl_label_batch_threshold(const ccl_image *imgs, int32_t n, int32_t connectivity, int32_t threshold,
+                                  int32_t *num_components_dev, ccl_stream_t stream)
+{
+    return label_batch(imgs, n, connectivity, threshold, num_components_dev, stream);
 }
 
 int32_t ccl_device_status(ccl_stream_t stream, int32_t *flags)

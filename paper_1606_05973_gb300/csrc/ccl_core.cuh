@@ -278,15 +278,19 @@ template <class I> CCL_HD I chk(I i, I n, int *st)
 #define CCL_CHK(i, n, st) (i)
 #endif
 
-// 16 bytes -> 16 object bits (bit i = byte i != 0)
-CCL_HD uint32_t nz_nibble(uint32_t v)
+// 4 bytes -> 4 object bits, bit i = (byte i > T), with c = (255 - T) in every byte.
+// x > T exactly when x + (255 - T) carries out of the byte; that carry is the majority of
+// bit 7 of x, bit 7 of c and the carry into bit 7, computed without crossing bytes.  With
+// T = 0 (c = 0xFF) this is the non-zero test.
+CCL_HD uint32_t gt_nibble(uint32_t v, uint32_t c)
 {
-    // bit 7 of each byte is set iff the byte is non-zero (no carry leaves a byte)
-    const uint32_t m = (((v & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | v) & 0x80808080u;
+    const uint32_t t = (v & 0x7F7F7F7Fu) + (c & 0x7F7F7F7Fu);  // bit 7: carry into bit 7
+    const uint32_t m = ((v & c) | ((v | c) & t)) & 0x80808080u;
     // gather bits 0, 8, 16, 24 of (m >> 7) into bits 28..31 (cross terms land elsewhere)
     return ((m >> 7) * 0x10204080u) >> 28;
 }
-CCL_HD uint32_t nz_mask16(const uint8_t *src)
+// 16 bytes -> 16 object bits (bit i = byte i > T), c as in gt_nibble
+CCL_HD uint32_t gt_mask16(const uint8_t *src, uint32_t c)
 {
     uint32_t v[4];
 #if defined(__CUDA_ARCH__)
@@ -298,7 +302,7 @@ CCL_HD uint32_t nz_mask16(const uint8_t *src)
 #else
     memcpy(v, src, 16);
 #endif
-    return nz_nibble(v[0]) | (nz_nibble(v[1]) << 4) | (nz_nibble(v[2]) << 8) | (nz_nibble(v[3]) << 12);
+    return gt_nibble(v[0], c) | (gt_nibble(v[1], c) << 4) | (gt_nibble(v[2], c) << 8) | (gt_nibble(v[3], c) << 12);
 }
 CCL_HD void store4(int *dst, const int v[4])
 {
@@ -333,9 +337,10 @@ template <int TH_, int TW_, int NT_, int CONN_ = 8> struct Cfg {
 
 // Per-image device arguments.  All workspace arrays are owned by the caller of the kernels.
 struct Img {
-    const uint8_t *img;  // H rows of `pitch` bytes; object = non-zero byte
+    const uint8_t *img;  // H rows of `pitch` bytes; object = byte > thr
     int64_t pitch;
     int H, W;
+    int thr;             // 0..255; 0 makes every non-zero byte an object pixel
     int vec_in;          // img 16-byte aligned and pitch % 16 == 0
     int nTX, nTY;        // tiles across / down
     uint32_t *bitpack;   // [H][nTX*NW] object bits, bit b of word w = column 32w+b
@@ -487,6 +492,7 @@ template <class C> struct Tile {
         uint16_t *half = reinterpret_cast<uint16_t *>(&s.bits[0][0]);
         constexpr int PER = (C::TH * C::CH + C::NT - 1) / C::NT;
         const bool full = a.vec_in && (y0 + C::TH <= a.H) && (x0 + C::TW <= a.W);
+        const uint32_t c = (uint32_t)(255 - a.thr) * 0x01010101u;  // object = byte > thr
         if (full) {
             // interior tile: issue every 16-byte load before using any of them
             uint32_t m[PER];
@@ -495,8 +501,8 @@ template <class C> struct Tile {
                 const int q = tid + i * C::NT;
                 m[i] = 0;
                 if (q < C::TH * C::CH) {
-                    const int r = q / C::CH, c = q % C::CH;
-                    m[i] = nz_mask16(a.img + (int64_t)(y0 + r) * a.pitch + x0 + 16 * c);
+                    const int r = q / C::CH, cc = q % C::CH;
+                    m[i] = gt_mask16(a.img + (int64_t)(y0 + r) * a.pitch + x0 + 16 * cc, c);
                 }
             }
 #pragma unroll
@@ -507,17 +513,17 @@ template <class C> struct Tile {
             }
         } else {
             for (int q = tid; q < C::TH * C::CH; q += C::NT) {
-                const int r = q / C::CH, c = q % C::CH;
-                const int y = y0 + r, x = x0 + 16 * c;
+                const int r = q / C::CH, cc = q % C::CH;
+                const int y = y0 + r, x = x0 + 16 * cc;
                 uint32_t m = 0;
                 if (y < a.H && x < a.W) {
                     const uint8_t *src = a.img + (int64_t)y * a.pitch + x;
                     if (a.vec_in && x + 16 <= a.W) {
-                        m = nz_mask16(src);
+                        m = gt_mask16(src, c);
                     } else {
                         const int n = imin(16, a.W - x);
                         for (int i = 0; i < n; i++)
-                            m |= (src[i] != 0 ? 1u : 0u) << i;
+                            m |= ((int)src[i] > a.thr ? 1u : 0u) << i;
                     }
                 }
                 half[q] = (uint16_t)m;  // little-endian: half 2w is the low half of word w

@@ -137,7 +137,7 @@ bool try_launch_locked(ccl_server *s, Lane &L)
     if (m == 0)
         return false;
     L.bytes = batch_bytes(L.imgs.data(), L.keep.data(), m, s->cfg.connectivity);
-    int32_t rc = enqueue_batch(L.imgs.data(), L.keep.data(), m, s->cfg.connectivity, L.k_dev, &L.ws, L.stream);
+    int32_t rc = enqueue_batch(L.imgs.data(), L.keep.data(), m, s->cfg.connectivity, 0, L.k_dev, &L.ws, L.stream);
     cudaError_t e = cudaSuccess;
     if (rc == CCL_OK) {
         // K values and the status word back to the host, then clear the status word

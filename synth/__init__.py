@@ -168,6 +168,30 @@ def blobs_device(h: int, w: int, sigma: float, seed: int, device):
     return (noise > 0).to(torch.uint8)
 
 
+def gray_field_device(h: int, w: int, sigma: float, seed: int, device):
+    """8-bit grayscale stand-in for the paper's land-cover rasters before binarisation: the
+    smoothed field of ``blobs_device`` scaled to unit variance and quantised as
+    clip(round(128 + 40 z), 0, 255).  Thresholding at 127 keeps z > -0.0125, about half the
+    pixels, near the percolation point of the field."""
+    import torch
+
+    rng = _rng(seed)
+    noise = torch.from_numpy(rng.standard_normal((h, w), dtype=np.float32)).to(device)
+    k = _gauss_kernel(sigma)
+    r = (k.size - 1) // 2
+    for axis in (0, 1):
+        n = noise.shape[axis]
+        kk = np.zeros(n, dtype=np.float32)
+        for i, v in enumerate(k):
+            kk[(i - r) % n] += v
+        fk = torch.fft.rfft(torch.from_numpy(kk).to(device))
+        shape = [1, 1]
+        shape[axis] = fk.numel()
+        noise = torch.fft.irfft(torch.fft.rfft(noise, dim=axis) * fk.reshape(shape), n=n, dim=axis)
+    z = noise / noise.std()
+    return torch.clamp(torch.round(128.0 + 40.0 * z), 0, 255).to(torch.uint8)
+
+
 def serpentine(h: int, w: int) -> np.ndarray:
     """One 1-px-wide path covering the image: even rows full; odd row y holds a single
     pixel at x = W-1 when y % 4 == 1 and at x = 0 when y % 4 == 3.  One component

@@ -234,6 +234,8 @@ int emu_shfl_up(int v, int delta, int width)
 
 namespace {
 
+int g_emu_thr = 0;  // object = byte > g_emu_thr
+
 template <class C> struct Emu {
     uint64_t seed;
     std::mt19937_64 rng;
@@ -291,6 +293,7 @@ template <class C> struct Emu {
             a.pitch = pitches[i];
             a.H = Hs[i];
             a.W = Ws[i];
+            a.thr = g_emu_thr;
             a.vec_in = ((uintptr_t)imgs[i] % 16 == 0) && (pitches[i] % 16 == 0);
             a.labels = labels[i];
             a.vec_out = ((uintptr_t)labels[i] % 16 == 0) && (Ws[i] % 4 == 0);
@@ -362,6 +365,7 @@ template <class C> struct Emu {
         a.pitch = pitch;
         a.H = H;
         a.W = W;
+        a.thr = g_emu_thr;
         a.vec_in = ((uintptr_t)img % 16 == 0) && (pitch % 16 == 0);
         a.labels = labels;
         a.vec_out = ((uintptr_t)labels % 16 == 0) && (W % 4 == 0);
@@ -396,6 +400,15 @@ template <class C> struct Emu {
 }  // namespace
 
 extern "C" {
+
+// threshold of the object test (object = byte > thr) for the following emu_label calls
+void emu_set_threshold(int32_t thr) { g_emu_thr = thr; }
+
+// the 16-byte object test of the load phase, for an exhaustive check of its arithmetic
+uint32_t emu_gt_mask16(const uint8_t *src, int32_t thr)
+{
+    return ccl::gt_mask16(src, (uint32_t)(255 - thr) * 0x01010101u);
+}
 
 // shapes, 8-connectivity: 0 = 64x256 tiles (256 threads); 1 = 4x32 (32); 2 = 8x64 (64);
 // 3 = 128x256 (256); 4 = 64x512 (256).  4-connectivity: 5 = 32x256 (256); 6 = 4x32 (32);

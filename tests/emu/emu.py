@@ -51,9 +51,21 @@ class Emu:
         fb.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p]
         fb.restype = None
+        self.lib.emu_set_threshold.argtypes = [ctypes.c_int32]
+        self.lib.emu_gt_mask16.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+        self.lib.emu_gt_mask16.restype = ctypes.c_uint32
 
-    def label(self, img: np.ndarray, seed: int = 1, shape: int = 0, pitch: int | None = None, fill: int = 7):
+    def gt_mask16(self, src16: np.ndarray, threshold: int) -> int:
+        """The load phase's test of 16 bytes: bit i set when byte i > threshold."""
+        src16 = np.ascontiguousarray(src16, dtype=np.uint8)
+        assert src16.size == 16
+        return int(self.lib.emu_gt_mask16(src16.ctypes.data, int(threshold)))
+
+    def label(self, img: np.ndarray, seed: int = 1, shape: int = 0, pitch: int | None = None, fill: int = 7,
+              threshold: int = 0):
         import synth
+
+        self.lib.emu_set_threshold(int(threshold))
 
         h, w = img.shape
         if pitch is None:

@@ -66,6 +66,9 @@ def test_argument_checks_need_no_gpu(lib):
     for conn in (8, 4):
         k.value = 7
         assert lib.ccl_label(p, 0, 9, 9, conn, p, ctypes.byref(k), None) == 0 and k.value == 0
+    for t in (-1, 256):  # threshold outside a byte's range
+        assert lib.ccl_label_threshold(p, 4, 4, 4, 8, t, p, ctypes.byref(k), None) == 1
+    assert lib.ccl_label_threshold(p, 0, 9, 9, 8, 127, p, ctypes.byref(k), None) == 0 and k.value == 0
     nb = ctypes.c_int64(0)
     assert lib.ccl_workspace_bytes(8192, 8192, ctypes.byref(nb)) == 0
     # the larger of the two connectivities' layouts.  8-connectivity: bit pack 1/8 B/px +

@@ -57,3 +57,47 @@ def test_emulated_path_tile_variants_quick():
     for shape in (0, 1, 2):
         lab, k, st = e.label(img, seed=shape, shape=shape)
         assert st == 0 and k == rk and np.array_equal(lab, ref)
+
+
+def test_object_test_of_the_load_phase_is_byte_greater_than_threshold():
+    """The load phase turns 16 bytes into 16 object bits with word arithmetic (the carry of
+    byte + (255 - T) out of its byte).  Checked against byte > T for every byte value and
+    every threshold, each byte in every one of the 16 positions."""
+    sys.path.insert(0, HERE)
+    import numpy as np
+
+    from emu import emu
+
+    e = emu.Emu(emu.build(sanitize=False))
+    vals = np.arange(256, dtype=np.uint8)
+    for t in range(256):
+        for k in range(16):
+            block = np.roll(vals.reshape(16, 16), k, axis=1)  # every value in every position
+            for row in block:
+                got = e.gt_mask16(row, t)
+                exp = int(sum(1 << i for i in range(16) if int(row[i]) > t))
+                assert got == exp, (t, row.tolist(), hex(got), hex(exp))
+
+
+def test_emulated_threshold_labelling_matches_oracle():
+    sys.path.insert(0, HERE)
+    import numpy as np
+
+    import oracle
+    from emu import emu
+
+    e = emu.Emu(emu.build(sanitize=False))
+    rng = np.random.default_rng(3)
+    for h, w in [(9, 65), (33, 97), (66, 300)]:
+        img = rng.integers(0, 256, size=(h, w), dtype=np.uint8)
+        for t in (0, 1, 100, 127, 200, 255):
+            ref, rk = oracle.cclremsp(oracle.binarize(img, t))
+            for shape in (1, 2, 0, 6):
+                conn = 4 if shape == 6 else 8
+                if conn == 4:
+                    ref4, rk4 = oracle.cclremsp(oracle.binarize(img, t), 4)
+                # a pitch of whole 16-byte chunks takes the vector loads, w + 3 the byte loop
+                pitch = ((w + 15) // 16) * 16 + 16 if t % 2 == 0 else w + 3
+                lab, k, st = e.label(img, seed=t, shape=shape, threshold=t, pitch=pitch)
+                exp, ek = (ref4, rk4) if conn == 4 else (ref, rk)
+                assert st == 0 and k == ek and np.array_equal(lab, exp), (h, w, t, shape)
