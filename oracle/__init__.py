@@ -48,9 +48,10 @@ def load(path: str) -> ctypes.CDLL:
     lib.oracle_aremsp.argtypes = [p, i64, i64, i64, p, i32]
     lib.oracle_paremsp.argtypes = [p, i64, i64, i64, p, i32, i32]
     lib.oracle_bfs.argtypes = [p, i64, i64, i64, i32, p]
+    lib.oracle_bfs_classes.argtypes = [p, i64, i64, i64, i32, p]
     lib.oracle_canonicalize.argtypes = [p, i64, i64]
     for f in (lib.oracle_cclremsp, lib.oracle_aremsp, lib.oracle_paremsp, lib.oracle_bfs,
-              lib.oracle_canonicalize):
+              lib.oracle_bfs_classes, lib.oracle_canonicalize):
         f.restype = i64
     lib.oracle_max_threads.restype = i32
     lib.oracle_max_threads.argtypes = []
@@ -110,6 +111,11 @@ class Oracle:
         k = self.lib.oracle_bfs(img.ctypes.data, h, w, pitch, conn, lab.ctypes.data)
         return lab, self._check(k)
 
+    def bfs_classes(self, img, conn: int = 8):
+        img, h, w, pitch, lab = self._prep(img)
+        k = self.lib.oracle_bfs_classes(img.ctypes.data, h, w, pitch, conn, lab.ctypes.data)
+        return lab, self._check(k)
+
     def canonicalize(self, labels: np.ndarray, k: int):
         lab = np.ascontiguousarray(labels, dtype=np.int32).copy()
         kk = self.lib.oracle_canonicalize(lab.ctypes.data, lab.size, int(k))
@@ -121,6 +127,12 @@ class Oracle:
 
 def default() -> Oracle:
     return Oracle(_get())
+
+
+def classes(img, conn: int = 8):
+    """Multi-class labelling: neighbours connect when their bytes are equal and non-zero;
+    canonical numbering (raster order of first pixels)."""
+    return default().bfs_classes(img, conn)
 
 
 def binarize(img, threshold: int) -> np.ndarray:

@@ -20,6 +20,8 @@
  *   oracle_paremsp   Algorithm 7 (PARemSP) with Algorithm 8 (merger) on OpenMP threads,
  *                    then the same renumbering.
  *   oracle_bfs       breadth-first flood fill straight from the definition (4 or 8).
+ *   oracle_bfs_classes  the same flood fill where neighbours connect only when their
+ *                    bytes are equal and non-zero (multi-class labelling).
  *
  * Readings taken where the paper's pseudocode is incomplete (each also listed in the
  * design notes):
@@ -513,6 +515,58 @@ int64_t oracle_bfs(const uint8_t *img, int64_t h, int64_t w, int64_t pitch, int3
                 if (ny < 0 || ny >= h || nx < 0 || nx >= w)
                     continue;
                 if (img[ny * pitch + nx] == 0 || label[ny * w + nx] != 0)
+                    continue;
+                label[ny * w + nx] = k;
+                queue[qt++] = ny * w + nx;
+            }
+        }
+    }
+    free(queue);
+    return k;
+}
+
+/* Multi-class labelling, from the definition: two pixels are connected when they are
+ * 4- or 8-neighbours with the same non-zero value (a class, e.g. a land-cover code; the
+ * paper's Section V labels binarised rasters and notes the method extends to such data).
+ * Breadth-first flood fill in raster order, so the numbering is canonical. */
+int64_t oracle_bfs_classes(const uint8_t *img, int64_t h, int64_t w, int64_t pitch, int32_t conn,
+                           int32_t *label)
+{
+    if (h < 0 || w < 0 || (h > 0 && w > 0 && (!img || !label || pitch < w)))
+        return ORACLE_ERR_ARG;
+    if (conn != 4 && conn != 8)
+        return ORACLE_ERR_ARG;
+    if (h == 0 || w == 0)
+        return 0;
+    int64_t n = h * w;
+    int64_t *queue = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!queue)
+        return ORACLE_ERR_NOMEM;
+    memset(label, 0, (size_t)n * sizeof(int32_t));
+    static const int dy8[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+    static const int dx8[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+    static const int dy4[4] = {-1, 0, 0, 1};
+    static const int dx4[4] = {0, -1, 1, 0};
+    const int *dy = conn == 8 ? dy8 : dy4;
+    const int *dx = conn == 8 ? dx8 : dx4;
+    lab_t k = 0;
+    for (int64_t s = 0; s < n; s++) {
+        int64_t sy = s / w, sx = s % w;
+        const uint8_t cls = img[sy * pitch + sx];
+        if (cls == 0 || label[s] != 0)
+            continue;
+        k++;
+        int64_t qh = 0, qt = 0;
+        queue[qt++] = s;
+        label[s] = k;
+        while (qh < qt) {
+            int64_t q = queue[qh++];
+            int64_t qy = q / w, qx = q % w;
+            for (int j = 0; j < conn; j++) {
+                int64_t ny = qy + dy[j], nx = qx + dx[j];
+                if (ny < 0 || ny >= h || nx < 0 || nx >= w)
+                    continue;
+                if (img[ny * pitch + nx] != cls || label[ny * w + nx] != 0)
                     continue;
                 label[ny * w + nx] = k;
                 queue[qt++] = ny * w + nx;
