@@ -140,6 +140,21 @@ typedef struct {
 int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity,
                         int32_t *num_components_dev, ccl_stream_t stream);
 
+/*
+ * ccl_label_classes - multi-class labelling: two pixels are connected when they are
+ * neighbours (4 or 8) with the same non-zero byte, e.g. land-cover codes of the rasters the
+ * paper binarises (Section V).  Background is byte 0; every other value is a class.  Each
+ * component has one class; numbering as ccl_label (raster order of first pixels over all
+ * classes).  Arguments, return values and blocking as ccl_label.
+ */
+int32_t ccl_label_classes(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes,
+                          int32_t connectivity, int32_t *labels, int32_t *num_components,
+                          ccl_stream_t stream);
+
+/* ccl_label_batch with multi-class labelling for every image (see ccl_label_classes). */
+int32_t ccl_label_batch_classes(const ccl_image *imgs, int32_t n, int32_t connectivity,
+                                int32_t *num_components_dev, ccl_stream_t stream);
+
 /* ccl_label_batch with object = byte > threshold for every image (see ccl_label_threshold). */
 int32_t ccl_label_batch_threshold(const ccl_image *imgs, int32_t n, int32_t connectivity,
                                   int32_t threshold, int32_t *num_components_dev,
@@ -218,7 +233,7 @@ int32_t ccl_server_reset_stats(ccl_server *srv);
 /* Finish every admitted and queued request, then free the server. */
 int32_t ccl_server_destroy(ccl_server *srv);
 
-/* Bytes of workspace one image of H x W needs under either connectivity (capacity planning). */
+/* Bytes of workspace one image of H x W needs in any mode (connectivity, multi-class) (capacity planning). */
 int32_t ccl_workspace_bytes(int32_t H, int32_t W, int64_t *bytes);
 
 /* Read and clear the device status word of `stream`'s workspace (waits for the stream).

@@ -77,6 +77,8 @@ _SIGS = {
     "ccl_label_batch": ([_P, _I32, _I32, _P, _P], _I32),
     "ccl_label_threshold": ([_P, _I32, _I32, _I64, _I32, _I32, _P, _P, _P], _I32),
     "ccl_label_batch_threshold": ([_P, _I32, _I32, _I32, _P, _P], _I32),
+    "ccl_label_classes": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
+    "ccl_label_batch_classes": ([_P, _I32, _I32, _P, _P], _I32),
     "ccl_workspace_bytes": ([_I32, _I32, _P], _I32),
     "ccl_device_status": ([_P, _P], _I32),
     "ccl_release": ([], _I32),
@@ -157,6 +159,14 @@ def ccl_label_threshold(img, H, W, pitch_bytes, connectivity, threshold, labels,
 
 def ccl_label_batch_threshold(imgs, n, connectivity, threshold, num_components_dev, stream) -> int:
     return lib().ccl_label_batch_threshold(imgs, n, connectivity, threshold, num_components_dev, stream)
+
+
+def ccl_label_classes(img, H, W, pitch_bytes, connectivity, labels, num_components, stream) -> int:
+    return lib().ccl_label_classes(img, H, W, pitch_bytes, connectivity, labels, num_components, stream)
+
+
+def ccl_label_batch_classes(imgs, n, connectivity, num_components_dev, stream) -> int:
+    return lib().ccl_label_batch_classes(imgs, n, connectivity, num_components_dev, stream)
 
 
 def ccl_workspace_bytes(H, W, bytes_ptr) -> int:
@@ -265,12 +275,15 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def label(img, connectivity: int = 8, out=None, stream=None, sync: bool = True, threshold: int | None = None):
+def label(img, connectivity: int = 8, out=None, stream=None, sync: bool = True, threshold: int | None = None,
+          classes: bool = False):
     """Label a 2-D uint8 CUDA tensor (rows may be padded: stride(1) must be 1).
 
     Returns ``(labels, K)`` with ``labels`` an int32 (H, W) CUDA tensor.  With ``sync=False``
     K is returned as a 1-element int32 CUDA tensor and nothing waits for the stream.  With
-    ``threshold`` set, object pixels are bytes greater than it (ccl_label_threshold).
+    ``threshold`` set, object pixels are bytes greater than it (ccl_label_threshold); with
+    ``classes``, neighbours connect when their bytes are equal and non-zero
+    (ccl_label_classes).
     """
     import torch
 
@@ -285,6 +298,13 @@ def label(img, connectivity: int = 8, out=None, stream=None, sync: bool = True, 
     elif out.dtype != torch.int32 or tuple(out.shape) != (H, W) or not out.is_contiguous():
         raise TypeError("out must be a contiguous int32 (H, W) tensor")
     s = _stream_ptr(stream)
+    if classes:
+        if not sync or threshold is not None:
+            raise ValueError("classes labelling returns K on the host and takes no threshold")
+        k = ctypes.c_int32(-1)
+        _check(ccl_label_classes(img.data_ptr(), H, W, pitch, connectivity, out.data_ptr(), ctypes.byref(k), s),
+               "ccl_label_classes")
+        return out, int(k.value)
     if threshold is not None:
         if not sync:
             raise ValueError("threshold labelling returns K on the host (sync=True)")
@@ -303,7 +323,8 @@ def label(img, connectivity: int = 8, out=None, stream=None, sync: bool = True, 
     return out, kd
 
 
-def label_batch(imgs, connectivity: int = 8, outs=None, stream=None, k_out=None, threshold: int | None = None):
+def label_batch(imgs, connectivity: int = 8, outs=None, stream=None, k_out=None, threshold: int | None = None,
+                classes: bool = False):
     """Label a list of 2-D uint8 CUDA tensors in one call.  Returns (labels list, K tensor).
     With ``threshold`` set, object pixels are bytes greater than it."""
     import torch
@@ -325,7 +346,10 @@ def label_batch(imgs, connectivity: int = 8, outs=None, stream=None, k_out=None,
         descs[i].pitch_bytes = im.stride(0) if H > 0 else W
         descs[i].labels = outs[i].data_ptr()
     kd = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if k_out is None else k_out
-    if threshold is None:
+    if classes:
+        _check(ccl_label_batch_classes(descs, n, connectivity, kd.data_ptr(), _stream_ptr(stream)),
+               "ccl_label_batch_classes")
+    elif threshold is None:
         _check(ccl_label_batch(descs, n, connectivity, kd.data_ptr(), _stream_ptr(stream)), "ccl_label_batch")
     else:
         _check(ccl_label_batch_threshold(descs, n, connectivity, int(threshold), kd.data_ptr(), _stream_ptr(stream)),

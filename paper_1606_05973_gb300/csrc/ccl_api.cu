@@ -97,7 +97,8 @@ int32_t check_args(const void *img, int32_t H, int32_t W, int64_t pitch, int32_t
 {
     if (H < 0 || W < 0)
         return CCL_ERR_INVALID_ARGUMENT;
-    if (conn != 4 && conn != 8)
+    const int c = conn & ~CONN_CLASSES;
+    if (c != 4 && c != 8)
         return CCL_ERR_INVALID_ARGUMENT;
     if (H == 0 || W == 0)
         return CCL_OK;
@@ -213,8 +214,12 @@ int32_t ccl_workspace_bytes(int32_t H, int32_t W, int64_t *bytes)
         *bytes = HDR;
         return CCL_OK;
     }
-    const int64_t b8 = main_layout(H, W, 8).bytes, b4 = main_layout(H, W, 4).bytes;
-    *bytes = HDR + (b8 > b4 ? b8 : b4);
+    int64_t mx = 0;
+    for (int conn : {8, 4, 8 | CONN_CLASSES, 4 | CONN_CLASSES}) {
+        const int64_t b = main_layout(H, W, conn).bytes;
+        mx = b > mx ? b : mx;
+    }
+    *bytes = HDR + mx;
     return CCL_OK;
 }
 
@@ -223,6 +228,8 @@ int32_t ccl_label_async(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_
                         ccl_stream_t stream)
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (connectivity & CONN_CLASSES)
+        return CCL_ERR_INVALID_ARGUMENT;
     int32_t rc = check_args(img, H, W, pitch_bytes, connectivity, labels);
     if (rc != CCL_OK)
         return rc;
@@ -273,13 +280,25 @@ int32_t label_sync(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes
 int32_t ccl_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes, int32_t connectivity,
                   int32_t *labels, int32_t *num_components, ccl_stream_t stream)
 {
+    if (connectivity & CONN_CLASSES)
+        return CCL_ERR_INVALID_ARGUMENT;
     return label_sync(img, H, W, pitch_bytes, connectivity, 0, labels, num_components, stream);
 }
 
 int32_t ccl_label_threshold(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes, int32_t connectivity,
                             int32_t threshold, int32_t *labels, int32_t *num_components, ccl_stream_t stream)
 {
+    if (connectivity & CONN_CLASSES)
+        return CCL_ERR_INVALID_ARGUMENT;
     return label_sync(img, H, W, pitch_bytes, connectivity, threshold, labels, num_components, stream);
+}
+
+int32_t ccl_label_classes(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes, int32_t connectivity,
+                          int32_t *labels, int32_t *num_components, ccl_stream_t stream)
+{
+    if (connectivity != 4 && connectivity != 8)
+        return CCL_ERR_INVALID_ARGUMENT;
+    return label_sync(img, H, W, pitch_bytes, connectivity | CONN_CLASSES, 0, labels, num_components, stream);
 }
 
 int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch_bytes,
@@ -287,6 +306,8 @@ int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pi
                        ccl_stream_t stream)
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (connectivity & CONN_CLASSES)
+        return CCL_ERR_INVALID_ARGUMENT;
     int32_t rc = check_args(img_host, H, W, pitch_bytes, connectivity, labels_host);
     if (rc != CCL_OK)
         return rc;
@@ -465,7 +486,7 @@ int32_t label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, int3
         if (imgs[i].H > 0 && imgs[i].W > 0)
             keep.push_back(i);
     }
-    if (connectivity != 4 && connectivity != 8)
+    if ((connectivity & ~CONN_CLASSES) != 4 && (connectivity & ~CONN_CLASSES) != 8)
         return CCL_ERR_INVALID_ARGUMENT;
     if (num_components_dev) {
         for (int32_t i = 0; i < n; i++) {
@@ -491,13 +512,25 @@ int32_t label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, int3
 int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, int32_t *num_components_dev,
                         ccl_stream_t stream)
 {
+    if (connectivity & CONN_CLASSES)
+        return CCL_ERR_INVALID_ARGUMENT;
     return label_batch(imgs, n, connectivity, 0, num_components_dev, stream);
 }
 
 int32_t ccl_label_batch_threshold(const ccl_image *imgs, int32_t n, int32_t connectivity, int32_t threshold,
                                   int32_t *num_components_dev, ccl_stream_t stream)
 {
+    if (connectivity & CONN_CLASSES)
+        return CCL_ERR_INVALID_ARGUMENT;
     return label_batch(imgs, n, connectivity, threshold, num_components_dev, stream);
+}
+
+int32_t ccl_label_batch_classes(const ccl_image *imgs, int32_t n, int32_t connectivity,
+                                int32_t *num_components_dev, ccl_stream_t stream)
+{
+    if (connectivity != 4 && connectivity != 8)
+        return CCL_ERR_INVALID_ARGUMENT;
+    return label_batch(imgs, n, connectivity | CONN_CLASSES, 0, num_components_dev, stream);
 }
 
 int32_t ccl_device_status(ccl_stream_t stream, int32_t *flags)

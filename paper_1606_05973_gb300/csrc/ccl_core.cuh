@@ -316,17 +316,22 @@ CCL_HD void store4(int *dst, const int v[4])
 // ---- tile configuration ----------------------------------------------------------------
 // CONN = 8: a strip is two rows (under 8-connectivity every run of row 2s | row 2s+1 is
 // connected).  CONN = 4: a strip is one row (diagonal contacts do not connect).
-template <int TH_, int TW_, int NT_, int CONN_ = 8> struct Cfg {
+// CLS: multi-class labelling (neighbours connect when their bytes are equal and non-zero);
+// a strip is one row and a run also ends where the value changes.
+template <int TH_, int TW_, int NT_, int CONN_ = 8, bool CLS_ = false> struct Cfg {
     static constexpr int TH = TH_;        // tile rows (even: whole strips)
     static constexpr int TW = TW_;        // tile columns (multiple of 32)
     static constexpr int NT = NT_;        // threads per CTA
     static constexpr int CONN = CONN_;    // 8 or 4
-    static constexpr int RPS = CONN == 8 ? 2 : 1;  // rows per strip
+    static constexpr bool CLS = CLS_;     // multi-class
+    static constexpr int RPS = (CONN == 8 && !CLS) ? 2 : 1;  // rows per strip
     static constexpr int NW = TW / 32;    // 32-bit words per tile row
     static constexpr int NS = TH / RPS;   // strips per tile
     static constexpr int CH = TW / 16;    // 16-byte chunks per tile row
-    static constexpr int ROWCAP = TW / 2; // max components whose first pixel is in one tile row
-    static constexpr int RC = TW / 2;     // max strip runs in one strip
+    // max components whose first pixel is in one tile row, and max runs in one strip: runs
+    // of one value are separated by background (TW/2); runs of different classes may touch
+    static constexpr int ROWCAP = CLS ? TW : TW / 2;
+    static constexpr int RC = CLS ? TW : TW / 2;
     static constexpr int RMAX = NS * RC;  // max strip runs in one tile
     static_assert(TW % 32 == 0 && TH % 2 == 0, "tile shape");
     static_assert(CONN == 8 || CONN == 4, "connectivity");
@@ -344,6 +349,7 @@ struct Img {
     int vec_in;          // img 16-byte aligned and pitch % 16 == 0
     int nTX, nTY;        // tiles across / down
     uint32_t *bitpack;   // [H][nTX*NW] object bits, bit b of word w = column 32w+b
+    uint32_t *cstart;    // multi-class only: [H][nTX*NW] run starts (a run ends where the value changes)
     uint16_t *runinfo;   // [tile][strip][RC] root code of each strip run (row*ROWCAP + j)
     int *P;              // global parents, index ((y*nTX + tx)*ROWCAP + j)
     int *nseg;           // [H*nTX] local components whose first pixel lies in (y, tx)
@@ -364,7 +370,7 @@ struct Img {
 struct Layout {
     int nTX, nTY;
     int64_t nSeg, nP, nBitWords, nEdgeRow, nEdgeCol, nBsum, nRunInfo;
-    int64_t off_bitpack, off_runinfo, off_P, off_nseg, off_cnt, off_edgeRow, off_edgeCol, off_bsum, bytes;
+    int64_t off_bitpack, off_runinfo, off_P, off_nseg, off_cnt, off_edgeRow, off_edgeCol, off_bsum, off_cstart, bytes;
 };
 constexpr int MAX_GLOBAL_CTAS = 4096;  // upper bound on the global kernel's grid
 
@@ -391,6 +397,7 @@ template <class C> CCL_HD Layout plan_layout(int H, int W)
     L.off_edgeRow = o; o = align256(o + L.nEdgeRow * 4);
     L.off_edgeCol = o; o = align256(o + L.nEdgeCol * 4);
     L.off_bsum = o; o = align256(o + L.nBsum * 4);
+    L.off_cstart = o; o = align256(o + (C::CLS ? L.nBitWords * 4 : 0));
     L.bytes = o;
     return L;
 }
@@ -408,7 +415,14 @@ template <class C> struct SmemRuns {
 // A parent word holds the parent's run number in its low 16 bits.  The high 16 bits are
 // all ones while runs are joined (so every comparison of two words compares parents), and
 // a root's high half later receives its component's first pixel (tile raster position).
-template <class C> struct SmemL : SmemRuns<C> {
+// multi-class tiles also keep the tile's bytes (load phase only) and, per row, which
+// pixels have the same class as their up-left, up and up-right neighbours
+template <class C, bool = C::CLS> struct SmemCls {};
+template <class C> struct SmemCls<C, true> {
+    uint32_t eq[3][C::TH][C::NW];    // bit x of eq[d+1][r]: byte(r, x) == byte(r-1, x+d) != 0
+    uint8_t raw[C::TH][C::TW];       // the tile's bytes (0 outside the image)
+};
+template <class C> struct SmemL : SmemRuns<C>, SmemCls<C> {
     uint32_t par[C::RMAX];           // union-find parents (see above)
     uint32_t rootbits[C::TH][C::NW]; // first pixels of the local components
     int rootpre[C::TH][C::NW];       // exclusive popcount prefix of rootbits along a row
@@ -488,6 +502,10 @@ template <class C> struct Tile {
     // -- phase: image bytes -> object bits; clear root bits; every parent starts as a root --
     CCL_HD static void load_image(const Img &a, SL &s, int ty, int tx, int tid)
     {
+        if constexpr (C::CLS) {
+            load_classes(a, s, ty, tx, tid);
+            return;
+        }
         const int y0 = ty * C::TH, x0 = tx * C::TW;
         uint16_t *half = reinterpret_cast<uint16_t *>(&s.bits[0][0]);
         constexpr int PER = (C::TH * C::CH + C::NT - 1) / C::NT;
@@ -535,15 +553,90 @@ template <class C> struct Tile {
             s.par[q] = PAR_HI | (uint32_t)q;
     }
 
+    // Multi-class load: the tile's bytes into shared memory, then per (row, word) the object
+    // bits (non-zero bytes), the run starts (object, and not the same value as the pixel to
+    // the left) and the same-class masks toward the row above.  Pixels outside the tile
+    // count as different (the boundary merge joins across tiles).
+    CCL_HD static void load_classes(const Img &a, SL &s, int ty, int tx, int tid)
+    {
+        if constexpr (C::CLS) {
+            const int y0 = ty * C::TH, x0 = tx * C::TW;
+            const bool full = a.vec_in && (y0 + C::TH <= a.H) && (x0 + C::TW <= a.W);
+            for (int q = tid; q < C::TH * C::CH; q += C::NT) {
+                const int r = q / C::CH, cc = q % C::CH;
+                const int y = y0 + r, x = x0 + 16 * cc;
+                uint8_t *dst = &s.raw[r][16 * cc];
+                if (full) {
+                    const uint8_t *src = a.img + (int64_t)y * a.pitch + x;
+                    uint32_t v[4];
+#if defined(__CUDA_ARCH__)
+                    const uint4 qv = __ldcs(reinterpret_cast<const uint4 *>(src));
+                    v[0] = qv.x;
+                    v[1] = qv.y;
+                    v[2] = qv.z;
+                    v[3] = qv.w;
+#else
+                    memcpy(v, src, 16);
+#endif
+                    for (int k = 0; k < 4; k++)
+                        reinterpret_cast<uint32_t *>(dst)[k] = v[k];
+                } else {
+                    for (int i = 0; i < 16; i++)
+                        dst[i] = (y < a.H && x + i < a.W) ? a.img[(int64_t)y * a.pitch + x + i] : (uint8_t)0;
+                }
+            }
+            cta_sync();
+            for (int q = tid; q < C::TH * C::NW; q += C::NT) {
+                const int r = q / C::NW, w = q % C::NW;
+                uint32_t obj = 0, eqL = 0, eqUL = 0, eqU = 0, eqUR = 0;
+                for (int b = 0; b < 32; b++) {
+                    const int x = w * 32 + b;
+                    const uint8_t v = s.raw[r][x];
+                    if (!v)
+                        continue;
+                    obj |= 1u << b;
+                    if (x > 0 && s.raw[r][x - 1] == v)
+                        eqL |= 1u << b;
+                    if (r > 0) {
+                        if (x > 0 && s.raw[r - 1][x - 1] == v)
+                            eqUL |= 1u << b;
+                        if (s.raw[r - 1][x] == v)
+                            eqU |= 1u << b;
+                        if (x + 1 < C::TW && s.raw[r - 1][x + 1] == v)
+                            eqUR |= 1u << b;
+                    }
+                }
+                s.bits[r][w] = obj;
+                s.starts[r][w] = obj & ~eqL;
+                s.eq[0][r][w] = eqUL;
+                s.eq[1][r][w] = eqU;
+                s.eq[2][r][w] = eqUR;
+            }
+            for (int q = tid; q < C::TH * C::NW; q += C::NT)
+                (&s.rootbits[0][0])[q] = 0u;
+            for (int q = tid; q < C::RMAX; q += C::NT)
+                s.par[q] = PAR_HI | (uint32_t)q;
+        } else {
+            (void)a;
+            (void)s;
+            (void)ty;
+            (void)tx;
+            (void)tid;
+        }
+    }
+
     CCL_HD static void store_bitpack(const Img &a, const SR &s, int ty, int tx, int tid)
     {
         const int y0 = ty * C::TH;
         const int64_t WW = (int64_t)a.nTX * C::NW;
         for (int q = tid; q < C::TH * C::NW; q += C::NT) {
             const int r = q / C::NW, w = q % C::NW;
-            if (y0 + r < a.H)
-                a.bitpack[CCL_CHK((int64_t)(y0 + r) * WW + tx * C::NW + w, (int64_t)a.H * WW, a.status)] =
-                    s.bits[r][w];
+            if (y0 + r < a.H) {
+                const int64_t i = CCL_CHK((int64_t)(y0 + r) * WW + tx * C::NW + w, (int64_t)a.H * WW, a.status);
+                a.bitpack[i] = s.bits[r][w];
+                if constexpr (C::CLS)
+                    a.cstart[i] = s.starts[r][w];
+            }
         }
     }
 
@@ -553,15 +646,17 @@ template <class C> struct Tile {
         const int64_t WW = (int64_t)a.nTX * C::NW;
         for (int q = tid; q < C::TH * C::NW; q += C::NT) {
             const int r = q / C::NW, w = q % C::NW;
-            s.bits[r][w] = (y0 + r < a.H)
-                ? ld_ro(&a.bitpack[CCL_CHK((int64_t)(y0 + r) * WW + tx * C::NW + w, (int64_t)a.H * WW, a.status)])
-                : 0u;
+            const bool in = y0 + r < a.H;
+            const int64_t i = in ? CCL_CHK((int64_t)(y0 + r) * WW + tx * C::NW + w, (int64_t)a.H * WW, a.status) : 0;
+            s.bits[r][w] = in ? ld_ro(&a.bitpack[i]) : 0u;
+            if constexpr (C::CLS)
+                s.starts[r][w] = in ? ld_ro(&a.cstart[i]) : 0u;
         }
     }
 
     CCL_HD static uint32_t strip_word(const SR &s, int st, int w)
     {
-        if constexpr (C::CONN == 4)
+        if constexpr (C::RPS == 1)
             return s.bits[st][w];
         else
             return s.bits[2 * st][w] | s.bits[2 * st + 1][w];
@@ -572,7 +667,7 @@ template <class C> struct Tile {
     // else the run's first column in the lower row.
     CCL_HD static int first_pixel(const SR &s, int st, int w, int b)
     {
-        if constexpr (C::CONN == 4)
+        if constexpr (C::RPS == 1)
             return st * C::TW + w * 32 + b;  // a one-row run starts at its first pixel
         else
             return first_pixel2(s, st, w, b);
@@ -620,7 +715,8 @@ template <class C> struct Tile {
             const int u = u0 + tid;
             const bool ok = u < C::NS * C::NW;
             const int st = ok ? u / C::NW : 0, w = u % C::NW;
-            const uint32_t st_bits = ok ? starts_of(s, st, w) : 0u;
+            // multi-class run starts come from the bytes (load phase, or the global copy)
+            const uint32_t st_bits = ok ? (C::CLS ? s.starts[st][w] : starts_of(s, st, w)) : 0u;
             const int c = popc32(st_bits);
             const int incl = warp_incl_sum(c, C::NW);
             if (ok) {
@@ -642,8 +738,85 @@ template <class C> struct Tile {
     // of single-row runs (one in A, one in B) that are 8-adjacent is found exactly once:
     // either the B run starts where A has a pixel at that column or one to the left, or
     // the A run starts one column right of a B pixel.
+    // Multi-class: rows A = st-1 and B = st, and for each direction d (up-left, up,
+    // up-right) the columns x where byte(B, x) == byte(A, x+d) != 0.  Every such contact
+    // joins the B run covering x with the A run covering x+d; a contact is an event unless
+    // the contact one column to the left (same d) joins the same two runs.
+    CCL_HD static void unions_cls(const Img &a, SL &s, int tid)
+    {
+        if constexpr (C::CLS) {
+            for (int u0 = 0; u0 < C::NS * C::NW; u0 += C::NT) {
+                const int u = u0 + tid, st = u / C::NW, w = u % C::NW;
+                uint32_t ev[3] = {0u, 0u, 0u}, sA = 0, sB = 0, sAn = 0;
+                int baseA = 0, baseB = 0, baseAn = 0;
+                if (u < C::NS * C::NW && st > 0) {
+                    sA = s.starts[st - 1][w];
+                    sB = s.starts[st][w];
+                    const uint32_t sAp = (w > 0) ? s.starts[st - 1][w - 1] : 0u;
+                    sAn = (w + 1 < C::NW) ? s.starts[st - 1][w + 1] : 0u;
+                    baseA = (st - 1) * C::RC + s.rpre[st - 1][w] - 1;
+                    baseB = st * C::RC + s.rpre[st][w] - 1;
+                    baseAn = (w + 1 < C::NW) ? (st - 1) * C::RC + s.rpre[st - 1][w + 1] - 1 : 0;
+                    // A starts seen from column x: at x-1, x, x+1
+                    const uint32_t SA[3] = {(sA << 1) | (sAp >> 31), sA, (sA >> 1) | (sAn << 31)};
+                    for (int d = 0; d < 3; d++) {
+                        if (C::CONN == 4 && d != 1)
+                            continue;
+                        const uint32_t M = s.eq[d][st][w];
+                        ev[d] = M & ~((M << 1) & ~sB & ~SA[d]);
+                    }
+                }
+                int rx = -1, ry = -1;
+                for (int it = 0;; it++) {
+                    if (rx < 0 && (ev[0] | ev[1] | ev[2])) {
+                        const int d = ev[0] ? 0 : (ev[1] ? 1 : 2);
+                        const int b = ctz32(ev[d]);
+                        ev[d] &= ev[d] - 1u;
+                        const int nb = baseB + popc32(sB & mask_upto(b));
+                        const int xa = b + d - 1;  // column of the A pixel, -1..32
+                        const int na = (xa < 32) ? baseA + popc32(sA & mask_upto(xa)) : baseAn + (int)(sAn & 1u);
+                        rx = CCL_CHK(nb, C::RMAX, a.status);
+                        ry = CCL_CHK(na, C::RMAX, a.status);
+                    }
+                    if (!warp_ballot(rx >= 0 || (ev[0] | ev[1] | ev[2]) != 0u))
+                        break;
+                    if (it == SMEM_LOOP_CAP) {
+                        flag_status(a.status, ST_LOOP_CAP);
+                        break;
+                    }
+                    if (rx >= 0) {
+                        const uint32_t px = ld_su(&s.par[rx]);
+                        const uint32_t py = ld_su(&s.par[ry]);
+                        const bool xs = px > py;
+                        const int r = xs ? rx : ry;
+                        const uint32_t pr = xs ? px : py, po = xs ? py : px;
+                        if (px == py) {
+                            rx = -1;
+                        } else if (at_cas_u(&s.par[r], pr, po) == pr) {
+                            const int up = CCL_CHK((int)(pr & PAR_LO), C::RMAX, a.status);
+                            if (up == r)
+                                rx = -1;
+                            else if (xs)
+                                rx = up;
+                            else
+                                ry = up;
+                        }
+                    }
+                }
+            }
+        } else {
+            (void)a;
+            (void)s;
+            (void)tid;
+        }
+    }
+
     CCL_HD static void unions(const Img &a, SL &s, int tid)
     {
+        if constexpr (C::CLS) {
+            unions_cls(a, s, tid);
+            return;
+        }
         // every thread runs the same number of outer passes (NT is a multiple of 32), so
         // whole warps reach the votes below
         for (int u0 = 0; u0 < C::NS * C::NW; u0 += C::NT) {
@@ -933,6 +1106,7 @@ template <class C> struct Tile {
 struct EdgeItem {
     int e, b, aa, c;
     bool same_prev;
+    int ce, cb, ca, cc;  // multi-class: the bytes of the four pixels
 };
 
 // item i < nh: horizontal boundary above band 1 + i / W at column i % W; else vertical
@@ -950,6 +1124,13 @@ template <class C> CCL_HD EdgeItem load_edge_item(const Img &a, int64_t i, int64
         it.aa = (x > 0) ? above[x - 1] : -1;
         it.c = (x + 1 < a.W) ? above[x + 1] : -1;
         it.same_prev = (x > 0) && top[x - 1] == it.e;
+        if constexpr (C::CLS) {
+            const uint8_t *r0 = a.img + (int64_t)(ty * C::TH) * a.pitch, *r1 = r0 - a.pitch;
+            it.ce = r0[x];
+            it.cb = r1[x];
+            it.ca = (x > 0) ? r1[x - 1] : -1;
+            it.cc = (x + 1 < a.W) ? r1[x + 1] : -1;
+        }
     } else {
         const int64_t k = i - nh;
         const int tx = 1 + (int)(k / a.H), y = (int)(k % a.H);
@@ -963,6 +1144,13 @@ template <class C> CCL_HD EdgeItem load_edge_item(const Img &a, int64_t i, int64
         it.aa = (y - 1 >= yb0) ? left[y - 1] : -1;
         it.c = (y + 1 < yb1) ? left[y + 1] : -1;
         it.same_prev = (y - 1 >= yb0) && me[y - 1] == it.e;
+        if constexpr (C::CLS) {
+            const uint8_t *col = a.img + tx * C::TW;  // column tx*TW of row 0
+            it.ce = col[(int64_t)y * a.pitch];
+            it.cb = col[(int64_t)y * a.pitch - 1];
+            it.ca = (y - 1 >= yb0) ? col[(int64_t)(y - 1) * a.pitch - 1] : -1;
+            it.cc = (y + 1 < yb1) ? col[(int64_t)(y + 1) * a.pitch - 1] : -1;
+        }
     }
     return it;
 }
@@ -971,6 +1159,19 @@ template <class C> CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it)
 {
     if (it.e < 0)
         return;
+    if constexpr (C::CLS) {
+        // multi-class: join each facing pixel (and, under 8-connectivity, each diagonal one)
+        // of the same value
+        if (it.b >= 0 && it.cb == it.ce)
+            rem_unite_g(a.P, a.nP, it.e, it.b, a.status);
+        if (C::CONN == 8) {
+            if (it.aa >= 0 && it.ca == it.ce)
+                rem_unite_g(a.P, a.nP, it.e, it.aa, a.status);
+            if (it.c >= 0 && it.cc == it.ce)
+                rem_unite_g(a.P, a.nP, it.e, it.c, a.status);
+        }
+        return;
+    }
     if constexpr (C::CONN == 4) {
         // 4-connectivity: only the facing pixel; the previous edge pixel (same node) has
         // already joined through its own facing pixel if that one is an object pixel

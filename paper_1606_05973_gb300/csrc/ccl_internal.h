@@ -36,6 +36,11 @@ void prof_end(int kid, cudaStream_t s);
 using MainCfg = Cfg<CCL_TILE_H, CCL_TILE_W, CCL_TILE_NT, 8>;
 // 4-connectivity: one-row strips, so half the tile height keeps the same shared memory
 using MainCfg4 = Cfg<CCL_TILE_H / 2, CCL_TILE_W, CCL_TILE_NT, 4>;
+// multi-class labelling (one-row strips as well)
+using MainCfgC8 = Cfg<CCL_TILE_H / 2, CCL_TILE_W, CCL_TILE_NT, 8, true>;
+using MainCfgC4 = Cfg<CCL_TILE_H / 2, CCL_TILE_W, CCL_TILE_NT, 4, true>;
+// Inside the library a connectivity value may carry this bit: multi-class labelling.
+constexpr int CONN_CLASSES = 0x100;
 
 Layout main_layout(int H, int W, int conn);
 

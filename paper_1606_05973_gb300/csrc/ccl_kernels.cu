@@ -67,7 +67,12 @@ template <class C> __global__ void __launch_bounds__(C::NT, 2048 / C::NT) k_fina
 
 Layout main_layout(int H, int W, int conn)
 {
-    return conn == 4 ? plan_layout<MainCfg4>(H, W) : plan_layout<MainCfg>(H, W);
+    switch (conn) {
+    case 4: return plan_layout<MainCfg4>(H, W);
+    case 8 | CONN_CLASSES: return plan_layout<MainCfgC8>(H, W);
+    case 4 | CONN_CLASSES: return plan_layout<MainCfgC4>(H, W);
+    default: return plan_layout<MainCfg>(H, W);
+    }
 }
 
 void bind_workspace(Img &a, const Layout &L, void *ws)
@@ -84,6 +89,7 @@ void bind_workspace(Img &a, const Layout &L, void *ws)
     a.edgeRow = reinterpret_cast<int *>(b + L.off_edgeRow);
     a.edgeCol = reinterpret_cast<int *>(b + L.off_edgeCol);
     a.bsum = reinterpret_cast<int *>(b + L.off_bsum);
+    a.cstart = reinterpret_cast<uint32_t *>(b + L.off_cstart);
     a.nP = L.nP;
     a.nSeg = L.nSeg;
 }
@@ -139,6 +145,10 @@ cudaError_t kernels_init()
             err = init_cfg<MainCfg>();
         if (err == cudaSuccess)
             err = init_cfg<MainCfg4>();
+        if (err == cudaSuccess)
+            err = init_cfg<MainCfgC8>();
+        if (err == cudaSuccess)
+            err = init_cfg<MainCfgC4>();
     });
     return err;
 }
@@ -207,13 +217,22 @@ static cudaError_t launch_batch_t(const Batch &B, int64_t tiles, int64_t items, 
 
 cudaError_t launch_label(const Img &a, const Layout &L, int conn, cudaStream_t s)
 {
-    return conn == 4 ? launch_label_t<MainCfg4>(a, L, s) : launch_label_t<MainCfg>(a, L, s);
+    switch (conn) {
+    case 4: return launch_label_t<MainCfg4>(a, L, s);
+    case 8 | CONN_CLASSES: return launch_label_t<MainCfgC8>(a, L, s);
+    case 4 | CONN_CLASSES: return launch_label_t<MainCfgC4>(a, L, s);
+    default: return launch_label_t<MainCfg>(a, L, s);
+    }
 }
 
 cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, int conn, cudaStream_t s)
 {
-    return conn == 4 ? launch_batch_t<MainCfg4>(B, tiles, items, segs, s)
-                     : launch_batch_t<MainCfg>(B, tiles, items, segs, s);
+    switch (conn) {
+    case 4: return launch_batch_t<MainCfg4>(B, tiles, items, segs, s);
+    case 8 | CONN_CLASSES: return launch_batch_t<MainCfgC8>(B, tiles, items, segs, s);
+    case 4 | CONN_CLASSES: return launch_batch_t<MainCfgC4>(B, tiles, items, segs, s);
+    default: return launch_batch_t<MainCfg>(B, tiles, items, segs, s);
+    }
 }
 
 }  // namespace ccl

@@ -192,6 +192,40 @@ def gray_field_device(h: int, w: int, sigma: float, seed: int, device):
     return torch.clamp(torch.round(128.0 + 40.0 * z), 0, 255).to(torch.uint8)
 
 
+def classes_device(h: int, w: int, sigma: float, ncls: int, seed: int, device, background: float = 0.1):
+    """Multi-class stand-in for a land-cover raster: a smoothed Gaussian field (as in
+    ``blobs_device``) cut at its equal-mass quantiles into classes 1..ncls, and byte 0 (no
+    data) where an independent smoothed field lies below its ``background`` quantile."""
+    import torch
+
+    def field(sd):
+        rng = _rng(sd)
+        noise = torch.from_numpy(rng.standard_normal((h, w), dtype=np.float32)).to(device)
+        k = _gauss_kernel(sigma)
+        r = (k.size - 1) // 2
+        for axis in (0, 1):
+            n = noise.shape[axis]
+            kk = np.zeros(n, dtype=np.float32)
+            for i, v in enumerate(k):
+                kk[(i - r) % n] += v
+            fk = torch.fft.rfft(torch.from_numpy(kk).to(device))
+            shape = [1, 1]
+            shape[axis] = fk.numel()
+            noise = torch.fft.irfft(torch.fft.rfft(noise, dim=axis) * fk.reshape(shape), n=n, dim=axis)
+        return noise.reshape(-1)
+
+    f = field(seed)
+    srt = torch.sort(f).values
+    m = f.numel()
+    cuts = torch.stack([srt[min(m - 1, (m * j) // ncls)] for j in range(1, ncls)]) if ncls > 1 else srt[:0]
+    cls = (torch.bucketize(f, cuts, right=True) + 1).to(torch.uint8)
+    if background > 0:
+        g = field(seed + 7919)
+        thr = torch.sort(g).values[int(background * (m - 1))]
+        cls[g < thr] = 0
+    return cls.reshape(h, w)
+
+
 def serpentine(h: int, w: int) -> np.ndarray:
     """One 1-px-wide path covering the image: even rows full; odd row y holds a single
     pixel at x = W-1 when y % 4 == 1 and at x = 0 when y % 4 == 3.  One component

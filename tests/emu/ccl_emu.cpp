@@ -304,6 +304,7 @@ template <class C> struct Emu {
             a.nTX = L[i].nTX;
             a.nTY = L[i].nTY;
             a.bitpack = (uint32_t *)(b + L[i].off_bitpack);
+            a.cstart = (uint32_t *)(b + L[i].off_cstart);
             a.runinfo = (uint16_t *)(b + L[i].off_runinfo);
             a.nRunInfo = L[i].nRunInfo;
             a.P = (int *)(b + L[i].off_P);
@@ -375,6 +376,7 @@ template <class C> struct Emu {
         a.nTX = L.nTX;
         a.nTY = L.nTY;
         a.bitpack = (uint32_t *)(b + L.off_bitpack);
+        a.cstart = (uint32_t *)(b + L.off_cstart);
         a.runinfo = (uint16_t *)(b + L.off_runinfo);
         a.nRunInfo = L.nRunInfo;
         a.P = (int *)(b + L.off_P);
@@ -412,7 +414,8 @@ uint32_t emu_gt_mask16(const uint8_t *src, int32_t thr)
 
 // shapes, 8-connectivity: 0 = 64x256 tiles (256 threads); 1 = 4x32 (32); 2 = 8x64 (64);
 // 3 = 128x256 (256); 4 = 64x512 (256).  4-connectivity: 5 = 32x256 (256); 6 = 4x32 (32);
-// 7 = 8x64 (64); 8 = 2x32 (32)
+// 7 = 8x64 (64); 8 = 2x32 (32).  Multi-class, 8: 9 = 4x32, 10 = 8x64, 11 = 32x256;
+// multi-class, 4: 12 = 4x32, 13 = 32x256
 int64_t emu_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t *labels, uint64_t seed,
                   int32_t shape, int32_t *status)
 {
@@ -426,7 +429,12 @@ int64_t emu_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32
     case 5: return Emu<Cfg<32, 256, 256, 4>>(seed).run(img, H, W, pitch, labels, status);
     case 6: return Emu<Cfg<4, 32, 32, 4>>(seed).run(img, H, W, pitch, labels, status);
     case 7: return Emu<Cfg<8, 64, 64, 4>>(seed).run(img, H, W, pitch, labels, status);
-    default: return Emu<Cfg<2, 32, 32, 4>>(seed).run(img, H, W, pitch, labels, status);
+    case 8: return Emu<Cfg<2, 32, 32, 4>>(seed).run(img, H, W, pitch, labels, status);
+    case 9: return Emu<Cfg<4, 32, 32, 8, true>>(seed).run(img, H, W, pitch, labels, status);
+    case 10: return Emu<Cfg<8, 64, 64, 8, true>>(seed).run(img, H, W, pitch, labels, status);
+    case 11: return Emu<Cfg<32, 256, 256, 8, true>>(seed).run(img, H, W, pitch, labels, status);
+    case 12: return Emu<Cfg<4, 32, 32, 4, true>>(seed).run(img, H, W, pitch, labels, status);
+    default: return Emu<Cfg<32, 256, 256, 4, true>>(seed).run(img, H, W, pitch, labels, status);
     }
 }
 
@@ -440,6 +448,8 @@ void emu_label_batch(int32_t n, const uint8_t *const *imgs, const int32_t *H, co
     case 1: Emu<Cfg<4, 32, 32>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
     case 2: Emu<Cfg<8, 64, 64>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
     case 6: Emu<Cfg<4, 32, 32, 4>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
+    case 9: Emu<Cfg<4, 32, 32, 8, true>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
+    case 12: Emu<Cfg<4, 32, 32, 4, true>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
     default: Emu<Cfg<8, 64, 64, 4>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
     }
 }

@@ -37,6 +37,29 @@ def main(path, n_random, sizes=None):
                     if not (k == rk and st == 0 and np.array_equal(lab, ref)):
                         bad += 1
                         print("mismatch", conn, img.shape, shape, seed, k, rk, st)
+    # multi-class images (0 = background, 1..n classes): single images and batches
+    crng = np.random.default_rng(17)
+    for i, (h, w) in enumerate(all_sizes if sizes is None else all_sizes[:sizes]):
+        for ncls in (1, 2, 3, 9):
+            img = crng.integers(0, ncls + 1, size=(h, w), dtype=np.uint8)
+            for conn, small, large in ((8, (9, 10), (11,)), (4, (12,), (13,))):
+                ref, rk = oracle.classes(img, conn)
+                for shape in small + (large if i % 3 == 0 else ()):
+                    pitch = None if ncls % 2 else w + 5
+                    lab, k, st = emu.label(img, seed=i * 11 + ncls, shape=shape, pitch=pitch)
+                    if not (k == rk and st == 0 and np.array_equal(lab, ref)):
+                        bad += 1
+                        print("classes mismatch", conn, img.shape, ncls, shape, k, rk, st)
+    for trial in range(4):
+        batch = [crng.integers(0, 4, size=(int(crng.integers(1, 40)), int(crng.integers(1, 150))), dtype=np.uint8)
+                 for _ in range(int(crng.integers(1, 6)))]
+        shape, conn = ((9, 8), (12, 4))[trial % 2]
+        labs, ks, st = emu.label_batch(batch, seed=trial, shape=shape)
+        for img, lab, kk in zip(batch, labs, ks):
+            ref, rk = oracle.classes(img, conn)
+            if not (kk == rk and st == 0 and np.array_equal(lab, ref)):
+                bad += 1
+                print("classes batch mismatch", img.shape, kk, rk, st)
     rng = np.random.default_rng(5)
     for i in range(n_random):
         h = int(rng.integers(1, 20))
