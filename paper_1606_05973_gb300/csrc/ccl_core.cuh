@@ -289,6 +289,14 @@ CCL_HD uint32_t gt_nibble(uint32_t v, uint32_t c)
     // gather bits 0, 8, 16, 24 of (m >> 7) into bits 28..31 (cross terms land elsewhere)
     return ((m >> 7) * 0x10204080u) >> 28;
 }
+// 4 bytes -> 4 bits, bit i = (byte i of a == byte i of b): a zero-byte test of a ^ b
+// (bit 7 of a byte of ~((t & 0x7F..) + 0x7F..) | t) is clear exactly when the byte of t is 0)
+CCL_HD uint32_t eq_nibble(uint32_t a, uint32_t b)
+{
+    const uint32_t t = a ^ b;
+    const uint32_t m = ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u;
+    return ((m >> 7) * 0x10204080u) >> 28;
+}
 // 16 bytes -> 16 object bits (bit i = byte i > T), c as in gt_nibble
 CCL_HD uint32_t gt_mask16(const uint8_t *src, uint32_t c)
 {
@@ -588,23 +596,29 @@ template <class C> struct Tile {
             cta_sync();
             for (int q = tid; q < C::TH * C::NW; q += C::NT) {
                 const int r = q / C::NW, w = q % C::NW;
+                // 32 bytes of row r and of row r-1 as words (byte i of word k = column 32w+4k+i),
+                // and the bytes just outside them; a byte outside the tile reads as 0, which
+                // equals no object byte
+                const uint32_t *cur = reinterpret_cast<const uint32_t *>(&s.raw[r][32 * w]);
+                const uint32_t *up = reinterpret_cast<const uint32_t *>(&s.raw[r > 0 ? r - 1 : 0][32 * w]);
+                const uint32_t upm = r > 0 ? 0xFFFFFFFFu : 0u;
+                const uint32_t lb = (w > 0) ? s.raw[r][32 * w - 1] : 0u;
+                const uint32_t ulb = (w > 0 && r > 0) ? s.raw[r - 1][32 * w - 1] : 0u;
+                const uint32_t urb = (w + 1 < C::NW && r > 0) ? s.raw[r - 1][32 * w + 32] : 0u;
                 uint32_t obj = 0, eqL = 0, eqUL = 0, eqU = 0, eqUR = 0;
-                for (int b = 0; b < 32; b++) {
-                    const int x = w * 32 + b;
-                    const uint8_t v = s.raw[r][x];
-                    if (!v)
-                        continue;
-                    obj |= 1u << b;
-                    if (x > 0 && s.raw[r][x - 1] == v)
-                        eqL |= 1u << b;
-                    if (r > 0) {
-                        if (x > 0 && s.raw[r - 1][x - 1] == v)
-                            eqUL |= 1u << b;
-                        if (s.raw[r - 1][x] == v)
-                            eqU |= 1u << b;
-                        if (x + 1 < C::TW && s.raw[r - 1][x + 1] == v)
-                            eqUR |= 1u << b;
-                    }
+                uint32_t cprev = lb << 24, uprev = ulb << 24;  // the byte before word k, in byte 3
+                CCL_UNROLL
+                for (int k = 0; k < 8; k++) {
+                    const uint32_t v = cur[k], u = up[k] & upm;
+                    const uint32_t un = (k < 7) ? (up[k + 1] & upm) : urb;
+                    const uint32_t nz = gt_nibble(v, 0xFFFFFFFFu);
+                    obj |= nz << (4 * k);
+                    eqL |= (eq_nibble(v, (v << 8) | (cprev >> 24)) & nz) << (4 * k);
+                    eqUL |= (eq_nibble(v, (u << 8) | (uprev >> 24)) & nz) << (4 * k);
+                    eqU |= (eq_nibble(v, u) & nz) << (4 * k);
+                    eqUR |= (eq_nibble(v, (u >> 8) | (un << 24)) & nz) << (4 * k);
+                    cprev = v;
+                    uprev = u;
                 }
                 s.bits[r][w] = obj;
                 s.starts[r][w] = obj & ~eqL;
@@ -1107,6 +1121,8 @@ struct EdgeItem {
     int e, b, aa, c;
     bool same_prev;
     int ce, cb, ca, cc;  // multi-class: the bytes of the four pixels
+    int pe, pm2;         // multi-class: the previous pixel's node on e's side, and the node
+                         // facing two pixels back (the previous pixel's other diagonal)
 };
 
 // item i < nh: horizontal boundary above band 1 + i / W at column i % W; else vertical
@@ -1130,6 +1146,8 @@ template <class C> CCL_HD EdgeItem load_edge_item(const Img &a, int64_t i, int64
             it.cb = r1[x];
             it.ca = (x > 0) ? r1[x - 1] : -1;
             it.cc = (x + 1 < a.W) ? r1[x + 1] : -1;
+            it.pe = (x > 0) ? top[x - 1] : -1;
+            it.pm2 = (x > 1) ? above[x - 2] : -1;
         }
     } else {
         const int64_t k = i - nh;
@@ -1150,6 +1168,8 @@ template <class C> CCL_HD EdgeItem load_edge_item(const Img &a, int64_t i, int64
             it.cb = col[(int64_t)y * a.pitch - 1];
             it.ca = (y - 1 >= yb0) ? col[(int64_t)(y - 1) * a.pitch - 1] : -1;
             it.cc = (y + 1 < yb1) ? col[(int64_t)(y + 1) * a.pitch - 1] : -1;
+            it.pe = (y - 1 >= yb0) ? me[y - 1] : -1;
+            it.pm2 = (y - 2 >= yb0) ? left[y - 2] : -1;
         }
     }
     return it;
@@ -1161,13 +1181,24 @@ template <class C> CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it)
         return;
     if constexpr (C::CLS) {
         // multi-class: join each facing pixel (and, under 8-connectivity, each diagonal one)
-        // of the same value
-        if (it.b >= 0 && it.cb == it.ce)
+        // of the same value.  A node has one value, so a pair is the same pair as one the
+        // previous pixel along the edge formed when that pixel has the same node e and n is
+        // one of its facing nodes (two back, one back, this one); that pair was joined there
+        // (or skipped the same way, back to where it was joined).
+        const bool prev = it.pe == it.e;
+        auto fresh = [&](int n) {
+            return !(prev && (n == it.b || n == it.aa || (C::CONN == 8 && n == it.pm2)));
+        };
+        const bool jb = it.b >= 0 && it.cb == it.ce;
+        if (jb && (C::CONN == 8 ? fresh(it.b) : !(prev && it.b == it.aa)))
             rem_unite_g(a.P, a.nP, it.e, it.b, a.status);
         if (C::CONN == 8) {
-            if (it.aa >= 0 && it.ca == it.ce)
+            const bool ja = it.aa >= 0 && it.ca == it.ce && !(jb && it.aa == it.b);
+            if (ja && fresh(it.aa))
                 rem_unite_g(a.P, a.nP, it.e, it.aa, a.status);
-            if (it.c >= 0 && it.cc == it.ce)
+            const bool jc = it.c >= 0 && it.cc == it.ce && !(jb && it.c == it.b) &&
+                            !(it.aa >= 0 && it.ca == it.ce && it.c == it.aa);
+            if (jc && fresh(it.c))
                 rem_unite_g(a.P, a.nP, it.e, it.c, a.status);
         }
         return;

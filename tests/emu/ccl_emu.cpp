@@ -406,6 +406,9 @@ extern "C" {
 // threshold of the object test (object = byte > thr) for the following emu_label calls
 void emu_set_threshold(int32_t thr) { g_emu_thr = thr; }
 
+// the 4-byte equality test of the multi-class load phase
+uint32_t emu_eq_nibble(uint32_t a, uint32_t b) { return ccl::eq_nibble(a, b); }
+
 // the 16-byte object test of the load phase, for an exhaustive check of its arithmetic
 uint32_t emu_gt_mask16(const uint8_t *src, int32_t thr)
 {

@@ -54,6 +54,8 @@ class Emu:
         self.lib.emu_set_threshold.argtypes = [ctypes.c_int32]
         self.lib.emu_gt_mask16.argtypes = [ctypes.c_void_p, ctypes.c_int32]
         self.lib.emu_gt_mask16.restype = ctypes.c_uint32
+        self.lib.emu_eq_nibble.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+        self.lib.emu_eq_nibble.restype = ctypes.c_uint32
 
     def gt_mask16(self, src16: np.ndarray, threshold: int) -> int:
         """The load phase's test of 16 bytes: bit i set when byte i > threshold."""

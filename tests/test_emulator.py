@@ -101,3 +101,26 @@ def test_emulated_threshold_labelling_matches_oracle():
                 lab, k, st = e.label(img, seed=t, shape=shape, threshold=t, pitch=pitch)
                 exp, ek = (ref4, rk4) if conn == 4 else (ref, rk)
                 assert st == 0 and k == ek and np.array_equal(lab, exp), (h, w, t, shape)
+
+
+def test_byte_equality_test_of_the_class_load():
+    """The multi-class load compares 4 bytes at a time (a zero-byte test of a ^ b).  Checked
+    for every pair of byte values in every byte position, with random other bytes."""
+    sys.path.insert(0, HERE)
+    import numpy as np
+
+    from emu import emu
+
+    e = emu.Emu(emu.build(sanitize=False))
+    rng = np.random.default_rng(2)
+    vals = np.arange(256, dtype=np.uint32)
+    for pos in range(4):
+        for a in range(256):
+            others_a = int(rng.integers(0, 1 << 32)) & ~(0xFF << (8 * pos))
+            others_b = int(rng.integers(0, 1 << 32)) & ~(0xFF << (8 * pos))
+            for b in vals[::17].tolist() + [a, (a + 1) & 255, a ^ 128]:
+                wa = others_a | (a << (8 * pos))
+                wb = others_b | (b << (8 * pos))
+                got = e.lib.emu_eq_nibble(wa, wb)
+                exp = sum(1 << i for i in range(4) if (wa >> (8 * i)) & 255 == (wb >> (8 * i)) & 255)
+                assert got == exp, (pos, hex(wa), hex(wb), got, exp)
