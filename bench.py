@@ -286,15 +286,22 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the host-buffer entry point (pinned memory), outside the timed region
     host_imgs = [t.cpu().pin_memory() for _, t in imgs]
     host_labs = [torch.empty(tuple(t.shape), dtype=torch.int32).pin_memory() for _, t in imgs]
-    kk = ctypes.c_int32(0)
+
+    # two streams, images alternating, so that one image's label download overlaps the next
+    # image's upload and labelling (each copy direction runs at about 200 GB/s)
+    e2e_streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    e2e_sptr = [ctypes.c_void_p(st.cuda_stream) for st in e2e_streams]
+    host_k = torch.zeros(len(host_imgs), dtype=torch.int32).pin_memory()
 
     def e2e_step():
-        for hi, hl in zip(host_imgs, host_labs):
+        for i, (hi, hl) in enumerate(zip(host_imgs, host_labs)):
             H, W = hi.shape
-            rc = lib.ccl_label_host(hi.data_ptr(), H, W, hi.stride(0), args.connectivity, hl.data_ptr(),
-                                    ctypes.byref(kk), sptr)
+            rc = lib.ccl_label_host_async(hi.data_ptr(), H, W, hi.stride(0), args.connectivity, hl.data_ptr(),
+                                          ctypes.c_void_p(host_k.data_ptr() + 4 * i), e2e_sptr[i % 2])
             if rc != 0:
-                raise RuntimeError(f"ccl_label_host: {ccl.ccl_status_string(rc)}")
+                raise RuntimeError(f"ccl_label_host_async: {ccl.ccl_status_string(rc)}")
+        for st in e2e_streams:
+            st.synchronize()
 
     e2e_step()
     e2e_steps = max(1, min(args.steps, 5))
@@ -306,7 +313,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
     for i, hl in enumerate(host_labs):
-        if int(hl.max()) != ks[i]:
+        if int(hl.max()) != ks[i] or int(host_k[i]) != ks[i]:
             raise RuntimeError("host-buffer labels disagree with the device run")
 
     if rank != 0:
@@ -344,7 +351,8 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": round(aggregate_gpx_s(px_per_step, world, e2e_s), 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(t.numel() for t in host_imgs)),
                 "d2h_bytes_per_step": int(sum(4 * t.numel() + 4 for t in host_labs)),
-                "api": "ccl_label_host (pinned host buffers, copies inside the timed region)"},
+                "api": "ccl_label_host_async on two streams, images alternating (pinned host buffers, "
+                       "copies inside the timed region, both streams synchronised at the end of each step)"},
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline:

@@ -122,6 +122,20 @@ int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pi
                        int32_t connectivity, int32_t *labels_host, int32_t *num_components,
                        ccl_stream_t stream);
 
+/*
+ * ccl_label_host_async - ccl_label_host without waiting: the upload, the labelling, the
+ * download of the labels and of K are enqueued on `stream` and the call returns.  The
+ * results are valid once the stream has reached this point (cudaStreamSynchronize, an
+ * event).  Host buffers should be pinned (page-locked) for the copies to run
+ * asynchronously and to overlap work on other streams; num_components_host (pinned int32,
+ * or NULL) receives K.  The device status word is not read (see ccl_device_status).  Calls
+ * on the same stream reuse that stream's device buffers in order; use several streams to
+ * overlap the copies of one image with the work on another.
+ */
+int32_t ccl_label_host_async(const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch_bytes,
+                             int32_t connectivity, int32_t *labels_host,
+                             int32_t *num_components_host, ccl_stream_t stream);
+
 /* One image of a batch: device pointers, same conventions as ccl_label. */
 typedef struct {
     const uint8_t *img;

@@ -74,6 +74,7 @@ _SIGS = {
     "ccl_label_async": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
     "ccl_label_static": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
     "ccl_label_host": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
+    "ccl_label_host_async": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
     "ccl_label_batch": ([_P, _I32, _I32, _P, _P], _I32),
     "ccl_label_threshold": ([_P, _I32, _I32, _I64, _I32, _I32, _P, _P, _P], _I32),
     "ccl_label_batch_threshold": ([_P, _I32, _I32, _I32, _P, _P], _I32),
@@ -147,6 +148,12 @@ def ccl_label_static(img, H, W, pitch_bytes, connectivity, labels, num_component
 
 def ccl_label_host(img_host, H, W, pitch_bytes, connectivity, labels_host, num_components, stream) -> int:
     return lib().ccl_label_host(img_host, H, W, pitch_bytes, connectivity, labels_host, num_components, stream)
+
+
+def ccl_label_host_async(img_host, H, W, pitch_bytes, connectivity, labels_host, num_components_host,
+                         stream) -> int:
+    return lib().ccl_label_host_async(img_host, H, W, pitch_bytes, connectivity, labels_host,
+                                      num_components_host, stream)
 
 
 def ccl_label_batch(imgs, n, connectivity, num_components_dev, stream) -> int:

@@ -301,27 +301,19 @@ int32_t ccl_label_classes(const uint8_t *img, int32_t H, int32_t W, int64_t pitc
     return label_sync(img, H, W, pitch_bytes, connectivity | CONN_CLASSES, 0, labels, num_components, stream);
 }
 
-int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch_bytes,
-                       int32_t connectivity, int32_t *labels_host, int32_t *num_components,
-                       ccl_stream_t stream)
+namespace {
+
+// Upload, label and download one image through the stream's workspace (which also holds the
+// device copies of the image and the labels); K is left at *k_dev_out (device).
+int32_t host_enqueue(const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch_bytes, int32_t connectivity,
+                     int32_t *labels_host, cudaStream_t s, Workspace **w_out, int32_t **k_dev_out)
 {
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (connectivity & CONN_CLASSES)
-        return CCL_ERR_INVALID_ARGUMENT;
-    int32_t rc = check_args(img_host, H, W, pitch_bytes, connectivity, labels_host);
-    if (rc != CCL_OK)
-        return rc;
-    if (H == 0 || W == 0) {
-        if (num_components)
-            *num_components = 0;
-        return CCL_OK;
-    }
     const Layout L = main_layout(H, W, connectivity);
     const int64_t dpitch = (W + 15) & ~(int64_t)15;
     const int64_t img_bytes = align256((int64_t)H * dpitch);
     const int64_t lab_bytes = align256((int64_t)H * W * 4);
     Workspace *w = nullptr;
-    rc = get_workspace(s, HDR + L.bytes + img_bytes + lab_bytes, &w);
+    int32_t rc = get_workspace(s, HDR + L.bytes + img_bytes + lab_bytes, &w);
     if (rc != CCL_OK)
         return rc;
     char *base = static_cast<char *>(w->dev);
@@ -338,11 +330,61 @@ int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pi
     e = cudaMemcpyAsync(labels_host, d_lab, (size_t)H * W * 4, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess)
         return map_cuda(e);
+    *w_out = w;
+    *k_dev_out = k_dev;
+    return CCL_OK;
+}
+
+}  // namespace
+
+int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch_bytes,
+                       int32_t connectivity, int32_t *labels_host, int32_t *num_components,
+                       ccl_stream_t stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (connectivity & CONN_CLASSES)
+        return CCL_ERR_INVALID_ARGUMENT;
+    int32_t rc = check_args(img_host, H, W, pitch_bytes, connectivity, labels_host);
+    if (rc != CCL_OK)
+        return rc;
+    if (H == 0 || W == 0) {
+        if (num_components)
+            *num_components = 0;
+        return CCL_OK;
+    }
+    Workspace *w = nullptr;
+    int32_t *k_dev = nullptr;
+    rc = host_enqueue(img_host, H, W, pitch_bytes, connectivity, labels_host, s, &w, &k_dev);
+    if (rc != CCL_OK)
+        return rc;
     int32_t k = 0;
     rc = read_k_and_status(w, k_dev, &k, s);
     if (rc == CCL_OK && num_components)
         *num_components = k;
     return rc;
+}
+
+int32_t ccl_label_host_async(const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch_bytes,
+                             int32_t connectivity, int32_t *labels_host, int32_t *num_components_host,
+                             ccl_stream_t stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (connectivity & CONN_CLASSES)
+        return CCL_ERR_INVALID_ARGUMENT;
+    int32_t rc = check_args(img_host, H, W, pitch_bytes, connectivity, labels_host);
+    if (rc != CCL_OK)
+        return rc;
+    if (H == 0 || W == 0) {
+        if (num_components_host)
+            *num_components_host = 0;
+        return CCL_OK;
+    }
+    Workspace *w = nullptr;
+    int32_t *k_dev = nullptr;
+    rc = host_enqueue(img_host, H, W, pitch_bytes, connectivity, labels_host, s, &w, &k_dev);
+    if (rc != CCL_OK || !num_components_host)
+        return rc;
+    return map_cuda(cudaMemcpyAsync(num_components_host, k_dev, 4, cudaMemcpyDeviceToHost, s));
 }
 
 }  // extern "C"

@@ -130,3 +130,25 @@ def test_batch_graph_replay(ccl):
     for im, o, k in zip(imgs, outs2, ks2.cpu().numpy()):
         ref, rk = oracle.cclremsp(im)
         assert k == rk and np.array_equal(o.cpu().numpy(), ref)
+
+
+def test_host_async_two_streams():
+    import torch
+
+    imgs = [synth.bernoulli(900 + 37 * i, 1300 - 41 * i, 0.4 + 0.05 * i, 30 + i) for i in range(5)]
+    pinned = [torch.from_numpy(im).pin_memory() for im in imgs]
+    outs = [torch.full(im.shape, -1, dtype=torch.int32).pin_memory() for im in imgs]
+    ks = torch.full((len(imgs),), -1, dtype=torch.int32).pin_memory()
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    lib = __import__("paper_1606_05973_gb300").lib()
+    for i, (p, o) in enumerate(zip(pinned, outs)):
+        H, W = p.shape
+        rc = lib.ccl_label_host_async(p.data_ptr(), H, W, W, 8, o.data_ptr(),
+                                      ctypes.c_void_p(ks.data_ptr() + 4 * i),
+                                      ctypes.c_void_p(streams[i % 2].cuda_stream))
+        assert rc == 0, rc
+    for st in streams:
+        st.synchronize()
+    for i, im in enumerate(imgs):
+        ref, rk = oracle.cclremsp(im)
+        assert int(ks[i]) == rk and np.array_equal(outs[i].numpy(), ref), i
