@@ -864,31 +864,29 @@ template <class C> struct Tile {
             // one step of Rem's union (Algorithm 2 with Algorithm 8's compare-and-swap
             // writes, as in rem_unite_g).  A warp vote ends the loop, so the lanes stay
             // converged and each pass is one short predicated block per part.
-            int last_a = -1, last_b = -1, rx = -1, ry = -1;
+            // An event at bit b joins the A run covering column b or b-1 with the B run
+            // covering b or b-1; with m = 1 << b, the runs covering b and b-1 are counted
+            // by the masks m | (m - 1) and m - 1 (b = 0: the word to the left).  An event
+            // that joins the same two runs as the thread's previous one is skipped (its pass
+            // is one the other lanes run anyway).
+            uint32_t last = 0xFFFFFFFFu;
+            int rx = -1, ry = -1;
             for (int it = 0;; it++) {
                 if (rx < 0 && (ev1 | ev2)) {
-                    const int b = ctz32(ev1 | ev2);
-                    int na, nb, x, y;
-                    if ((ev1 >> b) & 1u) {
-                        ev1 &= ev1 - 1u;
-                        const int ba = (C::CONN == 4 || ((A >> b) & 1u)) ? b : b - 1;
-                        na = baseA + popc32(sA & mask_upto(ba));
-                        nb = baseB + popc32(sB & mask_upto(b));
-                        x = nb;
-                        y = na;
-                    } else {
-                        ev2 &= ev2 - 1u;
-                        const int bb = (C::CONN == 4) ? b : b - 1;
-                        na = baseA + popc32(sA & mask_upto(b));
-                        nb = baseB + popc32(sB & mask_upto(bb));
-                        x = na;
-                        y = nb;
-                    }
-                    if (na != last_a || nb != last_b) {
-                        last_a = na;
-                        last_b = nb;
-                        rx = CCL_CHK(x, C::RMAX, a.status);
-                        ry = CCL_CHK(y, C::RMAX, a.status);
+                    const uint32_t E = ev1 | ev2;
+                    const uint32_t m = E & (0u - E);
+                    const uint32_t below = m - 1u, upto = below | m;
+                    const bool first = (ev1 & m) != 0u;  // an event of the first kind
+                    ev1 &= ~m;
+                    ev2 &= ~m;
+                    const uint32_t mA = (C::CONN == 8 && first && !(A & m)) ? below : upto;
+                    const uint32_t mB = (C::CONN == 8 && !first) ? below : upto;
+                    const int na = baseA + popc32(sA & mA), nb = baseB + popc32(sB & mB);
+                    const uint32_t key = ((uint32_t)na << 16) | (uint32_t)nb;
+                    if (key != last) {
+                        last = key;
+                        rx = CCL_CHK(nb, C::RMAX, a.status);
+                        ry = CCL_CHK(na, C::RMAX, a.status);
                     }
                 }
                 if (!warp_ballot(rx >= 0 || (ev1 | ev2) != 0u))
