@@ -162,6 +162,15 @@ CCL_HD int at_cas(int *a, int cmp, int val)
     return cmp;
 #endif
 }
+CCL_HD int at_add(int *a, int v)
+{
+#if defined(__CUDA_ARCH__)
+    return atomicAdd(a, v);
+#else
+    emu_yield();
+    return __atomic_fetch_add(a, v, __ATOMIC_SEQ_CST);
+#endif
+}
 CCL_HD void at_or(uint32_t *a, uint32_t v)
 {
 #if defined(__CUDA_ARCH__)
@@ -432,6 +441,8 @@ template <class C> struct SmemCls<C, true> {
 };
 template <class C> struct SmemL : SmemRuns<C>, SmemCls<C> {
     uint32_t par[C::RMAX];           // union-find parents (see above)
+    int ucount[33];                  // union phase: units per event count, then bucket starts
+    uint16_t uorder[C::NT];          // union phase: units of a chunk by event count
     uint32_t rootbits[C::TH][C::NW]; // first pixels of the local components
     int rootpre[C::TH][C::NW];       // exclusive popcount prefix of rootbits along a row
 };
@@ -756,6 +767,42 @@ template <class C> struct Tile {
     // up-right) the columns x where byte(B, x) == byte(A, x+d) != 0.  Every such contact
     // joins the B run covering x with the A run covering x+d; a contact is an event unless
     // the contact one column to the left (same d) joins the same two runs.
+    // The joins of unit u (strip boundary u / NW, word u % NW), as two event masks, with
+    // what is needed to turn an event into the two runs it joins.
+    // Rows A = last row of strip st-1 and B = first row of strip st.  Every pair of
+    // single-row runs (one in A, one in B) that are adjacent is found exactly once:
+    // 8: the B run starts where A has a pixel at that column or one to the left, or the A
+    //    run starts one column right of a B pixel;
+    // 4: the B run starts under an A pixel, or the A run starts over a B pixel that does
+    //    not start a B run.
+    // The run of strip s covering bit b of the word (b = -1: the last bit of the word to
+    // the left) is base + popcount(starts & bits 0..b).
+    struct UnitEvents {
+        uint32_t ev1 = 0, ev2 = 0, A = 0, sA = 0, sB = 0;
+        int baseA = 0, baseB = 0;
+    };
+    CCL_HD static UnitEvents unit_events(const SL &s, int u)
+    {
+        UnitEvents e;
+        const int st = u / C::NW, w = u % C::NW;
+        if (u < C::NS * C::NW && st > 0) {
+            const int ra = C::RPS * st - 1, rb = C::RPS * st;
+            e.A = s.bits[ra][w];
+            const uint32_t B = s.bits[rb][w];
+            const uint32_t Ap = (w > 0) ? (s.bits[ra][w - 1] >> 31) : 0u;
+            const uint32_t Bp = (w > 0) ? (s.bits[rb][w - 1] >> 31) : 0u;
+            const uint32_t Ash = (e.A << 1) | Ap, Bsh = (B << 1) | Bp;
+            const uint32_t sBr = B & ~Bsh, sAr = e.A & ~Ash;  // single-row run starts
+            e.ev1 = (C::CONN == 8) ? (sBr & (e.A | Ash)) : (sBr & e.A);
+            e.ev2 = (C::CONN == 8) ? (sAr & Bsh) : (sAr & B & ~sBr);
+            e.sA = s.starts[st - 1][w];
+            e.sB = s.starts[st][w];
+            e.baseA = (st - 1) * C::RC + s.rpre[st - 1][w] - 1;
+            e.baseB = st * C::RC + s.rpre[st][w] - 1;
+        }
+        return e;
+    }
+
     CCL_HD static void unions_cls(const Img &a, SL &s, int tid)
     {
         if constexpr (C::CLS) {
@@ -834,31 +881,30 @@ template <class C> struct Tile {
         // every thread runs the same number of outer passes (NT is a multiple of 32), so
         // whole warps reach the votes below
         for (int u0 = 0; u0 < C::NS * C::NW; u0 += C::NT) {
-            const int u = u0 + tid, st = u / C::NW, w = u % C::NW;
-            uint32_t ev1 = 0, ev2 = 0, A = 0, sA = 0, sB = 0;
-            int baseA = 0, baseB = 0;
-            if (u < C::NS * C::NW && st > 0) {
-                // A: last row of strip st-1, B: first row of strip st
-                const int ra = C::RPS * st - 1, rb = C::RPS * st;
-                A = s.bits[ra][w];
-                const uint32_t B = s.bits[rb][w];
-                const uint32_t Ap = (w > 0) ? (s.bits[ra][w - 1] >> 31) : 0u;
-                const uint32_t Bp = (w > 0) ? (s.bits[rb][w - 1] >> 31) : 0u;
-                const uint32_t Ash = (A << 1) | Ap, Bsh = (B << 1) | Bp;
-                const uint32_t sBr = B & ~Bsh, sAr = A & ~Ash;  // single-row run starts
-                // 8: the B run starts where A has a pixel at that column or one to the left,
-                //    or the A run starts one column right of a B pixel
-                // 4: the B run starts under an A pixel, or the A run starts over a B pixel
-                //    that does not start a B run
-                ev1 = (C::CONN == 8) ? (sBr & (A | Ash)) : (sBr & A);
-                ev2 = (C::CONN == 8) ? (sAr & Bsh) : (sAr & B & ~sBr);
-                // run of strip s covering bit b of this word (b = -1: the last bit of the
-                // word to the left) is base + popcount(starts & bits 0..b)
-                sA = s.starts[st - 1][w];
-                sB = s.starts[st][w];
-                baseA = (st - 1) * C::RC + s.rpre[st - 1][w] - 1;
-                baseB = st * C::RC + s.rpre[st][w] - 1;
+            // A warp's loop below runs as long as its busiest lane, so the chunk's units are
+            // first ordered by their number of events (a counting sort) and thread t takes
+            // the t-th: each warp then holds units of about the same length.
+            UnitEvents e = unit_events(s, u0 + tid);
+            for (int q = tid; q < 33; q += C::NT)
+                s.ucount[q] = 0;
+            cta_sync();
+            const int key = popc32(e.ev1 | e.ev2);
+            const int rank = at_add(&s.ucount[key], 1);
+            cta_sync();
+            if (tid < 32) {
+                const int c = s.ucount[tid];
+                const int incl = warp_incl_sum(c, 32);
+                s.ucount[tid] = incl - c;
+                if (tid == 31)
+                    s.ucount[32] = incl;
             }
+            cta_sync();
+            s.uorder[s.ucount[key] + rank] = (uint16_t)tid;
+            cta_sync();
+            e = unit_events(s, u0 + s.uorder[tid]);
+            uint32_t ev1 = e.ev1, ev2 = e.ev2;
+            const uint32_t A = e.A, sA = e.sA, sB = e.sB;
+            const int baseA = e.baseA, baseB = e.baseB;
             // One loop for all of this thread's joins, run in step by the whole warp: each
             // pass takes the thread's next event if it has no join in progress, then runs
             // one step of Rem's union (Algorithm 2 with Algorithm 8's compare-and-swap

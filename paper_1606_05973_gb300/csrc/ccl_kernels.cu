@@ -106,6 +106,12 @@ template <class C> static cudaError_t init_cfg()
 {
     cudaError_t err = cudaFuncSetAttribute(k_tile_local<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)sizeof(SmemL<C>));
+    // the tile kernels are sized for 8 CTAs per SM; ask for the shared-memory carveout that
+    // holds them
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_tile_local<C>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_tile_local_batch<C>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_final<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmemF<C>));
     if (err == cudaSuccess)
