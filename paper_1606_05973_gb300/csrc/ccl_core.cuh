@@ -874,10 +874,14 @@ template <class C> struct Tile {
 
     CCL_HD static void unions(const Img &a, SL &s, int tid)
     {
-        if constexpr (C::CLS) {
+        if constexpr (C::CLS)
             unions_cls(a, s, tid);
-            return;
-        }
+        else
+            unions_bin(a, s, tid);
+    }
+
+    CCL_HD static void unions_bin(const Img &a, SL &s, int tid)
+    {
         // every thread runs the same number of outer passes (NT is a multiple of 32), so
         // whole warps reach the votes below
         for (int u0 = 0; u0 < C::NS * C::NW; u0 += C::NT) {
