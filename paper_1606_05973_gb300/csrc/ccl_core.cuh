@@ -781,6 +781,24 @@ template <class C> struct Tile {
         uint32_t ev1 = 0, ev2 = 0, A = 0, sA = 0, sB = 0;
         int baseA = 0, baseB = 0;
     };
+
+    // Events of a word that can join a new pair of strip runs.  Both runs an event at
+    // column x joins cover a column in x-1..x, so two consecutive events y < x join the
+    // same two strip runs when neither strip has a run start in columns y..x; such an x
+    // is dropped (the kept event before it joins that pair).  With S the run starts of
+    // both strips, x is kept when flag(x) holds:
+    //   flag(x) = S(x) | (S(x-1) & E(x-1)) | (flag(x-1) & !E(x-1)),  flag(-1) = 1,
+    // a carry chain (generate G = S | (S & E) << 1, propagate = no event one column to
+    // the left), so one 64-bit addition evaluates it for all 32 columns.  Bit j of the
+    // 64-bit words stands for column j - 1.
+    CCL_HD static uint32_t new_pair_events(uint32_t E, uint32_t S)
+    {
+        const uint64_t G = ((uint64_t)(S | ((S & E) << 1)) << 1) | 1u;
+        const uint64_t P = ~((uint64_t)E << 2);
+        const uint64_t A = G | P;
+        const uint64_t carry = (A + G) ^ A ^ G;  // carry into bit j = flag(column j - 2)
+        return E & (uint32_t)(carry >> 2);
+    }
     CCL_HD static UnitEvents unit_events(const SL &s, int u)
     {
         UnitEvents e;
@@ -797,6 +815,9 @@ template <class C> struct Tile {
             e.ev2 = (C::CONN == 8) ? (sAr & Bsh) : (sAr & B & ~sBr);
             e.sA = s.starts[st - 1][w];
             e.sB = s.starts[st][w];
+            const uint32_t keep = new_pair_events(e.ev1 | e.ev2, e.sA | e.sB);
+            e.ev1 &= keep;
+            e.ev2 &= keep;
             e.baseA = (st - 1) * C::RC + s.rpre[st - 1][w] - 1;
             e.baseB = st * C::RC + s.rpre[st][w] - 1;
         }
