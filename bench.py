@@ -7,8 +7,15 @@ Workload (default ``sweep8192``): six 8192 x 8192 uint8 images - Bernoulli p in
 with the inputs already resident in HBM.  ``big21568`` labels the three ~465 MB images
 (sigma=16 blobs, Bernoulli(0.6), serpentine); ``small1024`` the 1024 x 1024 case.
 
+The images of a step alternate over two streams (``--streams``) with the cooperative
+global kernel capped at one CTA per SM (``--global-ctas-per-sm``,
+``ccl_set_global_ctas_per_sm``), so that one image's tile pass runs beside another's
+global pass.  The line also carries the same steps on one stream with the library's
+default grid (``one_stream``), and per-kernel launch times taken on one stream.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sweep8192|big21568|small1024]
+                    [--workload sweep8192|big21568|small1024] [--streams S]
+                    [--global-ctas-per-sm N]
 
 Under torchrun each rank labels its own copy of the workload (independent replicas, no
 collective on the data path); rank 0 prints one JSON line with the max time over ranks.
@@ -238,12 +245,21 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     sptr = ctypes.c_void_p(stream.cuda_stream)
     px_per_step = sum(t.shape[0] * t.shape[1] for _, t in imgs)
+    # images alternate over `streams` streams (the library keeps one workspace per stream),
+    # so one image's tile pass can run beside another's global pass
+    side = [torch.cuda.Stream(device=dev) for _ in range(args.streams - 1)]
+    step_streams = [stream] + side
+    step_sptr = [ctypes.c_void_p(st.cuda_stream) for st in step_streams]
+    if args.global_ctas_per_sm is not None:
+        if lib.ccl_set_global_ctas_per_sm(args.global_ctas_per_sm) != 0:
+            raise RuntimeError("ccl_set_global_ctas_per_sm rejected its argument")
 
-    def step():
+    def step(nstreams=None):
+        ns = nstreams or len(step_streams)
         for i, (_, t) in enumerate(imgs):
             H, W = t.shape
             rc = lib.ccl_label_async(t.data_ptr(), H, W, t.stride(0), args.connectivity, labels[i].data_ptr(),
-                                     kdev.data_ptr() + 4 * i, sptr)
+                                     kdev.data_ptr() + 4 * i, step_sptr[i % ns])
             if rc != 0:
                 raise RuntimeError(f"ccl_label_async: {ccl.ccl_status_string(rc)}")
 
@@ -251,9 +267,10 @@ def run_ours(args, rank, world, local_rank):
         step()
     torch.cuda.synchronize()
     flags = ctypes.c_int32(0)
-    lib.ccl_device_status(sptr, ctypes.byref(flags))
-    if flags.value:
-        raise RuntimeError(f"device status {flags.value} after warm-up")
+    for sp in step_sptr:
+        lib.ccl_device_status(sp, ctypes.byref(flags))
+        if flags.value:
+            raise RuntimeError(f"device status {flags.value} after warm-up")
 
     def barrier():
         if world > 1:
@@ -267,13 +284,34 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
         e0.record(stream)
+        for st in side:
+            st.wait_stream(stream)
         for _ in range(args.steps):
             step()
+        for st in side:
+            stream.wait_stream(st)
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms, world, dev)
+
+    # the same steps on one stream with the library's default global grid, for comparison
+    lib.ccl_set_global_ctas_per_sm(0)
+    o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        step(nstreams=1)
+    barrier()
+    torch.cuda.synchronize()
+    o0.record(stream)
+    for _ in range(args.steps):
+        step(nstreams=1)
+    o1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_one = max_over_ranks(o0.elapsed_time(o1), world, dev)
+    if args.global_ctas_per_sm is not None:
+        lib.ccl_set_global_ctas_per_sm(args.global_ctas_per_sm)
 
     # per-kernel device times: the same K steps again with the library's event pair around
     # every launch on its stream.  The events leave a small gap between launches (about 5%
@@ -286,7 +324,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     p0.record(stream)
     for _ in range(args.steps):
-        step()
+        step(nstreams=1)  # one stream: each launch's duration is its own
     p1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -327,6 +365,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
+    lib.ccl_set_global_ctas_per_sm(0)  # library default for the measurements below
     for i, hl in enumerate(host_labs):
         if int(hl.max()) != ks[i] or int(host_k[i]) != ks[i]:
             raise RuntimeError("host-buffer labels disagree with the device run")
@@ -355,11 +394,15 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8->int32", "data": "synthetic",
         "config": {**desc, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "streams": args.streams, "global_ctas_per_sm": args.global_ctas_per_sm or "all that fit",
                    "l2": "inputs larger than L2: 6 x 64 MiB images read and 6 x 256 MiB labels written per step"
                    if args.workload == "sweep8192" else "inputs larger than L2"},
         "roofline": roof,
         "path_roofline": {"bytes_per_px": PATH_BYTES_PER_PX, "achieved_gbs": round(path_gbs, 1),
                           "frac": round(path_gbs / peak, 4), "peak": peak, "peak_source": peak_kind},
+        "one_stream": {"value": round(aggregate_gpx_s(px_per_step, world, ms_one / args.steps * 1e-3), 2),
+                       "ms_per_step": round(ms_one / args.steps, 4),
+                       "how": "the same steps on one stream, global kernel with as many CTAs per SM as fit"},
         "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 4)} for k, v in kt.items() if v[0]},
         "kernels_pass": {"steps": args.steps, "ms_per_step": round(prof_ms / args.steps, 4),
                          "how": "a second timed pass of the same steps with an event pair around every "
@@ -706,6 +749,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["sweep8192", "big21568", "small1024"], default="sweep8192")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--streams", type=int, default=2,
+                    help="streams the images of a step alternate over (timed pass)")
+    ap.add_argument("--global-ctas-per-sm", type=int, default=1,
+                    help="cap on the global kernel's CTAs per SM during the timed pass "
+                         "(ccl_set_global_ctas_per_sm; 0 = as many as fit)")
     ap.add_argument("--connectivity", type=int, choices=[8, 4], default=8,
                     help="8 (the paper's) or 4; the reference arm supports 8 only")
     ap.add_argument("--only", default=None, help="keep one image of the workload (profiling)")

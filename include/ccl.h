@@ -258,6 +258,19 @@ int32_t ccl_device_status(ccl_stream_t stream, int32_t *flags);
 int32_t ccl_release(void);
 
 /*
+ * ccl_set_global_ctas_per_sm - how many CTAs of the cooperative boundary-merge / flatten
+ * kernel (1024 threads each; the merge of Algorithm 7's boundary loop with Algorithm 8's
+ * union, and Algorithm 3's flatten) may share one SM.  n = 0 (the default) places as many
+ * as fit (2 on GB300, every thread slot).  n = 1 leaves half of each SM's thread slots
+ * free, so that when images are labelled on two or more streams, the tile pass of one
+ * image (instruction-bound) runs beside the global pass of another (latency-bound); a
+ * single stream is then slower, since the global pass has half the threads to hide its
+ * latency.  Process-wide; applies to launches enqueued after the call.  Returns
+ * CCL_ERR_INVALID_ARGUMENT for n < 0; n above what fits is the same as 0.
+ */
+int32_t ccl_set_global_ctas_per_sm(int32_t n);
+
+/*
  * Kernel timing.  When enabled, the library records CUDA events on the launching stream
  * around each of its kernel launches; ccl_profile_read waits for them and reports, per
  * kernel, the number of launches and the summed device time since the last reset.

@@ -613,6 +613,14 @@ int32_t ccl_release(void)
     return map_cuda(e);
 }
 
+int32_t ccl_set_global_ctas_per_sm(int32_t n)
+{
+    if (n < 0)
+        return CCL_ERR_INVALID_ARGUMENT;
+    set_global_ctas_per_sm(n);
+    return CCL_OK;
+}
+
 int32_t ccl_profile_enable(int32_t on)
 {
     g_prof_on.store(on ? 1 : 0);

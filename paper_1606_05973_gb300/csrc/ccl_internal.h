@@ -57,6 +57,9 @@ cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t s
 // One-time per-process setup of kernel attributes (dynamic shared memory).
 cudaError_t kernels_init();
 
+// CTAs of the global kernel per SM (0: as many as fit); read at every launch.
+void set_global_ctas_per_sm(int n);
+
 // ---- host-side workspace (ccl_api.cu) ------------------------------------------------
 // A device workspace starts with a 256-byte header {K at 0, status word at 4, grid state
 // of the global kernel at 16}; the per-image or per-batch arrays follow.

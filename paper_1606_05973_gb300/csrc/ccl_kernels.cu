@@ -6,6 +6,7 @@
 //   k_final       one CTA per tile: label of every strip run, int32 labels (row a5)
 // The per-tile and per-segment phases live in ccl_core.cuh.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "ccl_internal.h"
@@ -95,6 +96,20 @@ void bind_workspace(Img &a, const Layout &L, void *ws)
 }
 
 static int g_num_sms = 0;
+static std::atomic<int> g_global_per_sm{0};
+
+void set_global_ctas_per_sm(int n) { g_global_per_sm.store(n); }
+
+// grid of the cooperative global kernel: `need` CTAs, at most `fit` (all resident), and at
+// most the per-SM cap times the SM count when a cap is set
+static int global_grid(int64_t need, int fit)
+{
+    const int cap = g_global_per_sm.load();
+    int64_t g = need < fit ? need : fit;
+    if (cap > 0 && g > (int64_t)cap * g_num_sms)
+        g = (int64_t)cap * g_num_sms;
+    return g < 1 ? 1 : (int)g;
+}
 
 template <class C> struct KernState {
     static int global_ctas, global_batch_ctas;
@@ -191,9 +206,7 @@ template <class C> static cudaError_t launch_label_t(const Img &a, const Layout 
     // the global kernel needs enough threads for its largest phase, and every CTA resident
     const int64_t work = (int64_t)(L.nTY - 1) * a.W + (int64_t)(L.nTX - 1) * a.H;
     const int64_t need = ((work > L.nSeg ? work : L.nSeg) + GNT - 1) / GNT;
-    int grid = (int)(need < KernState<C>::global_ctas ? need : KernState<C>::global_ctas);
-    if (grid < 1)
-        grid = 1;
+    const int grid = global_grid(need, KernState<C>::global_ctas);
     Img arg = a;
     void *args[] = {&arg};
     CCL_LAUNCH(KID_GLOBAL, cudaLaunchCooperativeKernel((const void *)k_global<C>, dim3(grid), dim3(GNT), args, 0, s));
@@ -210,9 +223,7 @@ static cudaError_t launch_batch_t(const Batch &B, int64_t tiles, int64_t items, 
         return cudaErrorInvalidValue;
     CCL_LAUNCH(KID_TILE_LOCAL, launch_tiles_b(k_tile_local_batch<C>, (int)tiles, C::NT, sizeof(SmemL<C>), s, B));
     const int64_t need = ((items > segs ? items : segs) + GNT - 1) / GNT;
-    int grid = (int)(need < KernState<C>::global_batch_ctas ? need : KernState<C>::global_batch_ctas);
-    if (grid < 1)
-        grid = 1;
+    const int grid = global_grid(need, KernState<C>::global_batch_ctas);
     Batch arg = B;
     void *args[] = {&arg};
     CCL_LAUNCH(KID_GLOBAL,

@@ -152,3 +152,38 @@ def test_host_async_two_streams():
     for i, im in enumerate(imgs):
         ref, rk = oracle.cclremsp(im)
         assert int(ks[i]) == rk and np.array_equal(outs[i].numpy(), ref), i
+
+
+def test_global_ctas_per_sm_cap_and_two_streams(ccl):
+    """With the global kernel capped at one CTA per SM (a grid of fewer CTAs than its
+    work items and segments, so its loops wrap), images labelled on two streams at once
+    match the oracle; a negative cap is rejected and the default is restored after."""
+    import torch
+
+    lib = ccl.lib()
+    assert lib.ccl_set_global_ctas_per_sm(-1) == 1
+    imgs = [synth.bernoulli(3000, 4000, p, 40 + i) for i, p in enumerate((0.3, 0.5, 0.6, 0.7))]
+    refs = [oracle.cclremsp(im) for im in imgs]
+    dev = [torch.from_numpy(im).cuda() for im in imgs]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    try:
+        for cap in (1, 0):
+            assert lib.ccl_set_global_ctas_per_sm(cap) == 0
+            outs = [torch.empty(im.shape, dtype=torch.int32, device="cuda") for im in imgs]
+            kd = torch.zeros(len(imgs), dtype=torch.int32, device="cuda")
+            for rep in range(3):
+                for i, t in enumerate(dev):
+                    st = streams[i % 2]
+                    rc = lib.ccl_label_async(t.data_ptr(), t.shape[0], t.shape[1], t.stride(0), 8,
+                                             outs[i].data_ptr(), ctypes.c_void_p(kd.data_ptr() + 4 * i),
+                                             ctypes.c_void_p(st.cuda_stream))
+                    assert rc == 0
+            torch.cuda.synchronize()
+            for (ref, rk), o, k in zip(refs, outs, kd.cpu().tolist()):
+                assert k == rk and np.array_equal(o.cpu().numpy(), ref)
+            flags = ctypes.c_int32(0)
+            for st in streams:
+                assert lib.ccl_device_status(ctypes.c_void_p(st.cuda_stream), ctypes.byref(flags)) == 0
+                assert flags.value == 0
+    finally:
+        lib.ccl_set_global_ctas_per_sm(0)
