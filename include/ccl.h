@@ -271,6 +271,20 @@ int32_t ccl_release(void);
 int32_t ccl_set_global_ctas_per_sm(int32_t n);
 
 /*
+ * ccl_set_tile_policy - the tile shape of the 8-connected path (the partitions that
+ * Algorithm 7 labels independently before its boundary merge).  policy 0 (the default)
+ * chooses by size: images of at most 3072 x 3072 pixels take 64 x 128 tiles, larger ones
+ * 64 x 256 (an offline sweep of tile shapes over sizes and contents:
+ * paper_1606_05973_gb300/tile_sweep.py): narrow tiles pay while wide ones would leave SMs
+ * idle.  A batch takes one shape for all its images, by the same rule on its total pixel
+ * count (a batch of 4096 images up to 2048 x 2048 takes wide tiles).  1 = always
+ * 64 x 256, 2 = always 64 x 128 (for tests and tuning).  Labels are identical under every
+ * policy.  Process-wide; applies to calls made after it.  CCL_ERR_INVALID_ARGUMENT for
+ * other values.
+ */
+int32_t ccl_set_tile_policy(int32_t policy);
+
+/*
  * Kernel timing.  When enabled, the library records CUDA events on the launching stream
  * around each of its kernel launches; ccl_profile_read waits for them and reports, per
  * kernel, the number of launches and the summed device time since the last reset.

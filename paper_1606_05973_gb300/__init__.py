@@ -19,6 +19,7 @@ from .build import build, lib_path
 __all__ = [
     "CCLError", "CCLUnavailable", "load", "lib", "ccl_label", "ccl_label_async", "ccl_label_static",
     "ccl_label_host", "ccl_label_batch", "ccl_workspace_bytes", "ccl_device_status", "ccl_release", "ccl_set_global_ctas_per_sm",
+    "ccl_set_tile_policy",
     "ccl_profile_enable", "ccl_profile_reset", "ccl_profile_read", "ccl_status_string",
     "ccl_version", "label", "label_batch", "label_host", "kernel_times", "CCL_OK", "Server",
     "ccl_server_create", "ccl_server_submit", "ccl_server_wait", "ccl_server_get_stats",
@@ -84,6 +85,7 @@ _SIGS = {
     "ccl_device_status": ([_P, _P], _I32),
     "ccl_release": ([], _I32),
     "ccl_set_global_ctas_per_sm": ([_I32], _I32),
+    "ccl_set_tile_policy": ([_I32], _I32),
     "ccl_profile_enable": ([_I32], _I32),
     "ccl_profile_reset": ([], _I32),
     "ccl_profile_read": ([_P, _I32, _P], _I32),
@@ -191,6 +193,10 @@ def ccl_release() -> int:
 
 def ccl_set_global_ctas_per_sm(n) -> int:
     return lib().ccl_set_global_ctas_per_sm(n)
+
+
+def ccl_set_tile_policy(policy) -> int:
+    return lib().ccl_set_tile_policy(policy)
 
 
 def ccl_profile_enable(on) -> int:

@@ -215,7 +215,7 @@ int32_t ccl_workspace_bytes(int32_t H, int32_t W, int64_t *bytes)
         return CCL_OK;
     }
     int64_t mx = 0;
-    for (int conn : {8, 4, 8 | CONN_CLASSES, 4 | CONN_CLASSES}) {
+    for (int conn : {8 | CONN_WIDE, 8 | CONN_NARROW, 4, 8 | CONN_CLASSES, 4 | CONN_CLASSES}) {
         const int64_t b = main_layout(H, W, conn).bytes;
         mx = b > mx ? b : mx;
     }
@@ -393,8 +393,23 @@ namespace ccl {
 
 // Workspace bytes of a batch of m non-empty images (header, descriptors, prefixes, rank
 // offsets, CTA sums, one layout per image).
+// The tile shape of a batch (one for all its images).  Narrow tiles pay only while wide
+// ones leave SMs idle, so under the automatic policy the batch's total pixel count decides,
+// with the single-image threshold: a batch that fills the GPU takes wide tiles however
+// small its images.
+int batch_conn(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn)
+{
+    if (conn != 8)
+        return conn;
+    int64_t all = 0;
+    for (int32_t k = 0; k < m; k++)
+        all += (int64_t)imgs[keep[k]].H * imgs[keep[k]].W;
+    return resolve_conn(conn, all, 1);
+}
+
 int64_t batch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn)
 {
+    conn = batch_conn(imgs, keep, m, conn);
     int64_t o = HDR + align256((int64_t)m * (int64_t)sizeof(Img)) + align256(3 * (int64_t)(m + 1) * 8) +
                 align256((int64_t)(m + 1) * 4) + align256((int64_t)MAX_GLOBAL_CTAS * 4);
     for (int32_t k = 0; k < m; k++)
@@ -411,6 +426,7 @@ int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int
     cudaError_t e = kernels_init();
     if (e != cudaSuccess)
         return map_cuda(e);
+    conn = batch_conn(imgs, keep, m, conn);  // the same shape batch_bytes planned with
     std::vector<Layout> L(m);
     std::vector<int64_t> loff(m);
     const int64_t desc_bytes = align256((int64_t)m * (int64_t)sizeof(Img));
@@ -611,6 +627,14 @@ int32_t ccl_release(void)
     }
     g_ws.clear();
     return map_cuda(e);
+}
+
+int32_t ccl_set_tile_policy(int32_t policy)
+{
+    if (policy < 0 || policy > 2)
+        return CCL_ERR_INVALID_ARGUMENT;
+    set_tile_policy(policy);
+    return CCL_OK;
 }
 
 int32_t ccl_set_global_ctas_per_sm(int32_t n)

@@ -39,8 +39,24 @@ using MainCfg4 = Cfg<CCL_TILE_H / 2, CCL_TILE_W, CCL_TILE_NT, 4>;
 // multi-class labelling (one-row strips as well)
 using MainCfgC8 = Cfg<CCL_TILE_H / 2, CCL_TILE_W, CCL_TILE_NT, 8, true>;
 using MainCfgC4 = Cfg<CCL_TILE_H / 2, CCL_TILE_W, CCL_TILE_NT, 4, true>;
+// 8-connectivity on narrow tiles (64 x 128 by default): smaller images run faster on them
+// (tile-shape sweep, paper_1606_05973_gb300/tile_sweep.py)
+using NarrowCfg = Cfg<CCL_TILE_H, CCL_TILE_W / 2, CCL_TILE_NT, 8>;
 // Inside the library a connectivity value may carry this bit: multi-class labelling.
 constexpr int CONN_CLASSES = 0x100;
+// ... and, for 8-connectivity, one of these: the tile shape chosen (resolve_conn)
+constexpr int CONN_NARROW = 0x200;  // NarrowCfg
+constexpr int CONN_WIDE = 0x400;    // MainCfg
+// Images of at most this many pixels take narrow tiles under the automatic policy.
+constexpr int64_t NARROW_MAX_PX = (int64_t)3072 * 3072;
+
+// Tile policy (ccl_set_tile_policy): 0 = by image size, 1 = always MainCfg, 2 = always
+// NarrowCfg.  Read at every call.
+void set_tile_policy(int p);
+int tile_policy();
+// `conn` with the tile shape an image of H x W takes (8-connectivity only; other modes and
+// values that already carry a shape are returned unchanged)
+int resolve_conn(int conn, int64_t H, int64_t W);
 
 Layout main_layout(int H, int W, int conn);
 

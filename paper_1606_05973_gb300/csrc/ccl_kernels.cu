@@ -66,9 +66,25 @@ template <class C> __global__ void __launch_bounds__(C::NT, 2048 / C::NT) k_fina
     batch_final_body<C>(B, ctx, *reinterpret_cast<SmemF<C> *>(smem_raw), blockIdx.x, threadIdx.x);
 }
 
+static std::atomic<int> g_tile_policy{0};
+void set_tile_policy(int p) { g_tile_policy.store(p); }
+int tile_policy() { return g_tile_policy.load(); }
+
+int resolve_conn(int conn, int64_t H, int64_t W)
+{
+    if (conn != 8)
+        return conn;
+    switch (tile_policy()) {
+    case 1: return 8 | CONN_WIDE;
+    case 2: return 8 | CONN_NARROW;
+    default: return 8 | (H * W <= NARROW_MAX_PX ? CONN_NARROW : CONN_WIDE);
+    }
+}
+
 Layout main_layout(int H, int W, int conn)
 {
-    switch (conn) {
+    switch (resolve_conn(conn, H, W)) {
+    case 8 | CONN_NARROW: return plan_layout<NarrowCfg>(H, W);
     case 4: return plan_layout<MainCfg4>(H, W);
     case 8 | CONN_CLASSES: return plan_layout<MainCfgC8>(H, W);
     case 4 | CONN_CLASSES: return plan_layout<MainCfgC4>(H, W);
@@ -165,6 +181,8 @@ cudaError_t kernels_init()
         if (err == cudaSuccess)
             err = init_cfg<MainCfg>();
         if (err == cudaSuccess)
+            err = init_cfg<NarrowCfg>();
+        if (err == cudaSuccess)
             err = init_cfg<MainCfg4>();
         if (err == cudaSuccess)
             err = init_cfg<MainCfgC8>();
@@ -234,7 +252,8 @@ static cudaError_t launch_batch_t(const Batch &B, int64_t tiles, int64_t items, 
 
 cudaError_t launch_label(const Img &a, const Layout &L, int conn, cudaStream_t s)
 {
-    switch (conn) {
+    switch (resolve_conn(conn, a.H, a.W)) {
+    case 8 | CONN_NARROW: return launch_label_t<NarrowCfg>(a, L, s);
     case 4: return launch_label_t<MainCfg4>(a, L, s);
     case 8 | CONN_CLASSES: return launch_label_t<MainCfgC8>(a, L, s);
     case 4 | CONN_CLASSES: return launch_label_t<MainCfgC4>(a, L, s);
@@ -244,7 +263,8 @@ cudaError_t launch_label(const Img &a, const Layout &L, int conn, cudaStream_t s
 
 cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, int conn, cudaStream_t s)
 {
-    switch (conn) {
+    switch (conn) {  // a batch's shape is chosen once for all its images (batch_conn)
+    case 8 | CONN_NARROW: return launch_batch_t<NarrowCfg>(B, tiles, items, segs, s);
     case 4: return launch_batch_t<MainCfg4>(B, tiles, items, segs, s);
     case 8 | CONN_CLASSES: return launch_batch_t<MainCfgC8>(B, tiles, items, segs, s);
     case 4 | CONN_CLASSES: return launch_batch_t<MainCfgC4>(B, tiles, items, segs, s);

@@ -418,7 +418,8 @@ uint32_t emu_gt_mask16(const uint8_t *src, int32_t thr)
 // shapes, 8-connectivity: 0 = 64x256 tiles (256 threads); 1 = 4x32 (32); 2 = 8x64 (64);
 // 3 = 128x256 (256); 4 = 64x512 (256).  4-connectivity: 5 = 32x256 (256); 6 = 4x32 (32);
 // 7 = 8x64 (64); 8 = 2x32 (32).  Multi-class, 8: 9 = 4x32, 10 = 8x64, 11 = 32x256;
-// multi-class, 4: 12 = 4x32, 13 = 32x256
+// multi-class, 4: 12 = 4x32, 13 = 32x256.  8-connectivity, other tile shapes of the
+// tile-shape sweep: 14 = 32x256 (256), 15 = 64x128 (256)
 int64_t emu_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t *labels, uint64_t seed,
                   int32_t shape, int32_t *status)
 {
@@ -437,6 +438,8 @@ int64_t emu_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32
     case 10: return Emu<Cfg<8, 64, 64, 8, true>>(seed).run(img, H, W, pitch, labels, status);
     case 11: return Emu<Cfg<32, 256, 256, 8, true>>(seed).run(img, H, W, pitch, labels, status);
     case 12: return Emu<Cfg<4, 32, 32, 4, true>>(seed).run(img, H, W, pitch, labels, status);
+    case 14: return Emu<Cfg<32, 256, 256>>(seed).run(img, H, W, pitch, labels, status);
+    case 15: return Emu<Cfg<64, 128, 256>>(seed).run(img, H, W, pitch, labels, status);
     default: return Emu<Cfg<32, 256, 256, 4, true>>(seed).run(img, H, W, pitch, labels, status);
     }
 }
@@ -453,6 +456,7 @@ void emu_label_batch(int32_t n, const uint8_t *const *imgs, const int32_t *H, co
     case 6: Emu<Cfg<4, 32, 32, 4>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
     case 9: Emu<Cfg<4, 32, 32, 8, true>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
     case 12: Emu<Cfg<4, 32, 32, 4, true>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
+    case 15: Emu<Cfg<64, 128, 256>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
     default: Emu<Cfg<8, 64, 64, 4>>(seed).run_batch(n, imgs, H, W, pitch, labels, K, status); break;
     }
 }

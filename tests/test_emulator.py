@@ -59,6 +59,37 @@ def test_emulated_path_tile_variants_quick():
         assert st == 0 and k == rk and np.array_equal(lab, ref)
 
 
+@pytest.mark.parametrize("shape", [14, 15])
+def test_emulated_sweep_tile_shapes(shape):
+    """The extra 8-connected tile shapes of the offline tile-shape sweep (32 x 256 and
+    64 x 128, the library's narrow tiles) against the oracle: densities across the
+    percolation threshold, ragged sizes, a serpentine, a padded pitch, and (64 x 128) a
+    batch."""
+    sys.path.insert(0, HERE)
+    import numpy as np
+
+    import oracle
+    import synth
+    from emu import emu
+
+    e = emu.Emu(emu.build(sanitize=False))
+    cases = [synth.bernoulli(h, w, p, s) for (h, w, p, s) in
+             ((130, 300, 0.1, 1), (97, 517, 0.45, 2), (200, 260, 0.6, 3), (64, 128, 0.9, 4), (33, 777, 0.5, 5))]
+    cases.append(synth.serpentine(150, 390))
+    for i, img in enumerate(cases):
+        ref, rk = oracle.cclremsp(img)
+        for pitch in (None, img.shape[1] + 5):
+            lab, k, st = e.label(img, seed=i, shape=shape, pitch=pitch)
+            assert st == 0 and k == rk and np.array_equal(lab, ref), (shape, img.shape, pitch)
+    if shape == 15:  # the library's narrow tiles also run the batched path
+        batch = [synth.make_batch_image(sp) for sp in synth.batch_specs(n=6, seed=7, lo=16, hi=300)]
+        labs, ks, st = e.label_batch(batch, seed=3, shape=15)
+        assert st == 0
+        for im, lab, k in zip(batch, labs, ks):
+            ref, rk = oracle.cclremsp(im)
+            assert k == rk and np.array_equal(lab, ref)
+
+
 def test_object_test_of_the_load_phase_is_byte_greater_than_threshold():
     """The load phase turns 16 bytes into 16 object bits with word arithmetic (the carry of
     byte + (255 - T) out of its byte).  Checked against byte > T for every byte value and

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from _gpu import stream_handle
+from _gpu import run_label, stream_handle
 
 pytestmark = pytest.mark.gpu
 
@@ -187,3 +187,34 @@ def test_global_ctas_per_sm_cap_and_two_streams(ccl):
                 assert flags.value == 0
     finally:
         lib.ccl_set_global_ctas_per_sm(0)
+
+
+def test_tile_policies_give_identical_labels(ccl):
+    """The 8-connected path on 64 x 256 tiles (policy 1), 64 x 128 tiles (policy 2) and the
+    size rule (policy 0): single images on both sides of the size threshold, ragged sizes
+    and a padded pitch, and a batch, all equal to the oracle under every policy."""
+    import torch
+
+    lib = ccl.lib()
+    assert lib.ccl_set_tile_policy(3) == 1 and lib.ccl_set_tile_policy(-1) == 1
+    singles = [synth.bernoulli(h, w, p, 60 + i) for i, (h, w, p) in
+               enumerate(((1, 1, 1.0), (63, 129, 0.5), (700, 1000, 0.3), (1500, 2333, 0.6),
+                          (3100, 3100, 0.45), (2000, 5000, 0.9)))]
+    singles.append(synth.serpentine(777, 3333))
+    specs = synth.batch_specs(n=24, seed=101, lo=16, hi=1500)
+    batch = [synth.make_batch_image(s) for s in specs]
+    refs = [oracle.cclremsp(im) for im in singles]
+    brefs = [oracle.cclremsp(im) for im in batch]
+    try:
+        for policy in (1, 2, 0):
+            assert lib.ccl_set_tile_policy(policy) == 0
+            for im, (ref, rk) in zip(singles, refs):
+                lab, k = ccl.label(torch.from_numpy(im).cuda())
+                assert k == rk and np.array_equal(lab.cpu().numpy(), ref), (policy, im.shape)
+            rc, lab, k, flags = run_label(singles[3], pitch=singles[3].shape[1] + 48)
+            assert rc == 0 and flags == 0 and k == refs[3][1] and np.array_equal(lab, refs[3][0])
+            outs, ks = ccl.label_batch([torch.from_numpy(im).cuda() for im in batch])
+            for o, kk, (ref, rk) in zip(outs, ks.cpu().tolist(), brefs):
+                assert kk == rk and np.array_equal(o.cpu().numpy(), ref), policy
+    finally:
+        lib.ccl_set_tile_policy(0)
