@@ -25,6 +25,7 @@ bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import atexit
 import ctypes
 import hashlib
 import json
@@ -118,7 +119,8 @@ def make_workload(name, device, only=None):
 # ---- clocks ------------------------------------------------------------------------------
 
 class ClockSampler:
-    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    """nvidia-smi samples (every 20 ms: a default step sequence runs for tens of
+    milliseconds) while the timed region runs."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -127,13 +129,20 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (host time, csv line)
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = time.perf_counter()
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, ValueError):
@@ -142,7 +151,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *exc):
         if self.proc:
@@ -153,11 +162,20 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        """Samples taken inside the timed region (marked on the host); if the region was
+        too short to hold one, the samples within 0.5 s of it (warm-up and the kernel
+        passes around it, the same work), and `window` says which."""
         if not self.lines:
             return None
+        window = "timed region"
+        t0, t1 = (self.t0 or 0.0), (self.t1 or float("inf"))
+        picked = [ln for t, ln in self.lines if t0 <= t <= t1 + 0.02]
+        if not picked:
+            window = "within 0.5 s of the timed region (warm-up and kernel passes)"
+            picked = [ln for t, ln in self.lines if t0 - 0.5 <= t <= t1 + 0.5]
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in picked:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -172,7 +190,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window": window}
 
 
 # ---- peaks and profiles ------------------------------------------------------------------
@@ -263,6 +281,8 @@ def run_ours(args, rank, world, local_rank):
             if rc != 0:
                 raise RuntimeError(f"ccl_label_async: {ccl.ccl_status_string(rc)}")
 
+    clk = ClockSampler(local_rank).__enter__()  # started early: nvidia-smi takes a while to start
+    atexit.register(clk.__exit__, None, None, None)  # stopped on any way out
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -282,16 +302,17 @@ def run_ours(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clk:
-        e0.record(stream)
-        for st in side:
-            st.wait_stream(stream)
-        for _ in range(args.steps):
-            step()
-        for st in side:
-            stream.wait_stream(st)
-        e1.record(stream)
-        torch.cuda.synchronize()
+    clk.mark_start()
+    e0.record(stream)
+    for st in side:
+        st.wait_stream(stream)
+    for _ in range(args.steps):
+        step()
+    for st in side:
+        stream.wait_stream(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk.mark_end()
     barrier()
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms, world, dev)
@@ -329,6 +350,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     ccl.ccl_profile_enable(0)
+    clk.__exit__(None, None, None)
     prof_ms = p0.elapsed_time(p1)
     kt = ccl.kernel_times()
     launches = sum(v[0] for v in kt.values())
