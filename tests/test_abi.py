@@ -69,6 +69,13 @@ def test_argument_checks_need_no_gpu(lib):
     for t in (-1, 256):  # threshold outside a byte's range
         assert lib.ccl_label_threshold(p, 4, 4, 4, 8, t, p, ctypes.byref(k), None) == 1
     assert lib.ccl_label_threshold(p, 0, 9, 9, 8, 127, p, ctypes.byref(k), None) == 0 and k.value == 0
+    # process-wide options: checked on the host, no GPU call (restored to the defaults)
+    for bad in (-1, 3):
+        assert lib.ccl_set_tile_policy(bad) == 1
+    for ok in (1, 2, 0):
+        assert lib.ccl_set_tile_policy(ok) == 0
+    assert lib.ccl_set_global_ctas_per_sm(-1) == 1
+    assert lib.ccl_set_global_ctas_per_sm(1) == 0 and lib.ccl_set_global_ctas_per_sm(0) == 0
     nb = ctypes.c_int64(0)
     assert lib.ccl_workspace_bytes(8192, 8192, ctypes.byref(nb)) == 0
     # the largest layout over the modes.  8-connectivity: bit pack 1/8 B/px + run codes
