@@ -233,6 +233,7 @@ int32_t ccl_label_async(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_
     int32_t rc = check_args(img, H, W, pitch_bytes, connectivity, labels);
     if (rc != CCL_OK)
         return rc;
+    connectivity = resolve_conn(connectivity, H, W);  // one tile shape for sizing and launch
     if (H == 0 || W == 0) {
         if (num_components_dev)
             return map_cuda(cudaMemsetAsync(num_components_dev, 0, 4, s));
@@ -258,6 +259,7 @@ int32_t label_sync(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes
     int32_t rc = check_args(img, H, W, pitch_bytes, connectivity, labels);
     if (rc != CCL_OK)
         return rc;
+    connectivity = resolve_conn(connectivity, H, W);  // one tile shape for sizing and launch
     if (H == 0 || W == 0) {
         if (num_components)
             *num_components = 0;
@@ -347,6 +349,7 @@ int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pi
     int32_t rc = check_args(img_host, H, W, pitch_bytes, connectivity, labels_host);
     if (rc != CCL_OK)
         return rc;
+    connectivity = resolve_conn(connectivity, H, W);  // one tile shape for sizing and launch
     if (H == 0 || W == 0) {
         if (num_components)
             *num_components = 0;
@@ -374,6 +377,7 @@ int32_t ccl_label_host_async(const uint8_t *img_host, int32_t H, int32_t W, int6
     int32_t rc = check_args(img_host, H, W, pitch_bytes, connectivity, labels_host);
     if (rc != CCL_OK)
         return rc;
+    connectivity = resolve_conn(connectivity, H, W);  // one tile shape for sizing and launch
     if (H == 0 || W == 0) {
         if (num_components_host)
             *num_components_host = 0;

@@ -70,6 +70,7 @@ extern "C" int32_t ccl_label_static(const uint8_t *img, int32_t H, int32_t W, in
     }
     if (!img || !labels || pitch_bytes < W || (int64_t)H * (int64_t)W >= ((int64_t)1 << 31) - 1)
         return CCL_ERR_INVALID_ARGUMENT;
+    connectivity = resolve_conn(connectivity, H, W);  // one tile shape for sizing and launch
     const Layout L = main_layout(H, W, connectivity);
     if (L.nP >= ((int64_t)1 << 31) - 1)
         return CCL_ERR_UNSUPPORTED;
