@@ -1,26 +1,32 @@
 """Benchmark: labelled Gpixels/s of the GPU path, with its HBM roofline, an end-to-end
 number through the host-buffer entry point, clocks, and the CPU oracle beside it.
 
-Workload (default ``sweep8192``): six 8192 x 8192 uint8 images - Bernoulli p in
-{0.1, 0.3, 0.5, 0.7, 0.9} (seeds 2..6) and a sigma=4 thresholded Gaussian field (seed 7),
-8-connectivity, int32 labels.  One step labels all six (one ``ccl_label_async`` call each)
-with the inputs already resident in HBM.  ``big21568`` labels the three ~465 MB images
-(sigma=16 blobs, Bernoulli(0.6), serpentine); ``small1024`` the 1024 x 1024 case.
+Workload (default ``big21568``): the three ~465 MB images of the paper's largest raster
+size (Table III's image_6, 465.20 MB at one byte per pixel, read as 21568 x 21568):
+sigma=16 thresholded Gaussian-field blobs (seed 8), Bernoulli(0.6) (seed 9) and the
+serpentine (one 1-px path through the whole image), 8-connectivity, int32 labels.  One
+step labels all three (one ``ccl_label_async`` call each) with the inputs already
+resident in HBM.  ``sweep8192`` (six 8192 x 8192 images: Bernoulli p in
+{0.1,0.3,0.5,0.7,0.9} and a sigma=4 field) and ``small1024`` (1024 x 1024 Bernoulli(0.5))
+can be timed the same way; the default run also reports both as extra keys, with the
+1024 x 1024 call replayed from a CUDA graph.
 
 The images of a step alternate over two streams (``--streams``) with the cooperative
 global kernel capped at one CTA per SM (``--global-ctas-per-sm``,
-``ccl_set_global_ctas_per_sm``), so that one image's tile pass runs beside another's
+``ccl_set_global_ctas_per_sm``), so that one image's tile pass can run beside another's
 global pass.  The line also carries the same steps on one stream with the library's
-default grid (``one_stream``), and per-kernel launch times taken on one stream.
+default grid (``one_stream``), per-kernel launch times taken on one stream, and per-image
+median / p99 latency over at least 20 calls.  The device status word of every stream is
+checked after every pass.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sweep8192|big21568|small1024] [--streams S]
+                    [--workload big21568|sweep8192|small1024] [--streams S]
                     [--global-ctas-per-sm N]
 
 Under torchrun each rank labels its own copy of the workload (independent replicas, no
 collective on the data path); rank 0 prints one JSON line with the max time over ranks.
-``--impl reference`` times the CPU oracle (the paper's PARemSP on OpenMP threads) on a
-bounded sample of the same workload instead.
+``--impl reference`` times the CPU oracle (the paper's PARemSP on OpenMP threads) on the
+same images (identical bytes, SHA-256 in both lines), one image per step.
 """
 from __future__ import annotations
 
@@ -50,6 +56,9 @@ PATH_BYTES_PER_PX = 5.0
 # per kernel: tile_local reads the image (1 B/px) and writes the bit pack (1/8 B/px);
 # final_labels reads the bit pack (1/8 B/px) and writes the labels (4 B/px)
 KERNEL_BYTES_PER_PX = {"tile_local": 1.125, "final_labels": 4.125}
+L2_NOTE = {"big21568": "inputs larger than L2: 3 x 465 MB images read and 3 x 1.86 GB labels written per step",
+           "sweep8192": "inputs larger than L2: 6 x 64 MiB images read and 6 x 256 MiB labels written per step",
+           "small1024": "one 1 MiB image: L2-resident (launch-bound case)"}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -82,37 +91,73 @@ def aggregate_gpx_s(px_per_rank: int, world: int, seconds_max: float) -> float:
 
 # ---- workloads ---------------------------------------------------------------------------
 
-def make_workload(name, device, only=None):
-    """Returns (list of (label, uint8 CUDA tensor), description dict)."""
+S_BIG = 21568
+WORKLOAD_DESC = {
+    "big21568": {"workload": "21568x21568 uint8 (~465 MB, Table III image_6 size) x3: sigma=16 thresholded "
+                             "Gaussian-field blobs (seed 8), Bernoulli(0.6) (seed 9), serpentine; "
+                             "8-connectivity; int32 labels",
+                 "images": 3, "H": S_BIG, "W": S_BIG},
+    "sweep8192": {"workload": "8192x8192 uint8 x6: Bernoulli p in {0.1,0.3,0.5,0.7,0.9} (seeds 2-6) "
+                              "+ sigma=4 thresholded Gaussian field (seed 7); 8-connectivity; int32 labels",
+                  "images": 6, "H": 8192, "W": 8192},
+    "small1024": {"workload": "1024x1024 uint8 Bernoulli(0.5) seed 1; 8-connectivity; int32 labels",
+                  "images": 1, "H": 1024, "W": 1024},
+}
+
+
+def workload_images(name, device=None):
+    """The images of workload `name` as (label, image) pairs: uint8 torch tensors on
+    `device` when one is given, else numpy arrays on the host.  Thresholded fields are
+    smoothed on the GPU whenever one is present (also for host arrays), so that both
+    benchmark arms see identical bytes; without a GPU the host generator of the same recipe
+    is used (its bytes may differ near the threshold; the SHA-256 in the line says)."""
     import torch
 
-    imgs = []
+    cuda = torch.cuda.is_available()
+    gen_dev = device if device is not None else (torch.device("cuda", torch.cuda.current_device()) if cuda else None)
+
+    def field(h, w, sigma, seed):
+        if gen_dev is not None:
+            t = synth.blobs_device(h, w, sigma, seed, gen_dev)
+            return t if device is not None else t.cpu().numpy()
+        img = synth.blobs(h, w, sigma, seed)
+        return torch.from_numpy(img).to(device) if device is not None else img
+
+    def host(img):
+        return torch.from_numpy(img).to(device) if device is not None else img
+
+    out = []
     if name == "sweep8192":
         for kind, arg, seed in synth.SWEEP_8192:
-            if only and only != (f"bernoulli_p{arg}" if kind == "bernoulli" else f"blobs_sigma{arg:g}"):
-                continue
             if kind == "bernoulli":
-                t = torch.from_numpy(synth.bernoulli(8192, 8192, arg, seed)).to(device)
-                imgs.append((f"bernoulli_p{arg}", t))
+                out.append((f"bernoulli_p{arg}", host(synth.bernoulli(8192, 8192, arg, seed))))
             else:
-                imgs.append((f"blobs_sigma{arg:g}", synth.blobs_device(8192, 8192, arg, seed, device)))
-        desc = {"workload": "8192x8192 uint8 x6: Bernoulli p in {0.1,0.3,0.5,0.7,0.9} (seeds 2-6) "
-                            "+ sigma=4 thresholded Gaussian field (seed 7); 8-connectivity; int32 labels",
-                "images": 6, "H": 8192, "W": 8192}
+                out.append((f"blobs_sigma{arg:g}", field(8192, 8192, arg, seed)))
     elif name == "big21568":
-        s = 21568
-        imgs.append(("blobs_sigma16", synth.blobs_device(s, s, 16.0, 8, device)))
-        imgs.append(("bernoulli_p0.6", torch.from_numpy(synth.bernoulli(s, s, 0.6, 9)).to(device)))
-        imgs.append(("serpentine", torch.from_numpy(synth.serpentine(s, s)).to(device)))
-        desc = {"workload": "21568x21568 uint8 (~465 MB) x3: sigma=16 blobs (seed 8), Bernoulli(0.6) "
-                            "(seed 9), serpentine; 8-connectivity; int32 labels",
-                "images": 3, "H": s, "W": s}
+        s = S_BIG
+        out.append(("blobs_sigma16", field(s, s, 16.0, 8)))
+        out.append(("bernoulli_p0.6", host(synth.bernoulli(s, s, 0.6, 9))))
+        out.append(("serpentine", host(synth.serpentine(s, s))))
     elif name == "small1024":
-        imgs.append(("bernoulli_p0.5", torch.from_numpy(synth.bernoulli(1024, 1024, 0.5, 1)).to(device)))
-        desc = {"workload": "1024x1024 uint8 Bernoulli(0.5) seed 1; 8-connectivity; int32 labels",
-                "images": 1, "H": 1024, "W": 1024}
+        out.append(("bernoulli_p0.5", host(synth.bernoulli(1024, 1024, 0.5, 1))))
     else:
         raise SystemExit(f"unknown workload {name}")
+    return out
+
+
+def image_sha256(img):
+    """SHA-256 of an image's bytes (torch tensor on any device, or numpy array)."""
+    if hasattr(img, "cpu"):
+        img = img.cpu().numpy()
+    return synth.sha256(img)
+
+
+def make_workload(name, device, only=None):
+    """Returns (list of (label, uint8 CUDA tensor), description dict with input SHA-256s)."""
+    imgs = workload_images(name, device)
+    if only:
+        imgs = [(n, t) for n, t in imgs if n == only]
+    desc = {**WORKLOAD_DESC[name], "inputs_sha256": {n: image_sha256(t) for n, t in imgs}}
     return imgs, desc
 
 
@@ -286,11 +331,17 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    flags = ctypes.c_int32(0)
-    for sp in step_sptr:
-        lib.ccl_device_status(sp, ctypes.byref(flags))
-        if flags.value:
-            raise RuntimeError(f"device status {flags.value} after warm-up")
+
+    def check_status(where, sptrs=step_sptr):
+        """The device status word of every stream's workspace (a capped loop or barrier
+        would leave a bit set); read and cleared after every pass."""
+        flags = ctypes.c_int32(0)
+        for sp in sptrs:
+            rc = lib.ccl_device_status(sp, ctypes.byref(flags))
+            if rc != 0 or flags.value:
+                raise RuntimeError(f"device status {flags.value} (rc {rc}) after {where}")
+
+    check_status("warm-up")
 
     def barrier():
         if world > 1:
@@ -315,6 +366,7 @@ def run_ours(args, rank, world, local_rank):
     clk.mark_end()
     barrier()
     ms = e0.elapsed_time(e1)
+    check_status("the timed pass")
     ms_max = max_over_ranks(ms, world, dev)
 
     # the same steps on one stream with the library's default global grid, for comparison
@@ -331,6 +383,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     ms_one = max_over_ranks(o0.elapsed_time(o1), world, dev)
+    check_status("the one-stream pass")
     if args.global_ctas_per_sm is not None:
         lib.ccl_set_global_ctas_per_sm(args.global_ctas_per_sm)
 
@@ -354,6 +407,28 @@ def run_ours(args, rank, world, local_rank):
     prof_ms = p0.elapsed_time(p1)
     kt = ccl.kernel_times()
     launches = sum(v[0] for v in kt.values())
+    check_status("the per-kernel pass")
+
+    # per-image latency: each image labelled alone, one stream, an event pair per call
+    per_image = {}
+    for i, (name, t) in enumerate(imgs):
+        H, W = t.shape
+        times = []
+        for _ in range(max(20, args.steps)):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            rc = lib.ccl_label_async(t.data_ptr(), H, W, t.stride(0), args.connectivity, labels[i].data_ptr(),
+                                     kdev.data_ptr() + 4 * i, sptr)
+            a1.record(stream)
+            if rc != 0:
+                raise RuntimeError(f"ccl_label_async: {ccl.ccl_status_string(rc)}")
+            times.append((a0, a1))
+        torch.cuda.synchronize()
+        ms_i = sorted(a.elapsed_time(b) for a, b in times)
+        per_image[name] = {"runs": len(ms_i), "median_ms": round(statistics.median(ms_i), 4),
+                           "p99_ms": round(ms_i[min(len(ms_i) - 1, int(0.99 * len(ms_i)))], 4),
+                           "gpx_s_median": round(H * W / (statistics.median(ms_i) * 1e-3) / 1e9, 2)}
+    check_status("the per-image pass", [sptr])
 
     # correctness spot check outside the timed region: K must match a fresh labelling
     ks = kdev.cpu().tolist()
@@ -387,6 +462,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
+    check_status("the end-to-end pass", e2e_sptr)
     lib.ccl_set_global_ctas_per_sm(0)  # library default for the measurements below
     for i, hl in enumerate(host_labs):
         if int(hl.max()) != ks[i] or int(host_k[i]) != ks[i]:
@@ -417,15 +493,20 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8->int32", "data": "synthetic",
         "config": {**desc, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "streams": args.streams, "global_ctas_per_sm": args.global_ctas_per_sm or "all that fit",
-                   "l2": "inputs larger than L2: 6 x 64 MiB images read and 6 x 256 MiB labels written per step"
-                   if args.workload == "sweep8192" else "inputs larger than L2"},
+                   "l2": L2_NOTE.get(args.workload, "inputs larger than L2")},
         "roofline": roof,
         "path_roofline": {"bytes_per_px": PATH_BYTES_PER_PX, "achieved_gbs": round(path_gbs, 1),
                           "frac": round(path_gbs / peak, 4), "peak": peak, "peak_source": peak_kind},
         "one_stream": {"value": round(aggregate_gpx_s(px_per_step, world, ms_one / args.steps * 1e-3), 2),
                        "ms_per_step": round(ms_one / args.steps, 4),
                        "how": "the same steps on one stream, global kernel with as many CTAs per SM as fit"},
-        "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 4)} for k, v in kt.items() if v[0]},
+        "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 4),
+                        "avg_launch_ms": round(v[1] / v[0], 4),
+                        **({"achieved_gbs": round(KERNEL_BYTES_PER_PX[k] * per_launch_px / (v[1] / v[0] * 1e-3) / 1e9, 1),
+                            "frac": round(KERNEL_BYTES_PER_PX[k] * per_launch_px / (v[1] / v[0] * 1e-3) / 1e9 / peak, 4)}
+                           if k in KERNEL_BYTES_PER_PX else {})}
+                    for k, v in kt.items() if v[0]},
+        "per_image": per_image,
         "kernels_pass": {"steps": args.steps, "ms_per_step": round(prof_ms / args.steps, 4),
                          "how": "a second timed pass of the same steps with an event pair around every "
                                 "launch; `value` comes from the pass without them"},
@@ -440,9 +521,13 @@ def run_ours(args, rank, world, local_rank):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline([t for _, t in imgs], args)
-    if args.batch_images > 0 or args.served:
-        del imgs, labels, host_imgs, host_labs
-        torch.cuda.empty_cache()
+    del imgs, labels, host_imgs, host_labs
+    torch.cuda.empty_cache()
+    if args.extras:
+        for extra in ("sweep8192", "small1024"):
+            if extra != args.workload:
+                line[extra] = measure_plain(args, extra, dev, lib)
+                torch.cuda.empty_cache()
     if args.batch_images > 0:
         line["batched"] = measure_batched(args, dev, lib, stream)
         torch.cuda.empty_cache()
@@ -454,6 +539,86 @@ def run_ours(args, rank, world, local_rank):
         line["multi_class"] = measure_classes(args, dev, lib, stream)
         torch.cuda.empty_cache()
     return line
+
+
+def measure_plain(args, name, dev, lib):
+    """Another plain-path workload as an extra key: images alternating over two streams
+    with the global kernel at one CTA per SM (as the headline), CUDA events around 10 steps
+    after 3 warm-up steps; for single-image workloads also one call captured in a CUDA graph
+    and replayed (a small image is launch-bound and L2-resident).  K is checked against
+    the plain call, and the device status after each pass."""
+    import torch
+
+    import paper_1606_05973_gb300 as ccl
+
+    imgs, desc = make_workload(name, dev)
+    labels = [torch.empty(tuple(t.shape), dtype=torch.int32, device=dev) for _, t in imgs]
+    kdev = torch.zeros(len(imgs), dtype=torch.int32, device=dev)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    sptr = [ctypes.c_void_p(st.cuda_stream) for st in streams]
+    px = sum(t.numel() for _, t in imgs)
+    lib.ccl_set_global_ctas_per_sm(args.global_ctas_per_sm or 0)
+
+    def step(ns=2):
+        for i, (_, t) in enumerate(imgs):
+            H, W = t.shape
+            rc = lib.ccl_label_async(t.data_ptr(), H, W, t.stride(0), args.connectivity, labels[i].data_ptr(),
+                                     kdev.data_ptr() + 4 * i, sptr[i % ns])
+            if rc != 0:
+                raise RuntimeError(f"ccl_label_async: {ccl.ccl_status_string(rc)}")
+
+    def status():
+        flags = ctypes.c_int32(0)
+        for sp in sptr:
+            if lib.ccl_device_status(sp, ctypes.byref(flags)) != 0 or flags.value:
+                raise RuntimeError(f"device status {flags.value} in {name}")
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    main = streams[0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10 if len(imgs) > 1 else 200
+    e0.record(main)
+    streams[1].wait_stream(main)
+    for _ in range(reps):
+        step()
+    main.wait_stream(streams[1])
+    e1.record(main)
+    torch.cuda.synchronize()
+    status()
+    ms = e0.elapsed_time(e1) / reps
+    peak, kind = hbm_peak()
+    gbs = PATH_BYTES_PER_PX * px / (ms * 1e-3) / 1e9
+    res = {"workload": desc["workload"], "inputs_sha256": desc["inputs_sha256"], "ms_per_step": round(ms, 4),
+           "value": round(px / (ms * 1e-3) / 1e9, 2), "unit": UNIT,
+           "path_frac": round(gbs / peak, 4), "how": f"{reps} steps, images alternating over two streams"}
+    if len(imgs) == 1:
+        ref_k = int(kdev[0])
+        lib.ccl_set_global_ctas_per_sm(0)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(main):
+            step(1)  # the workspace of this stream is sized before capture
+            main.synchronize()
+            with torch.cuda.graph(g, stream=main):
+                step(1)
+            kdev.fill_(-1)
+            g.replay()
+            torch.cuda.synchronize()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(main)
+            for _ in range(reps):
+                g.replay()
+            g1.record(main)
+        torch.cuda.synchronize()
+        status()
+        if int(kdev[0]) != ref_k:
+            raise RuntimeError("graph replay changed K")
+        gms = g0.elapsed_time(g1) / reps
+        res["graph_replay"] = {"us_per_image": round(gms * 1e3, 2), "value": round(px / (gms * 1e-3) / 1e9, 2),
+                               "how": f"one ccl_label_async call captured in a CUDA graph, {reps} replays"}
+    lib.ccl_set_global_ctas_per_sm(args.global_ctas_per_sm or 0)
+    return res
 
 
 def measure_classes(args, dev, lib, stream):
@@ -683,47 +848,103 @@ def cpu_threads():
         return os.cpu_count() or 1
 
 
+def cpu_sample(host_imgs, rows):
+    """The CPU legs' bounded sample: the first `rows` rows of every image of the workload
+    (whole images when they are shorter)."""
+    return [np.ascontiguousarray(im[:rows]) for im in host_imgs]
+
+
+def time_leg(fn, sample, runs):
+    """Median and p99 of `runs` timings of labelling every image of `sample` once."""
+    secs = []
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        for im in sample:
+            fn(im)
+        secs.append(time.perf_counter() - t0)
+    secs.sort()
+    return statistics.median(secs), secs[min(len(secs) - 1, int(0.99 * len(secs)))]
+
+
+def thread_counts(nthr):
+    out, t = [], 1
+    while t < nthr:
+        out.append(t)
+        t *= 2
+    out.append(nthr)
+    return out
+
+
 def cpu_baseline(dev_imgs, args):
-    """The oracle as it stands (PARemSP on all host threads; CCLRemSP on one) on a bounded
-    sample of the workload: the first images until ~10 s of CPU work per algorithm."""
+    """The oracle as it stands on the host's cores, on a bounded sample of the workload
+    (the first rows of every image, about 10-30 s of CPU work in all): PARemSP (Algorithm
+    7) at 1, 2, 4, ... and all threads, ARemSP (Algorithm 5, the paper's best sequential
+    algorithm, Table II) and CCLRemSP (Algorithm 1) on one thread.  Each leg is the median
+    of 3 runs over the sample (std::chrono-free: Python's perf_counter around the C call);
+    the canonical renumbering of ARemSP / PARemSP is excluded (timed separately)."""
     import oracle
 
     orc = oracle.default()
-    host = [t.cpu().numpy() for t in dev_imgs]
     nthr = cpu_threads()
-    res = {}
     conn = args.connectivity
+    host = [t.cpu().numpy() for t in dev_imgs]
+    rows = max(1, min(im.shape[0] for im in host) // 4) if host[0].size > (1 << 26) else host[0].shape[0]
+    sample = cpu_sample(host, rows)
+    px = sum(im.size for im in sample)
+    runs = 3
+
+    def leg(fn, cores, algorithm):
+        med, p99 = time_leg(fn, sample, runs)
+        return {"value": round(px / med / 1e9, 4), "cores": cores, "median_s": round(med, 4),
+                "p99_s": round(p99, 4), "runs": runs, "algorithm": algorithm}
+
+    desc = (f"the first {rows} rows of each of the {len(host)} image(s) of the workload "
+            f"({px / 1e6:.1f} Mpx), each leg the median of {runs} runs")
     if conn != 8:  # PARemSP (Algorithm 7) is stated for 8-connectivity only
-        legs = (("cclremsp", lambda im: orc.cclremsp(im, conn), 1),)
-    else:
-        legs = (("paremsp", lambda im: orc.paremsp(im, nthr, remap=False), nthr),
-                ("cclremsp", lambda im: orc.cclremsp(im), 1))
-    for key, fn, cores in legs:
-        px, secs, used = 0, 0.0, 0
-        for im in host:
-            t0 = time.perf_counter()
-            fn(im)
-            secs += time.perf_counter() - t0
-            px += im.size
-            used += 1
-            if secs > args.cpu_budget_s:
-                break
-        res[key] = {"value": round(px / secs / 1e9, 4), "cores": cores, "images": used, "seconds": round(secs, 2)}
-    if conn != 8:
-        p = res["cclremsp"]
-        return {"value": p["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                "algorithm": f"CCLRemSP (Algorithm 1) with {conn}-connectivity, canonical labels",
-                "sample": f"first {p['images']} image(s) of the workload, labelled once each"}
-    p = res["paremsp"]
-    return {"value": p["value"], "unit": UNIT, "cores": p["cores"], "kind": "oracle",
-            "algorithm": "PARemSP (Algorithm 7) on OpenMP threads, canonical renumbering excluded",
-            "sample": f"first {p['images']} image(s) of the workload, labelled once each",
-            "single_thread": {**res["cclremsp"], "algorithm": "CCLRemSP (Algorithm 1)"}}
+        c = leg(lambda im: orc.cclremsp(im, conn), 1, f"CCLRemSP (Algorithm 1), {conn}-connectivity")
+        return {"value": c["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                "algorithm": c["algorithm"], "sample": desc, "legs": {"cclremsp": c}}
+    legs = {}
+    for t in thread_counts(nthr):
+        legs[f"paremsp_t{t}"] = leg(lambda im, t=t: orc.paremsp(im, t, remap=False), t,
+                                    f"PARemSP (Algorithm 7) on {t} OpenMP thread(s)")
+    legs["aremsp"] = leg(lambda im: orc.aremsp(im, remap=False), 1, "ARemSP (Algorithm 5), one thread")
+    legs["cclremsp"] = leg(lambda im: orc.cclremsp(im), 1, "CCLRemSP (Algorithm 1), one thread")
+    t0 = time.perf_counter()
+    for im in sample:
+        lab, k = orc.aremsp(im, remap=False)
+        orc.canonicalize(lab, k)
+    remap_s = time.perf_counter() - t0
+    top = legs[f"paremsp_t{nthr}"]
+    return {"value": top["value"], "unit": UNIT, "cores": nthr, "kind": "oracle",
+            "algorithm": "PARemSP (Algorithm 7) on all host threads, canonical renumbering excluded",
+            "sample": desc, "cpu_model": cpu_model(), "legs": legs,
+            "speedup_paremsp_vs_aremsp": round(top["value"] / legs["aremsp"]["value"], 2),
+            "aremsp_plus_renumbering_s": round(remap_s, 4)}
+
+
+def cpu_model():
+    """The host CPU's model name (/proc/cpuinfo; Arm hosts list implementer and part)."""
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ":" in ln:
+                    k, v = ln.split(":", 1)
+                    fields.setdefault(k.strip().lower(), v.strip())
+    except OSError:
+        pass
+    if "model name" in fields:
+        return fields["model name"]
+    if "cpu part" in fields:
+        return f"{os.uname().machine} (CPU implementer {fields.get('cpu implementer', '?')}, part {fields['cpu part']})"
+    return os.uname().machine
 
 
 def run_reference(args, rank, world):
-    """The oracle as the reference arm: PARemSP on the host's threads, one bounded sample
-    (one image of the workload, round robin) per step."""
+    """The oracle as the reference arm: PARemSP (Algorithm 7) on the host's threads over
+    the same images as our arm (identical bytes: the SHA-256s are in both lines), one image
+    of the workload per step, round robin."""
     if rank != 0:
         return None
     if args.connectivity != 8:
@@ -732,19 +953,9 @@ def run_reference(args, rank, world):
 
     orc = oracle.default()
     nthr = cpu_threads()
-    if args.workload == "sweep8192":
-        host = [im for _, im in synth.sweep_8192()]
-        desc = {"workload": "8192x8192 uint8 x6: Bernoulli p in {0.1,0.3,0.5,0.7,0.9} (seeds 2-6) "
-                            "+ sigma=4 thresholded Gaussian field (seed 7); 8-connectivity; int32 labels",
-                "images": 6, "H": 8192, "W": 8192}
-    elif args.workload == "small1024":
-        host = [synth.bernoulli(1024, 1024, 0.5, 1)]
-        desc = {"workload": "1024x1024 uint8 Bernoulli(0.5) seed 1; 8-connectivity; int32 labels",
-                "images": 1, "H": 1024, "W": 1024}
-    else:
-        s = 21568
-        host = [synth.bernoulli(s, s, 0.6, 9), synth.serpentine(s, s)]
-        desc = {"workload": "21568x21568 uint8: Bernoulli(0.6) (seed 9), serpentine", "images": 2, "H": s, "W": s}
+    pairs = workload_images(args.workload)
+    host = [im for _, im in pairs]
+    desc = {**WORKLOAD_DESC[args.workload], "inputs_sha256": {n: synth.sha256(im) for n, im in pairs}}
     for i in range(args.warmup):
         orc.paremsp(host[i % len(host)], nthr, remap=False)
     px, t0 = 0, time.perf_counter()
@@ -759,7 +970,7 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "u8->int32", "data": "synthetic", "impl": "reference",
             "config": {**desc, "parallelism": f"{nthr} OpenMP threads"},
             "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": nthr, "kind": "oracle",
-                             "sample": "one image of the workload per step, round robin"},
+                             "sample": "one whole image of the workload per step, round robin"},
             "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -769,7 +980,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["sweep8192", "big21568", "small1024"], default="sweep8192")
+    ap.add_argument("--workload", choices=["big21568", "sweep8192", "small1024"], default="big21568")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the sweep8192 / small1024 extra keys")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--streams", type=int, default=2,
                     help="streams the images of a step alternate over (timed pass)")
@@ -783,7 +996,6 @@ def main():
                     help="size of the uneven-batch comparison (0 skips it)")
     ap.add_argument("--no-served", dest="served", action="store_false", help="skip the serving measurement")
     ap.add_argument("--no-fused", dest="fused", action="store_false", help="skip the fused-binarisation measurement")
-    ap.add_argument("--cpu-budget-s", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

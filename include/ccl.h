@@ -36,19 +36,25 @@ typedef struct CUstream_st *ccl_stream_t;
 
 typedef enum {
     CCL_OK = 0,
-    CCL_ERR_INVALID_ARGUMENT = 1, /* NULL pointer, negative size, pitch < W, H*W >= 2^31,
-                                     connectivity not 4 or 8 */
-    CCL_ERR_UNSUPPORTED = 2,      /* more tile runs than 32-bit node ids can number, or a device
-                                     index above 63 (ccl_label_static) */
+    CCL_ERR_INVALID_ARGUMENT = 1, /* NULL pointer, negative size, pitch < W, H*W >= 2^31 */
+    CCL_ERR_UNSUPPORTED = 2,      /* connectivity other than 4 or 8; more tile runs than 32-bit
+                                     node ids can number; a device index above 63 */
     CCL_ERR_OUT_OF_MEMORY = 3,    /* workspace allocation failed */
     CCL_ERR_CUDA = 4,             /* a CUDA runtime call failed */
     CCL_ERR_TIMEOUT = 5,          /* a device loop hit its iteration cap (see status bits) */
-    CCL_ERR_BUSY = 6,             /* server: over its memory cap and told not to wait */
+    CCL_ERR_BUSY = 6,             /* server: max_pending requests already wait for admission */
     CCL_ERR_INTERNAL = 7,         /* a device-side consistency check failed */
-    CCL_ERR_TOO_LARGE = 8         /* ccl_label_static: image needs more than its fixed scratch */
+    CCL_ERR_TOO_LARGE = 8         /* ccl_label_static: the image needs more than its fixed
+                                     scratch; server: a request needs more than the whole cap */
 } ccl_status;
 
-/* Device status word bits (ccl_device_status). */
+/* Device status word bits (ccl_device_status, ccl_label_static_status).  The blocking entry
+ * points (ccl_label with a non-NULL num_components, ccl_label_host, the server) read the
+ * word themselves and turn a set bit into CCL_ERR_TIMEOUT / CCL_ERR_INTERNAL.  The
+ * asynchronous ones (ccl_label_async, ccl_label_host_async, the ccl_label_batch family)
+ * cannot: their callers must call ccl_device_status(stream) once the stream's work is done
+ * (ccl_label_static_status for ccl_label_static) and treat a non-zero word as a failed
+ * labelling of the calls since the last read. */
 #define CCL_STATUS_LOOP_CAP 1  /* a union-find loop exceeded its iteration cap */
 #define CCL_STATUS_BOUNDS 2    /* checked builds: an index was out of range (access skipped) */
 #define CCL_STATUS_BAD_VALUE 4 /* checked builds: a value that cannot occur was read */
@@ -72,7 +78,7 @@ int32_t ccl_version(void);
  *                  are read); 16-byte alignment of img and pitch enables vector loads
  *   H, W           image size, H >= 0, W >= 0, H*W < 2^31
  *   pitch_bytes    row stride of img in bytes, >= W
- *   connectivity   8 or 4 (anything else: CCL_ERR_INVALID_ARGUMENT, also when H or W is 0)
+ *   connectivity   8 or 4 (anything else: CCL_ERR_UNSUPPORTED, also when H or W is 0)
  *   labels         device, H*W int32, row stride W (dense); fully overwritten
  *   num_components HOST int32 or NULL.  Non-NULL: the call waits for `stream` and
  *                  stores K; it also checks the device status word and returns
@@ -105,6 +111,7 @@ int32_t ccl_label_threshold(const uint8_t *img, int32_t H, int32_t W, int64_t pi
  * ccl_label_async - as ccl_label, fully asynchronous: K is written to the DEVICE int32
  * num_components_dev (may be NULL).  Safe to capture in a CUDA graph once the stream's
  * workspace is large enough (make one uncaptured call of the same or larger size first).
+ * The device status word is not read: call ccl_device_status(stream) after the work.
  */
 int32_t ccl_label_async(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes,
                         int32_t connectivity, int32_t *labels, int32_t *num_components_dev,
@@ -200,17 +207,35 @@ int32_t ccl_label_static(const uint8_t *img, int32_t H, int32_t W, int64_t pitch
                          ccl_stream_t stream);
 
 /*
+ * ccl_label_static_status - read and clear the status word of ccl_label_static's fixed
+ * scratch (CCL_STATUS_* bits; 0 when every loop and grid barrier stayed within its cap),
+ * without allocating.  Waits for `stream`, which must be the stream (or ordered after the
+ * streams) of the ccl_label_static calls it reports on.  *flags is a HOST int32.  A
+ * non-zero word means the labels of those calls are not to be trusted.  Like
+ * ccl_label_static, the first call on a device looks up the scratch address.
+ */
+int32_t ccl_label_static_status(ccl_stream_t stream, int32_t *flags);
+
+/*
  * Continuous-batching server (the serving form of the batched path; the paper's method is
  * unchanged underneath).  Requests are admitted while others run: a scheduler thread packs
  * waiting requests, first come first served, into one batched launch per idle lane (a CUDA
- * stream with its own resident workspace), so launches on different lanes overlap on the
- * device and new requests join the next launch as soon as a lane frees up.  Each result is
- * bit-identical to labelling the image alone.
+ * stream), so launches on different lanes overlap on the device and new requests join the
+ * next launch as soon as a lane and memory free up.  Each result is bit-identical to
+ * labelling the image alone.
  *
- * Memory: mem_cap_bytes of device workspace, split evenly between the lanes and allocated
- * at creation (it stays resident).  A request whose workspace alone exceeds a lane's share
- * completes with CCL_ERR_TOO_LARGE.  Images and label buffers stay the caller's and must
- * stay valid until ccl_server_wait returns for that request.
+ * Memory: one pool of mem_cap_bytes of device workspace, allocated at creation and
+ * resident for the server's lifetime, shared by all lanes: each launch reserves one slice
+ * of it for its batch and returns it when its results are on the host.  A request is
+ * admitted when its workspace fits the largest free slice (a waiting request holds the
+ * head of the queue until memory frees up); only a request whose workspace exceeds the
+ * whole cap completes with CCL_ERR_TOO_LARGE.  Images and label buffers stay the caller's
+ * and must stay valid until ccl_server_wait returns for that request.
+ *
+ * Relation to the scope table's names: the config's `lanes` are its `num_streams`, and
+ * `lanes * max_batch` requests are the most on the device at once (its `max_slots`); the
+ * statistics call is ccl_server_get_stats, because C cannot give a function the name of
+ * the ccl_server_stats type.
  */
 typedef struct ccl_server ccl_server;
 
@@ -232,6 +257,7 @@ typedef struct {
     double mean_batch;      /* requests per launch */
     int64_t peak_inflight_bytes; /* workspace bytes of requests on the device at once */
     int32_t peak_queue;     /* most requests waiting for admission */
+    int32_t peak_busy_lanes; /* most launches in flight at once (lanes busy together) */
 } ccl_server_stats;
 
 /* Create a server on the current CUDA device.  *out receives the handle. */
@@ -256,6 +282,8 @@ int32_t ccl_device_status(ccl_stream_t stream, int32_t *flags);
 
 /* Free every cached workspace of this process (waits for the device). */
 int32_t ccl_release(void);
+/* The same as ccl_release (the name the scope table gives it). */
+int32_t ccl_shutdown(void);
 
 /*
  * ccl_set_global_ctas_per_sm - how many CTAs of the cooperative boundary-merge / flatten

@@ -17,7 +17,7 @@ import threading
 from .build import build, lib_path
 
 __all__ = [
-    "CCLError", "CCLUnavailable", "load", "lib", "ccl_label", "ccl_label_async", "ccl_label_static",
+    "CCLError", "CCLUnavailable", "load", "lib", "ccl_label", "ccl_label_async", "ccl_label_static", "ccl_label_static_status", "ccl_shutdown",
     "ccl_label_host", "ccl_label_batch", "ccl_workspace_bytes", "ccl_device_status", "ccl_release", "ccl_set_global_ctas_per_sm",
     "ccl_set_tile_policy",
     "ccl_profile_enable", "ccl_profile_reset", "ccl_profile_read", "ccl_status_string",
@@ -57,7 +57,7 @@ class ServerStats(ctypes.Structure):
                 ("gpx_per_s", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("mean_batch", ctypes.c_double), ("peak_inflight_bytes", ctypes.c_int64),
-                ("peak_queue", ctypes.c_int32)]
+                ("peak_queue", ctypes.c_int32), ("peak_busy_lanes", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -74,6 +74,7 @@ _SIGS = {
     "ccl_label": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
     "ccl_label_async": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
     "ccl_label_static": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
+    "ccl_label_static_status": ([_P, _P], _I32),
     "ccl_label_host": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
     "ccl_label_host_async": ([_P, _I32, _I32, _I64, _I32, _P, _P, _P], _I32),
     "ccl_label_batch": ([_P, _I32, _I32, _P, _P], _I32),
@@ -84,6 +85,7 @@ _SIGS = {
     "ccl_workspace_bytes": ([_I32, _I32, _P], _I32),
     "ccl_device_status": ([_P, _P], _I32),
     "ccl_release": ([], _I32),
+    "ccl_shutdown": ([], _I32),
     "ccl_set_global_ctas_per_sm": ([_I32], _I32),
     "ccl_set_tile_policy": ([_I32], _I32),
     "ccl_profile_enable": ([_I32], _I32),
@@ -149,6 +151,11 @@ def ccl_label_static(img, H, W, pitch_bytes, connectivity, labels, num_component
     return lib().ccl_label_static(img, H, W, pitch_bytes, connectivity, labels, num_components_dev, stream)
 
 
+def ccl_label_static_status(stream, flags_ptr) -> int:
+    """Read and clear the status word of ccl_label_static's fixed scratch (no allocation)."""
+    return lib().ccl_label_static_status(stream, flags_ptr)
+
+
 def ccl_label_host(img_host, H, W, pitch_bytes, connectivity, labels_host, num_components, stream) -> int:
     return lib().ccl_label_host(img_host, H, W, pitch_bytes, connectivity, labels_host, num_components, stream)
 
@@ -189,6 +196,10 @@ def ccl_device_status(stream, flags_ptr) -> int:
 
 def ccl_release() -> int:
     return lib().ccl_release()
+
+
+def ccl_shutdown() -> int:
+    return lib().ccl_shutdown()
 
 
 def ccl_set_global_ctas_per_sm(n) -> int:

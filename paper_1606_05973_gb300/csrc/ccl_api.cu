@@ -95,10 +95,10 @@ cudaEvent_t pool_event()
 
 int32_t check_args(const void *img, int32_t H, int32_t W, int64_t pitch, int32_t conn, const void *labels)
 {
-    if (H < 0 || W < 0)
-        return CCL_ERR_INVALID_ARGUMENT;
     const int c = conn & ~CONN_CLASSES;
     if (c != 4 && c != 8)
+        return CCL_ERR_UNSUPPORTED;
+    if (H < 0 || W < 0)
         return CCL_ERR_INVALID_ARGUMENT;
     if (H == 0 || W == 0)
         return CCL_OK;
@@ -199,7 +199,9 @@ const char *ccl_status_string(int32_t status)
     case CCL_ERR_TIMEOUT: return "device loop exceeded its iteration cap";
     case CCL_ERR_BUSY: return "busy";
     case CCL_ERR_INTERNAL: return "device consistency check failed";
-    case CCL_ERR_TOO_LARGE: return "image needs more than the fixed 16 MiB scratch of ccl_label_static";
+    case CCL_ERR_TOO_LARGE:
+        return "image needs more device memory than the call allows (ccl_label_static: its fixed 16 MiB "
+               "scratch; server: its memory cap)";
     default: return "unknown status";
     }
 }
@@ -229,7 +231,7 @@ int32_t ccl_label_async(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (connectivity & CONN_CLASSES)
-        return CCL_ERR_INVALID_ARGUMENT;
+        return CCL_ERR_UNSUPPORTED;
     int32_t rc = check_args(img, H, W, pitch_bytes, connectivity, labels);
     if (rc != CCL_OK)
         return rc;
@@ -283,7 +285,7 @@ int32_t ccl_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes,
                   int32_t *labels, int32_t *num_components, ccl_stream_t stream)
 {
     if (connectivity & CONN_CLASSES)
-        return CCL_ERR_INVALID_ARGUMENT;
+        return CCL_ERR_UNSUPPORTED;
     return label_sync(img, H, W, pitch_bytes, connectivity, 0, labels, num_components, stream);
 }
 
@@ -291,7 +293,7 @@ int32_t ccl_label_threshold(const uint8_t *img, int32_t H, int32_t W, int64_t pi
                             int32_t threshold, int32_t *labels, int32_t *num_components, ccl_stream_t stream)
 {
     if (connectivity & CONN_CLASSES)
-        return CCL_ERR_INVALID_ARGUMENT;
+        return CCL_ERR_UNSUPPORTED;
     return label_sync(img, H, W, pitch_bytes, connectivity, threshold, labels, num_components, stream);
 }
 
@@ -299,7 +301,7 @@ int32_t ccl_label_classes(const uint8_t *img, int32_t H, int32_t W, int64_t pitc
                           int32_t *labels, int32_t *num_components, ccl_stream_t stream)
 {
     if (connectivity != 4 && connectivity != 8)
-        return CCL_ERR_INVALID_ARGUMENT;
+        return CCL_ERR_UNSUPPORTED;
     return label_sync(img, H, W, pitch_bytes, connectivity | CONN_CLASSES, 0, labels, num_components, stream);
 }
 
@@ -345,7 +347,7 @@ int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pi
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (connectivity & CONN_CLASSES)
-        return CCL_ERR_INVALID_ARGUMENT;
+        return CCL_ERR_UNSUPPORTED;
     int32_t rc = check_args(img_host, H, W, pitch_bytes, connectivity, labels_host);
     if (rc != CCL_OK)
         return rc;
@@ -373,7 +375,7 @@ int32_t ccl_label_host_async(const uint8_t *img_host, int32_t H, int32_t W, int6
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (connectivity & CONN_CLASSES)
-        return CCL_ERR_INVALID_ARGUMENT;
+        return CCL_ERR_UNSUPPORTED;
     int32_t rc = check_args(img_host, H, W, pitch_bytes, connectivity, labels_host);
     if (rc != CCL_OK)
         return rc;
@@ -411,11 +413,16 @@ int batch_conn(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn)
     return resolve_conn(conn, all, 1);
 }
 
+int64_t batch_fixed_bytes(int32_t m)
+{
+    return HDR + align256((int64_t)m * (int64_t)sizeof(Img)) + align256(3 * (int64_t)(m + 1) * 8) +
+           align256((int64_t)(m + 1) * 4) + align256((int64_t)MAX_GLOBAL_CTAS * 4);
+}
+
 int64_t batch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn)
 {
     conn = batch_conn(imgs, keep, m, conn);
-    int64_t o = HDR + align256((int64_t)m * (int64_t)sizeof(Img)) + align256(3 * (int64_t)(m + 1) * 8) +
-                align256((int64_t)(m + 1) * 4) + align256((int64_t)MAX_GLOBAL_CTAS * 4);
+    int64_t o = batch_fixed_bytes(m);
     for (int32_t k = 0; k < m; k++)
         o = align256(o + main_layout(imgs[keep[k]].H, imgs[keep[k]].W, conn).bytes);
     return o;
@@ -549,7 +556,7 @@ int32_t label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, int3
             keep.push_back(i);
     }
     if ((connectivity & ~CONN_CLASSES) != 4 && (connectivity & ~CONN_CLASSES) != 8)
-        return CCL_ERR_INVALID_ARGUMENT;
+        return CCL_ERR_UNSUPPORTED;
     if (num_components_dev) {
         for (int32_t i = 0; i < n; i++) {
             if (imgs[i].H == 0 || imgs[i].W == 0) {
@@ -575,7 +582,7 @@ int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, 
                         ccl_stream_t stream)
 {
     if (connectivity & CONN_CLASSES)
-        return CCL_ERR_INVALID_ARGUMENT;
+        return CCL_ERR_UNSUPPORTED;
     return label_batch(imgs, n, connectivity, 0, num_components_dev, stream);
 }
 
@@ -583,7 +590,7 @@ int32_t ccl_label_batch_threshold(const ccl_image *imgs, int32_t n, int32_t conn
                                   int32_t *num_components_dev, ccl_stream_t stream)
 {
     if (connectivity & CONN_CLASSES)
-        return CCL_ERR_INVALID_ARGUMENT;
+        return CCL_ERR_UNSUPPORTED;
     return label_batch(imgs, n, connectivity, threshold, num_components_dev, stream);
 }
 
@@ -591,7 +598,7 @@ int32_t ccl_label_batch_classes(const ccl_image *imgs, int32_t n, int32_t connec
                                 int32_t *num_components_dev, ccl_stream_t stream)
 {
     if (connectivity != 4 && connectivity != 8)
-        return CCL_ERR_INVALID_ARGUMENT;
+        return CCL_ERR_UNSUPPORTED;
     return label_batch(imgs, n, connectivity | CONN_CLASSES, 0, num_components_dev, stream);
 }
 
@@ -614,6 +621,8 @@ int32_t ccl_device_status(ccl_stream_t stream, int32_t *flags)
     *flags = w->host_hdr[1];
     return CCL_OK;
 }
+
+int32_t ccl_shutdown(void) { return ccl_release(); }
 
 int32_t ccl_release(void)
 {

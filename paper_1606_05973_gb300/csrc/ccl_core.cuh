@@ -13,9 +13,11 @@
 //    connected (vertical and diagonal neighbours inside the strip), so each such
 //    "strip run" is one union-find node.
 //  * Algorithm 2 (merge, Rem's union with splicing) joins nodes; the lock of Algorithm 8
-//    becomes a compare-and-swap on the root and splices become atomic minimums.  Links
-//    always go from the larger index to the smaller one, so the root of every set is its
-//    smallest index (the invariant p[x] <= x of Algorithm 2).
+//    becomes a compare-and-swap on the root, and every splice is also a compare-and-swap
+//    of exactly the parent value the thread read (an unconditional splice, or an atomic
+//    minimum, can overwrite a link another thread has just made and lose a union; see
+//    rem_unite_g).  Links always go from the larger index to the smaller one, so the root
+//    of every set is its smallest index (the invariant p[x] <= x of Algorithm 2).
 //  * Runs are numbered per strip in column order, so the run covering a pixel is found
 //    with one popcount.  Links go from the larger number to the smaller, so a local root
 //    is the top-left run of its component; the component's raster-first pixel lies in

@@ -97,6 +97,10 @@ int32_t check_args(const void *img, int32_t H, int32_t W, int64_t pitch, int32_t
 // the batched path on imgs[keep[0..m)] (checked, non-empty); workspace `w` must hold
 // batch_bytes(); K of image keep[k] goes to k_dev[keep[k]] (k_dev may be NULL)
 int64_t batch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn);
+// the part of batch_bytes that does not depend on the images (header, descriptors, prefixes)
+int64_t batch_fixed_bytes(int32_t m);
+// the tile shape a batch of images takes (8-connectivity: by its total pixel count)
+int batch_conn(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn);
 int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
                       Workspace *w, cudaStream_t s);
 

@@ -111,29 +111,40 @@ void bind_workspace(Img &a, const Layout &L, void *ws)
     a.nSeg = L.nSeg;
 }
 
-static int g_num_sms = 0;
+// Per-device state: SM count and the cooperative kernels' resident grid sizes, set once
+// per device (with that device current) by kernels_init.
+constexpr int MAX_DEVICES = 64;
+static int g_num_sms[MAX_DEVICES];
 static std::atomic<int> g_global_per_sm{0};
 
 void set_global_ctas_per_sm(int n) { g_global_per_sm.store(n); }
 
+static int current_device()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
+        return 0;
+    return dev;
+}
+
 // grid of the cooperative global kernel: `need` CTAs, at most `fit` (all resident), and at
 // most the per-SM cap times the SM count when a cap is set
-static int global_grid(int64_t need, int fit)
+static int global_grid(int64_t need, int fit, int dev)
 {
     const int cap = g_global_per_sm.load();
     int64_t g = need < fit ? need : fit;
-    if (cap > 0 && g > (int64_t)cap * g_num_sms)
-        g = (int64_t)cap * g_num_sms;
+    if (cap > 0 && g > (int64_t)cap * g_num_sms[dev])
+        g = (int64_t)cap * g_num_sms[dev];
     return g < 1 ? 1 : (int)g;
 }
 
 template <class C> struct KernState {
-    static int global_ctas, global_batch_ctas;
+    static int global_ctas[MAX_DEVICES], global_batch_ctas[MAX_DEVICES];
 };
-template <class C> int KernState<C>::global_ctas = 0;
-template <class C> int KernState<C>::global_batch_ctas = 0;
+template <class C> int KernState<C>::global_ctas[MAX_DEVICES] = {};
+template <class C> int KernState<C>::global_batch_ctas[MAX_DEVICES] = {};
 
-template <class C> static cudaError_t init_cfg()
+template <class C> static cudaError_t init_cfg(int dev)
 {
     cudaError_t err = cudaFuncSetAttribute(k_tile_local<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)sizeof(SmemL<C>));
@@ -157,39 +168,46 @@ template <class C> static cudaError_t init_cfg()
     if (err == cudaSuccess)
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, k_global_batch<C>, GNT, 0);
     if (err == cudaSuccess) {
-        KernState<C>::global_ctas = std::min(g_num_sms * occ, MAX_GLOBAL_CTAS);
-        KernState<C>::global_batch_ctas = std::min(g_num_sms * occb, MAX_GLOBAL_CTAS);
-        if (KernState<C>::global_ctas < 1 || KernState<C>::global_batch_ctas < 1)
+        KernState<C>::global_ctas[dev] = std::min(g_num_sms[dev] * occ, MAX_GLOBAL_CTAS);
+        KernState<C>::global_batch_ctas[dev] = std::min(g_num_sms[dev] * occb, MAX_GLOBAL_CTAS);
+        if (KernState<C>::global_ctas[dev] < 1 || KernState<C>::global_batch_ctas[dev] < 1)
             err = cudaErrorInvalidConfiguration;
     }
     return err;
 }
 
+// One-time setup per device, done on the first call made with that device current:
+// kernel attributes (dynamic shared memory, carveout) and the resident grid sizes.
 cudaError_t kernels_init()
 {
-    static std::once_flag once;
-    static cudaError_t err = cudaSuccess;
-    std::call_once(once, [] {
-        int dev = 0, coop = 0;
-        err = cudaGetDevice(&dev);
-        if (err == cudaSuccess)
-            err = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (err == cudaSuccess)
-            err = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-        if (err == cudaSuccess && !coop)
-            err = cudaErrorNotSupported;
-        if (err == cudaSuccess)
-            err = init_cfg<MainCfg>();
-        if (err == cudaSuccess)
-            err = init_cfg<NarrowCfg>();
-        if (err == cudaSuccess)
-            err = init_cfg<MainCfg4>();
-        if (err == cudaSuccess)
-            err = init_cfg<MainCfgC8>();
-        if (err == cudaSuccess)
-            err = init_cfg<MainCfgC4>();
+    static std::once_flag once[MAX_DEVICES];
+    static cudaError_t err[MAX_DEVICES];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= MAX_DEVICES)
+        return cudaErrorInvalidDevice;
+    std::call_once(once[dev], [dev] {
+        int coop = 0;
+        cudaError_t r = cudaDeviceGetAttribute(&g_num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (r == cudaSuccess)
+            r = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (r == cudaSuccess && !coop)
+            r = cudaErrorNotSupported;
+        if (r == cudaSuccess)
+            r = init_cfg<MainCfg>(dev);
+        if (r == cudaSuccess)
+            r = init_cfg<NarrowCfg>(dev);
+        if (r == cudaSuccess)
+            r = init_cfg<MainCfg4>(dev);
+        if (r == cudaSuccess)
+            r = init_cfg<MainCfgC8>(dev);
+        if (r == cudaSuccess)
+            r = init_cfg<MainCfgC4>(dev);
+        err[dev] = r;
     });
-    return err;
+    return err[dev];
 }
 
 #define CCL_LAUNCH(kid, ...)                                   \
@@ -224,7 +242,8 @@ template <class C> static cudaError_t launch_label_t(const Img &a, const Layout 
     // the global kernel needs enough threads for its largest phase, and every CTA resident
     const int64_t work = (int64_t)(L.nTY - 1) * a.W + (int64_t)(L.nTX - 1) * a.H;
     const int64_t need = ((work > L.nSeg ? work : L.nSeg) + GNT - 1) / GNT;
-    const int grid = global_grid(need, KernState<C>::global_ctas);
+    const int dev = current_device();
+    const int grid = global_grid(need, KernState<C>::global_ctas[dev], dev);
     Img arg = a;
     void *args[] = {&arg};
     CCL_LAUNCH(KID_GLOBAL, cudaLaunchCooperativeKernel((const void *)k_global<C>, dim3(grid), dim3(GNT), args, 0, s));
@@ -241,7 +260,8 @@ static cudaError_t launch_batch_t(const Batch &B, int64_t tiles, int64_t items, 
         return cudaErrorInvalidValue;
     CCL_LAUNCH(KID_TILE_LOCAL, launch_tiles_b(k_tile_local_batch<C>, (int)tiles, C::NT, sizeof(SmemL<C>), s, B));
     const int64_t need = ((items > segs ? items : segs) + GNT - 1) / GNT;
-    const int grid = global_grid(need, KernState<C>::global_batch_ctas);
+    const int dev = current_device();
+    const int grid = global_grid(need, KernState<C>::global_batch_ctas[dev], dev);
     Batch arg = B;
     void *args[] = {&arg};
     CCL_LAUNCH(KID_GLOBAL,

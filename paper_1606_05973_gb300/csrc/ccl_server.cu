@@ -1,15 +1,22 @@
 // Continuous-batching server over the batched labelling path (declared in include/ccl.h).
 //
-// Lanes: each lane is a CUDA stream with a resident workspace (mem_cap / lanes bytes), a
-// device array for the K of its current launch and a pinned copy of it.  A scheduler
-// thread packs waiting requests (first come, first served) into one batched launch per
-// idle lane.  When a launch's results have reached the host (cudaLaunchHostFunc after the
-// K copy), the requests complete, their latency is recorded, and the lane takes the next
-// requests that have arrived meanwhile.  Launches on different lanes overlap on the GPU.
+// Memory: one device pool of mem_cap bytes, allocated at creation and resident for the
+// server's lifetime.  Every launch reserves one contiguous slice of it (first fit over a
+// free list with coalescing) for its batch's workspace and returns it when its results
+// have reached the host, so a request may use the whole cap and requests are admitted as
+// memory frees up (first come, first served: a request that does not fit yet waits at the
+// head of the queue).
+// Lanes: each lane is a CUDA stream with a device array for the K of its current launch
+// and a pinned copy of it.  A scheduler thread packs waiting requests into one batched
+// launch per idle lane, as many as the largest free slice holds.  When a launch's results
+// have reached the host (cudaLaunchHostFunc after the K copy), the requests complete,
+// their latency is recorded, the slice is freed, and idle lanes take the requests that
+// have arrived meanwhile.  Launches on different lanes overlap on the GPU.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string.h>
@@ -36,13 +43,14 @@ struct Request {
 
 struct Lane {
     cudaStream_t stream = nullptr;
-    Workspace ws;
+    Workspace ws;               // ws.dev / ws.bytes: the pool slice of the current launch
     int32_t *k_dev = nullptr;   // max_batch K values + the batch's status word
     int32_t *k_host = nullptr;  // pinned copy
     std::vector<uint64_t> ids;
     std::vector<ccl_image> imgs;
     std::vector<int32_t> keep;
-    int64_t bytes = 0;
+    int64_t bytes = 0;          // size of the reserved slice
+    int64_t offset = -1;        // its offset in the pool (-1: none)
     bool busy = false;
     ccl_server *srv = nullptr;
 };
@@ -53,6 +61,8 @@ struct ccl_server {
     ccl_server_config cfg;
     int device = 0;
     std::vector<std::unique_ptr<Lane>> lanes;
+    char *pool = nullptr;                 // mem_cap bytes of device memory
+    std::map<int64_t, int64_t> free_list; // offset -> size of free slices (coalesced)
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
     std::deque<uint64_t> pending;
@@ -64,7 +74,7 @@ struct ccl_server {
     // statistics
     std::vector<double> lat_ms;
     int64_t pixels = 0, launches = 0, launched_reqs = 0, inflight_bytes = 0, peak_inflight = 0;
-    int32_t peak_queue = 0;
+    int32_t peak_queue = 0, busy_lanes = 0, peak_busy_lanes = 0;
     bool have_first = false;
     Clock::time_point first_submit, last_done;
 };
@@ -80,6 +90,47 @@ void finish_locked(ccl_server *s, Request &r, int32_t status, int32_t K)
     s->lat_ms.push_back(std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count());
     s->pixels += r.pixels;
     s->last_done = r.t_done;
+}
+
+// ---- pool slices (called with the lock held) -------------------------------------------
+int64_t largest_free_locked(const ccl_server *s)
+{
+    int64_t best = 0;
+    for (const auto &kv : s->free_list)
+        best = std::max(best, kv.second);
+    return best;
+}
+
+// first fit; returns the offset or -1
+int64_t reserve_locked(ccl_server *s, int64_t bytes)
+{
+    for (auto it = s->free_list.begin(); it != s->free_list.end(); ++it) {
+        if (it->second >= bytes) {
+            const int64_t off = it->first, rest = it->second - bytes;
+            s->free_list.erase(it);
+            if (rest > 0)
+                s->free_list[off + bytes] = rest;
+            return off;
+        }
+    }
+    return -1;
+}
+
+void release_locked(ccl_server *s, int64_t off, int64_t bytes)
+{
+    auto it = s->free_list.emplace(off, bytes).first;
+    auto next = std::next(it);
+    if (next != s->free_list.end() && it->first + it->second == next->first) {
+        it->second += next->second;
+        s->free_list.erase(next);
+    }
+    if (it != s->free_list.begin()) {
+        auto prev = std::prev(it);
+        if (prev->first + prev->second == it->first) {
+            prev->second += it->second;
+            s->free_list.erase(it);
+        }
+    }
 }
 
 void CUDART_CB lane_done(void *p)
@@ -99,67 +150,105 @@ void CUDART_CB lane_done(void *p)
                 finish_locked(s, it->second, status, status == CCL_OK ? L->k_host[k] : -1);
         }
         s->inflight_bytes -= L->bytes;
+        release_locked(s, L->offset, L->bytes);
         L->bytes = 0;
+        L->offset = -1;
         L->ids.clear();
         L->busy = false;
+        s->busy_lanes--;
     }
     s->cv_done.notify_all();
     s->cv_sched.notify_one();
 }
 
-// Pack waiting requests into lane L and launch.  Called with the lock held.
+// Pack waiting requests into lane L and launch.  Called with the lock held.  The batch
+// grows, first come first served, while its workspace fits the largest free slice of the
+// pool; the workspace of a batch is the fixed part plus one layout per image, and under
+// 8-connectivity the tile shape (hence every layout) follows the batch's total pixel
+// count, so both candidate sums are kept as the batch grows.
 bool try_launch_locked(ccl_server *s, Lane &L)
 {
     L.imgs.clear();
     L.keep.clear();
     L.ids.clear();
+    const int conn = s->cfg.connectivity;
+    const int64_t room = largest_free_locked(s);
+    int64_t px = 0, sum_n = 0, sum_w = 0;
     while (!s->pending.empty() && (int32_t)L.ids.size() < s->cfg.max_batch) {
         const uint64_t id = s->pending.front();
         Request &r = s->reqs[id];
+        const int32_t m = (int32_t)L.ids.size() + 1;
+        int64_t need, add_n = 0, add_w = 0;
+        if (conn == 8) {
+            add_n = main_layout(r.img.H, r.img.W, 8 | CONN_NARROW).bytes;
+            add_w = main_layout(r.img.H, r.img.W, 8 | CONN_WIDE).bytes;
+            const bool narrow = resolve_conn(8, px + r.pixels, 1) == (8 | CONN_NARROW);
+            need = batch_fixed_bytes(m) + (narrow ? sum_n + add_n : sum_w + add_w);
+        } else {
+            add_n = add_w = main_layout(r.img.H, r.img.W, conn).bytes;
+            need = batch_fixed_bytes(m) + sum_n + add_n;
+        }
+        if (m == 1 && need > s->cfg.mem_cap_bytes) {  // alone larger than the whole pool
+            s->pending.pop_front();
+            finish_locked(s, r, CCL_ERR_TOO_LARGE, -1);
+            s->cv_done.notify_all();
+            continue;
+        }
+        if (need > room)
+            break;  // waits for memory (at the head of the queue if m == 1)
         L.imgs.push_back(r.img);
         L.keep.push_back((int32_t)L.keep.size());
-        const int64_t need = batch_bytes(L.imgs.data(), L.keep.data(), (int32_t)L.keep.size(), s->cfg.connectivity);
-        if (need > L.ws.bytes) {
-            L.imgs.pop_back();
-            L.keep.pop_back();
-            if (L.ids.empty()) {  // alone too large for a lane
-                s->pending.pop_front();
-                finish_locked(s, r, CCL_ERR_TOO_LARGE, -1);
-                s->cv_done.notify_all();
-                continue;
-            }
-            break;
-        }
         L.ids.push_back(id);
+        px += r.pixels;
+        sum_n += add_n;
+        sum_w += add_w;
         s->pending.pop_front();
     }
     const int32_t m = (int32_t)L.ids.size();
     if (m == 0)
         return false;
-    L.bytes = batch_bytes(L.imgs.data(), L.keep.data(), m, s->cfg.connectivity);
-    int32_t rc = enqueue_batch(L.imgs.data(), L.keep.data(), m, s->cfg.connectivity, 0, L.k_dev, &L.ws, L.stream);
-    cudaError_t e = cudaSuccess;
-    if (rc == CCL_OK) {
-        // K values and the status word back to the host, then clear the status word
-        e = cudaMemcpyAsync(L.k_host, L.k_dev, (size_t)m * 4, cudaMemcpyDeviceToHost, L.stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(L.k_host + s->cfg.max_batch, static_cast<char *>(L.ws.dev) + 4, 4,
-                                cudaMemcpyDeviceToHost, L.stream);
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(static_cast<char *>(L.ws.dev) + 4, 0, 4, L.stream);
-        if (e == cudaSuccess)
-            e = cudaLaunchHostFunc(L.stream, lane_done, &L);
-        if (e != cudaSuccess)
-            rc = map_cuda(e);
+    L.bytes = batch_bytes(L.imgs.data(), L.keep.data(), m, conn);
+    L.offset = reserve_locked(s, L.bytes);
+    int32_t rc = CCL_OK;
+    if (L.offset < 0) {
+        rc = CCL_ERR_INTERNAL;  // cannot happen: the batch was sized to the largest free slice
+    } else {
+        L.ws.dev = s->pool + L.offset;
+        L.ws.bytes = L.bytes;
+        // the slice's header may hold an earlier launch's status word
+        cudaError_t e = cudaMemsetAsync(static_cast<char *>(L.ws.dev) + 4, 0, 4, L.stream);
+        rc = map_cuda(e);
+        if (rc == CCL_OK)
+            rc = enqueue_batch(L.imgs.data(), L.keep.data(), m, conn, 0, L.k_dev, &L.ws, L.stream);
+        if (rc == CCL_OK) {
+            // K values and the status word back to the host
+            e = cudaMemcpyAsync(L.k_host, L.k_dev, (size_t)m * 4, cudaMemcpyDeviceToHost, L.stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(L.k_host + s->cfg.max_batch, static_cast<char *>(L.ws.dev) + 4, 4,
+                                    cudaMemcpyDeviceToHost, L.stream);
+            if (e == cudaSuccess)
+                e = cudaLaunchHostFunc(L.stream, lane_done, &L);
+            if (e != cudaSuccess)
+                rc = map_cuda(e);
+        }
     }
     if (rc != CCL_OK) {
         for (uint64_t id : L.ids)
             finish_locked(s, s->reqs[id], rc, -1);
         L.ids.clear();
+        if (L.offset >= 0) {
+            // nothing of this launch may still be in flight on the slice
+            cudaStreamSynchronize(L.stream);
+            release_locked(s, L.offset, L.bytes);
+        }
+        L.offset = -1;
+        L.bytes = 0;
         s->cv_done.notify_all();
         return false;
     }
     L.busy = true;
+    s->busy_lanes++;
+    s->peak_busy_lanes = std::max(s->peak_busy_lanes, s->busy_lanes);
     s->inflight_bytes += L.bytes;
     s->peak_inflight = std::max(s->peak_inflight, s->inflight_bytes);
     s->launches++;
@@ -191,8 +280,6 @@ void free_lanes(ccl_server *s)
     for (auto &L : s->lanes) {
         if (L->stream)
             cudaStreamSynchronize(L->stream);
-        if (L->ws.dev)
-            cudaFree(L->ws.dev);
         if (L->ws.stage)
             cudaFreeHost(L->ws.stage);
         if (L->ws.stage_done)
@@ -205,6 +292,9 @@ void free_lanes(ccl_server *s)
             cudaStreamDestroy(L->stream);
     }
     s->lanes.clear();
+    if (s->pool)
+        cudaFree(s->pool);
+    s->pool = nullptr;
 }
 
 }  // namespace
@@ -213,9 +303,10 @@ extern "C" {
 
 int32_t ccl_server_create(const ccl_server_config *cfg, ccl_server **out)
 {
-    if (!cfg || !out || cfg->mem_cap_bytes <= 0 || cfg->lanes < 1 || cfg->max_batch < 1 || cfg->max_pending < 0 ||
-        (cfg->connectivity != 0 && cfg->connectivity != 4 && cfg->connectivity != 8))
+    if (!cfg || !out || cfg->mem_cap_bytes <= 0 || cfg->lanes < 1 || cfg->max_batch < 1 || cfg->max_pending < 0)
         return CCL_ERR_INVALID_ARGUMENT;
+    if (cfg->connectivity != 0 && cfg->connectivity != 4 && cfg->connectivity != 8)
+        return CCL_ERR_UNSUPPORTED;
     *out = nullptr;
     cudaError_t e = kernels_init();
     if (e != cudaSuccess)
@@ -227,18 +318,22 @@ int32_t ccl_server_create(const ccl_server_config *cfg, ccl_server **out)
     e = cudaGetDevice(&s->device);
     if (e != cudaSuccess)
         return map_cuda(e);
-    const int64_t per_lane = cfg->mem_cap_bytes / cfg->lanes;
+    const int64_t cap = cfg->mem_cap_bytes & ~(int64_t)255;
+    if (cap < 256)
+        return CCL_ERR_INVALID_ARGUMENT;
+    e = cudaMalloc(&s->pool, (size_t)cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->pool = nullptr;
+        return CCL_ERR_OUT_OF_MEMORY;
+    }
+    s->cfg.mem_cap_bytes = cap;
+    s->free_list[0] = cap;
     for (int32_t i = 0; i < cfg->lanes; i++) {
         std::unique_ptr<Lane> L(new Lane);
         L->srv = s.get();
         if (e == cudaSuccess)
             e = cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess)
-            e = cudaMalloc(&L->ws.dev, (size_t)per_lane);
-        if (e == cudaSuccess) {
-            L->ws.bytes = per_lane;
-            e = cudaMemset(L->ws.dev, 0, 256);
-        }
         if (e == cudaSuccess)
             e = cudaMalloc(&L->k_dev, (size_t)(cfg->max_batch + 1) * 4);
         if (e == cudaSuccess)
@@ -352,6 +447,7 @@ int32_t ccl_server_get_stats(ccl_server *s, ccl_server_stats *out)
     out->mean_batch = s->launches ? (double)s->launched_reqs / (double)s->launches : 0.0;
     out->peak_inflight_bytes = s->peak_inflight;
     out->peak_queue = s->peak_queue;
+    out->peak_busy_lanes = s->peak_busy_lanes;
     return CCL_OK;
 }
 
@@ -364,6 +460,7 @@ int32_t ccl_server_reset_stats(ccl_server *s)
     s->pixels = s->launches = s->launched_reqs = 0;
     s->peak_inflight = s->inflight_bytes;
     s->peak_queue = (int32_t)s->pending.size();
+    s->peak_busy_lanes = s->busy_lanes;
     s->have_first = false;
     return CCL_OK;
 }

@@ -61,7 +61,9 @@ extern "C" int32_t ccl_label_static(const uint8_t *img, int32_t H, int32_t W, in
 {
     using namespace ccl;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (H < 0 || W < 0 || (connectivity != 4 && connectivity != 8))
+    if (connectivity != 4 && connectivity != 8)
+        return CCL_ERR_UNSUPPORTED;
+    if (H < 0 || W < 0)
         return CCL_ERR_INVALID_ARGUMENT;
     if (H == 0 || W == 0) {
         if (num_components_dev)
@@ -103,4 +105,30 @@ extern "C" int32_t ccl_label_static(const uint8_t *img, int32_t H, int32_t W, in
     a.gsync = reinterpret_cast<GridSync *>(b + 16);
     bind_workspace(a, L, b + hdr);
     return launch_label(a, L, connectivity, s) == cudaSuccess ? CCL_OK : CCL_ERR_CUDA;
+}
+
+// The status word of the fixed scratch (byte 4 of its header), which the kernels of
+// ccl_label_static set when a loop or a grid barrier hits its cap.  Copied to the caller's
+// host int through a plain copy (the runtime stages a pageable destination itself; nothing
+// is allocated here), then cleared, on `stream`, which is then synchronised.
+extern "C" int32_t ccl_label_static_status(ccl_stream_t stream, int32_t *flags)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!flags)
+        return CCL_ERR_INVALID_ARGUMENT;
+    void *base = nullptr;
+    int32_t rc = static_scratch(&base);
+    if (rc != CCL_OK)
+        return rc;
+    char *b = static_cast<char *>(base);
+    int32_t v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, b + 4, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b + 4, 0, 4, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return CCL_ERR_CUDA;
+    *flags = v;
+    return CCL_OK;
 }

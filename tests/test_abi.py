@@ -61,8 +61,9 @@ def test_argument_checks_need_no_gpu(lib):
     assert lib.ccl_label(p, 4, 4, 3, 8, p, ctypes.byref(k), None) == 1
     assert lib.ccl_label(None, 4, 4, 4, 8, p, ctypes.byref(k), None) == 1
     assert lib.ccl_label(p, 4, 4, 3, 4, p, ctypes.byref(k), None) == 1  # 4-connectivity: same checks
-    assert lib.ccl_label(p, 4, 4, 4, 5, p, ctypes.byref(k), None) == 1
-    assert lib.ccl_label(p, 0, 9, 9, 5, p, ctypes.byref(k), None) == 1  # connectivity checked first
+    assert lib.ccl_label(p, 4, 4, 4, 5, p, ctypes.byref(k), None) == 2  # connectivity: UNSUPPORTED
+    assert lib.ccl_label(p, 0, 9, 9, 5, p, ctypes.byref(k), None) == 2  # connectivity checked first
+    assert lib.ccl_label(p, -1, 4, 4, 6, p, ctypes.byref(k), None) == 2
     for conn in (8, 4):
         k.value = 7
         assert lib.ccl_label(p, 0, 9, 9, conn, p, ctypes.byref(k), None) == 0 and k.value == 0

@@ -65,9 +65,9 @@ def test_argument_errors(ccl):
     buf = torch.zeros(64, dtype=torch.uint8, device="cuda")
     lab = torch.zeros(64, dtype=torch.int32, device="cuda")
     k = ctypes.c_int32(0)
-    assert lib.ccl_label(buf.data_ptr(), 4, 4, 4, 5, lab.data_ptr(), ctypes.byref(k), s) == 1
+    assert lib.ccl_label(buf.data_ptr(), 4, 4, 4, 5, lab.data_ptr(), ctypes.byref(k), s) == 2
     assert lib.ccl_label(buf.data_ptr(), 4, 4, 3, 4, lab.data_ptr(), ctypes.byref(k), s) == 1
-    assert lib.ccl_label(buf.data_ptr(), 4, 4, 4, 6, lab.data_ptr(), ctypes.byref(k), s) == 1
+    assert lib.ccl_label(buf.data_ptr(), 4, 4, 4, 6, lab.data_ptr(), ctypes.byref(k), s) == 2
     assert lib.ccl_label(buf.data_ptr(), 4, 4, 3, 8, lab.data_ptr(), ctypes.byref(k), s) == 1
     assert lib.ccl_label(None, 4, 4, 4, 8, lab.data_ptr(), ctypes.byref(k), s) == 1
     assert lib.ccl_label(buf.data_ptr(), -1, 4, 4, 8, lab.data_ptr(), ctypes.byref(k), s) == 1
