@@ -105,7 +105,7 @@ WORKLOAD_DESC = {
 }
 
 
-def workload_images(name, device=None):
+def workload_images(name, device=None, side=None):
     """The images of workload `name` as (label, image) pairs: uint8 torch tensors on
     `device` when one is given, else numpy arrays on the host.  Thresholded fields are
     smoothed on the GPU whenever one is present (also for host arrays), so that both
@@ -134,7 +134,7 @@ def workload_images(name, device=None):
             else:
                 out.append((f"blobs_sigma{arg:g}", field(8192, 8192, arg, seed)))
     elif name == "big21568":
-        s = S_BIG
+        s = side or S_BIG  # a smaller side keeps the recipe for profiling captures
         out.append(("blobs_sigma16", field(s, s, 16.0, 8)))
         out.append(("bernoulli_p0.6", host(synth.bernoulli(s, s, 0.6, 9))))
         out.append(("serpentine", host(synth.serpentine(s, s))))
@@ -152,12 +152,16 @@ def image_sha256(img):
     return synth.sha256(img)
 
 
-def make_workload(name, device, only=None):
+def make_workload(name, device, only=None, side=None):
     """Returns (list of (label, uint8 CUDA tensor), description dict with input SHA-256s)."""
-    imgs = workload_images(name, device)
+    imgs = workload_images(name, device, side)
     if only:
         imgs = [(n, t) for n, t in imgs if n == only]
     desc = {**WORKLOAD_DESC[name], "inputs_sha256": {n: image_sha256(t) for n, t in imgs}}
+    if side and name == "big21568" and side != S_BIG:
+        desc = {**desc, "H": side, "W": side,
+                "workload": desc["workload"].replace("21568x21568 uint8 (~465 MB, Table III image_6 size)",
+                                                     f"{side}x{side} uint8 (the 21568x21568 recipe at a smaller side)")}
     return imgs, desc
 
 
@@ -296,7 +300,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     lib = ccl.lib()
-    imgs, desc = make_workload(args.workload, dev, args.only)
+    imgs, desc = make_workload(args.workload, dev, args.only, args.side)
     desc = conn_desc(desc, args.connectivity)
     if args.only:
         imgs = [(n, t) for n, t in imgs if n == args.only]
@@ -992,6 +996,8 @@ def main():
     ap.add_argument("--connectivity", type=int, choices=[8, 4], default=8,
                     help="8 (the paper's) or 4; the reference arm supports 8 only")
     ap.add_argument("--only", default=None, help="keep one image of the workload (profiling)")
+    ap.add_argument("--side", type=int, default=None,
+                    help="big21568 only: the same three images at a smaller side (profiling captures)")
     ap.add_argument("--batch-images", type=int, default=4096,
                     help="size of the uneven-batch comparison (0 skips it)")
     ap.add_argument("--no-served", dest="served", action="store_false", help="skip the serving measurement")

@@ -86,6 +86,26 @@ CCL_HD int lane_id()
     return emu_lane();
 #endif
 }
+// number of threads of the CTA for which p holds; every thread of the CTA calls it (it is a
+// barrier).  The emulator counts in *slot, a shared int no other thread uses meanwhile.
+CCL_HD int cta_count(bool p, int *slot, int tid)
+{
+#if defined(__CUDA_ARCH__)
+    (void)slot;
+    (void)tid;
+    return __syncthreads_count(p ? 1 : 0);
+#else
+    if (tid == 0)
+        __atomic_store_n(slot, 0, __ATOMIC_SEQ_CST);
+    emu_cta_sync();
+    if (p)
+        __atomic_fetch_add(slot, 1, __ATOMIC_SEQ_CST);
+    emu_cta_sync();
+    const int n = __atomic_load_n(slot, __ATOMIC_SEQ_CST);
+    emu_cta_sync();
+    return n;
+#endif
+}
 // all 32 lanes of the warp must call these together
 CCL_HD uint32_t warp_ballot(bool p)
 {
@@ -308,9 +328,12 @@ CCL_HD uint32_t eq_nibble(uint32_t a, uint32_t b)
     const uint32_t m = ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u;
     return ((m >> 7) * 0x10204080u) >> 28;
 }
-// 16 bytes -> 16 object bits (bit i = byte i > T), c as in gt_nibble
-CCL_HD uint32_t gt_mask16(const uint8_t *src, uint32_t c)
+// 16 bytes -> 16 object bits (bit i = byte i > T), c as in gt_nibble.  NZ: T = 0 (c is all
+// ones), which the compiler then folds to the plain non-zero test.
+template <bool NZ = false> CCL_HD uint32_t gt_mask16(const uint8_t *src, uint32_t c)
 {
+    if (NZ)
+        c = 0xFFFFFFFFu;
     uint32_t v[4];
 #if defined(__CUDA_ARCH__)
     const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(src));
@@ -444,6 +467,7 @@ template <class C> struct SmemCls<C, true> {
 template <class C> struct SmemL : SmemRuns<C>, SmemCls<C> {
     uint32_t par[C::RMAX];           // union-find parents (see above)
     int ucount[33];                  // union phase: units per event count, then bucket starts
+    int red;                         // cta_count's slot (host emulation only)
     uint16_t uorder[C::NT];          // union phase: units of a chunk by event count
     uint32_t rootbits[C::TH][C::NW]; // first pixels of the local components
     int rootpre[C::TH][C::NW];       // exclusive popcount prefix of rootbits along a row
@@ -534,22 +558,10 @@ template <class C> struct Tile {
         const uint32_t c = (uint32_t)(255 - a.thr) * 0x01010101u;  // object = byte > thr
         if (full) {
             // interior tile: issue every 16-byte load before using any of them
-            uint32_t m[PER];
-#pragma unroll
-            for (int i = 0; i < PER; i++) {
-                const int q = tid + i * C::NT;
-                m[i] = 0;
-                if (q < C::TH * C::CH) {
-                    const int r = q / C::CH, cc = q % C::CH;
-                    m[i] = gt_mask16(a.img + (int64_t)(y0 + r) * a.pitch + x0 + 16 * cc, c);
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < PER; i++) {
-                const int q = tid + i * C::NT;
-                if (q < C::TH * C::CH)
-                    half[q] = (uint16_t)m[i];
-            }
+            if (a.thr == 0)
+                load_full<true, PER>(a, half, y0, x0, c, tid);
+            else
+                load_full<false, PER>(a, half, y0, x0, c, tid);
         } else {
             for (int q = tid; q < C::TH * C::CH; q += C::NT) {
                 const int r = q / C::CH, cc = q % C::CH;
@@ -570,8 +582,27 @@ template <class C> struct Tile {
         }
         for (int q = tid; q < C::TH * C::NW; q += C::NT)
             (&s.rootbits[0][0])[q] = 0u;
-        for (int q = tid; q < C::RMAX; q += C::NT)
-            s.par[q] = PAR_HI | (uint32_t)q;
+    }
+
+    template <bool NZ, int PER>
+    CCL_HD static void load_full(const Img &a, uint16_t *half, int y0, int x0, uint32_t c, int tid)
+    {
+        uint32_t m[PER];
+#pragma unroll
+        for (int i = 0; i < PER; i++) {
+            const int q = tid + i * C::NT;
+            m[i] = 0;
+            if (q < C::TH * C::CH) {
+                const int r = q / C::CH, cc = q % C::CH;
+                m[i] = gt_mask16<NZ>(a.img + (int64_t)(y0 + r) * a.pitch + x0 + 16 * cc, c);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PER; i++) {
+            const int q = tid + i * C::NT;
+            if (q < C::TH * C::CH)
+                half[q] = (uint16_t)m[i];
+        }
     }
 
     // Multi-class load: the tile's bytes into shared memory, then per (row, word) the object
@@ -641,8 +672,6 @@ template <class C> struct Tile {
             }
             for (int q = tid; q < C::TH * C::NW; q += C::NT)
                 (&s.rootbits[0][0])[q] = 0u;
-            for (int q = tid; q < C::RMAX; q += C::NT)
-                s.par[q] = PAR_HI | (uint32_t)q;
         } else {
             (void)a;
             (void)s;
@@ -735,7 +764,12 @@ template <class C> struct Tile {
 
     // -- phase: strip run starts, and how many runs of the strip start before each word.
     // The NW words of a strip sit in NW consecutive lanes, so the prefix is a shuffle scan.
-    CCL_HD static void strip_runs(SR &s, int tid)
+    // The tile pass also makes every run it numbers a union-find root here (par holds an
+    // entry only for runs that exist; no phase reads the entry of a run that does not).
+    CCL_HD static void strip_runs(SL &s, int tid) { strip_runs_t<true>(s, s.par, tid); }
+    CCL_HD static void strip_runs(SF &s, int tid) { strip_runs_t<false>(s, nullptr, tid); }
+
+    template <bool INIT> CCL_HD static void strip_runs_t(SR &s, uint32_t *par, int tid)
     {
         static_assert(32 % C::NW == 0 && C::NT % 32 == 0, "a strip's words must share a warp");
         for (int u0 = 0; u0 < C::NS * C::NW; u0 += C::NT) {
@@ -749,6 +783,11 @@ template <class C> struct Tile {
             if (ok) {
                 s.starts[st][w] = st_bits;
                 s.rpre[st][w] = incl - c;
+                if constexpr (INIT) {
+                    const int v0 = st * C::RC + incl - c;
+                    for (int k = 0; k < c; k++)
+                        par[v0 + k] = PAR_HI | (uint32_t)(v0 + k);
+                }
             }
         }
     }
@@ -911,24 +950,30 @@ template <class C> struct Tile {
             // A warp's loop below runs as long as its busiest lane, so the chunk's units are
             // first ordered by their number of events (a counting sort) and thread t takes
             // the t-th: each warp then holds units of about the same length.
+            // The sort pays only when some units have several events; a chunk without
+            // events (sparse or run-aligned content) skips the loop altogether.
             UnitEvents e = unit_events(s, u0 + tid);
-            for (int q = tid; q < 33; q += C::NT)
-                s.ucount[q] = 0;
-            cta_sync();
             const int key = popc32(e.ev1 | e.ev2);
-            const int rank = at_add(&s.ucount[key], 1);
-            cta_sync();
-            if (tid < 32) {
-                const int c = s.ucount[tid];
-                const int incl = warp_incl_sum(c, 32);
-                s.ucount[tid] = incl - c;
-                if (tid == 31)
-                    s.ucount[32] = incl;
+            if (cta_count(key > 2, &s.red, tid) > 0) {
+                for (int q = tid; q < 33; q += C::NT)
+                    s.ucount[q] = 0;
+                cta_sync();
+                const int rank = at_add(&s.ucount[key], 1);
+                cta_sync();
+                if (tid < 32) {
+                    const int c = s.ucount[tid];
+                    const int incl = warp_incl_sum(c, 32);
+                    s.ucount[tid] = incl - c;
+                    if (tid == 31)
+                        s.ucount[32] = incl;
+                }
+                cta_sync();
+                s.uorder[s.ucount[key] + rank] = (uint16_t)tid;
+                cta_sync();
+                e = unit_events(s, u0 + s.uorder[tid]);
+            } else if (cta_count(key > 0, &s.red, tid) == 0) {
+                continue;
             }
-            cta_sync();
-            s.uorder[s.ucount[key] + rank] = (uint16_t)tid;
-            cta_sync();
-            e = unit_events(s, u0 + s.uorder[tid]);
             uint32_t ev1 = e.ev1, ev2 = e.ev2;
             const uint32_t A = e.A, sA = e.sA, sB = e.sB;
             const int baseA = e.baseA, baseB = e.baseB;
