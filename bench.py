@@ -621,6 +621,29 @@ def measure_plain(args, name, dev, lib):
         gms = g0.elapsed_time(g1) / reps
         res["graph_replay"] = {"us_per_image": round(gms * 1e3, 2), "value": round(px / (gms * 1e-3) / 1e9, 2),
                                "how": f"one ccl_label_async call captured in a CUDA graph, {reps} replays"}
+        # the same with the three-kernel path forced (ccl_set_launch_mode(1)), for comparison
+        lib.ccl_set_launch_mode(1)
+        g3 = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(main):
+            step(1)
+            main.synchronize()
+            with torch.cuda.graph(g3, stream=main):
+                step(1)
+            g3.replay()
+            torch.cuda.synchronize()
+            h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h0.record(main)
+            for _ in range(reps):
+                g3.replay()
+            h1.record(main)
+        torch.cuda.synchronize()
+        lib.ccl_set_launch_mode(0)
+        status()
+        if int(kdev[0]) != ref_k:
+            raise RuntimeError("three-kernel graph replay changed K")
+        tms = h0.elapsed_time(h1) / reps
+        res["graph_replay_three_launches"] = {"us_per_image": round(tms * 1e3, 2),
+                                              "value": round(px / (tms * 1e-3) / 1e9, 2)}
     lib.ccl_set_global_ctas_per_sm(args.global_ctas_per_sm or 0)
     return res
 
@@ -820,27 +843,69 @@ def measure_batched(args, dev, lib, stream):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    reps = max(2, min(args.steps, 5))
-    with torch.cuda.stream(stream):
-        ms_single = timed(per_image, reps)
-        ms_batch = timed(batched, reps)
-        ref_k = kd_single.clone()
-        # CUDA graph of the batch call (the workspace is already sized); replayed on `stream`
+    def status():
+        flags = ctypes.c_int32(0)
+        if lib.ccl_device_status(sptr, ctypes.byref(flags)) != 0 or flags.value:
+            raise RuntimeError(f"device status {flags.value} in the batched measurement")
+
+    def graph_ms(fn, reps):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
-            batched()
+            fn()
         kd_batch.fill_(-1)
-        ms_graph = timed(g.replay, reps)
-    if not torch.equal(kd_batch, ref_k):
-        raise RuntimeError("batched and per-image component counts differ")
-    return {"workload": f"{len(imgs)} uint8 images, H and W each log-uniform in [64, 2048], "
-                        "p ~ U(0.2, 0.8), half Bernoulli / half sigma in {2,4,8} blobs, seed 100",
-            "images": len(imgs), "pixels": int(px),
-            "per_image_ms": round(ms_single, 3), "batched_ms": round(ms_batch, 3),
-            "batched_graph_ms": round(ms_graph, 3),
-            "gpx_s_per_image": round(px / ms_single / 1e6, 2), "gpx_s_batched": round(px / ms_batch / 1e6, 2),
-            "gpx_s_batched_graph": round(px / ms_graph / 1e6, 2),
-            "speedup_batched_graph_vs_per_image": round(ms_single / ms_graph, 2)}
+        ms = timed(g.replay, reps)
+        if not torch.equal(kd_batch, ref_k):
+            raise RuntimeError("graph replay changed the component counts")
+        return ms
+
+    reps = max(2, min(args.steps, 5))
+    res = {"workload": f"{len(imgs)} uint8 images, H and W each log-uniform in [64, 2048], "
+                       "p ~ U(0.2, 0.8), half Bernoulli / half sigma in {2,4,8} blobs, seed 100",
+           "images": len(imgs), "pixels": int(px)}
+    with torch.cuda.stream(stream):
+        ms_single = timed(per_image, reps)
+        ref_k = kd_single.clone()
+        status()
+        out = {}
+        for mode, tag in ((0, "persistent"), (1, "three_launches")):
+            lib.ccl_set_launch_mode(mode)
+            kd_batch.fill_(-1)
+            ms_b = timed(batched, reps)
+            if not torch.equal(kd_batch, ref_k):
+                raise RuntimeError(f"{tag} batch and per-image component counts differ")
+            ms_g = graph_ms(batched, reps)
+            status()
+            out[tag] = {"ms": round(ms_b, 3), "graph_ms": round(ms_g, 3),
+                        "gpx_s": round(px / ms_b / 1e6, 2), "gpx_s_graph": round(px / ms_g / 1e6, 2)}
+        # a 64-image batch (the first 64 images) both ways, as a CUDA graph
+        sub, sub_labs = imgs[:64], labs[:64]
+        sub_px = sum(t.numel() for t in sub)
+        k64 = torch.zeros(64, dtype=torch.int32, device=dev)
+        small = {}
+        for mode, tag in ((0, "persistent"), (1, "three_launches")):
+            lib.ccl_set_launch_mode(mode)
+
+            def b64():
+                ccl.label_batch(sub, connectivity=args.connectivity, outs=sub_labs, stream=stream, k_out=k64)
+
+            b64()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                b64()
+            ms = timed(g.replay, 20)
+            if not torch.equal(k64, ref_k[:64]):
+                raise RuntimeError("64-image batch component counts differ")
+            small[tag] = {"graph_ms": round(ms, 4), "gpx_s": round(sub_px / ms / 1e6, 2)}
+        lib.ccl_set_launch_mode(0)
+        status()
+    res.update({"per_image_ms": round(ms_single, 3), "gpx_s_per_image": round(px / ms_single / 1e6, 2),
+                "batched_ms": out["persistent"]["ms"], "batched_graph_ms": out["persistent"]["graph_ms"],
+                "gpx_s_batched": out["persistent"]["gpx_s"], "gpx_s_batched_graph": out["persistent"]["gpx_s_graph"],
+                "speedup_batched_graph_vs_per_image": round(ms_single / out["persistent"]["graph_ms"], 2),
+                "modes": out, "batch64": {"pixels": int(sub_px), **small},
+                "how": "per-image: one ccl_label_async call per image; persistent: one ccl_label_batch call "
+                       "(one cooperative launch); three_launches: the same call with ccl_set_launch_mode(1)"})
+    return res
 
 
 # ---- CPU oracle ---------------------------------------------------------------------------

@@ -153,10 +153,20 @@ typedef struct {
 } ccl_image;
 
 /*
- * ccl_label_batch - label n images (uneven sizes allowed) on one stream.
+ * ccl_label_batch - label n images (uneven sizes allowed) on one stream, in ONE persistent
+ * cooperative kernel launch: the tile pass (Algorithms 6 and 2 per tile), the boundary
+ * merge (Algorithms 7-8), flatten (Algorithm 3) and the labelling pass run back to back in
+ * one grid, separated by grid barriers, with tiles handed out from a counter.  The tile
+ * shape comes from the library's tuning table (written by an offline sweep,
+ * paper_1606_05973_gb300/tuning.json): a row per size class (the batch's pixel count)
+ * gives a shape per density class, and when they differ a probe at the start of the
+ * launch (the object fraction of 64 samples of 16 bytes per image) picks the class.
  *   imgs               HOST array of n descriptors (device pointers inside)
  *   num_components_dev DEVICE int32[n] or NULL; entry i receives K of image i
- * Asynchronous; results are identical to labelling each image alone.
+ * Asynchronous and capturable in a CUDA graph once the stream's workspace is large enough
+ * (make one uncaptured call of the same or a larger batch first); results are identical
+ * to labelling each image alone.  ccl_set_launch_mode(1) selects the earlier form (three
+ * kernel launches per batch) instead.
  */
 int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity,
                         int32_t *num_components_dev, ccl_stream_t stream);
@@ -299,6 +309,16 @@ int32_t ccl_shutdown(void);
 int32_t ccl_set_global_ctas_per_sm(int32_t n);
 
 /*
+ * ccl_set_launch_mode - how the path is launched.  0 (the default): a batch is one
+ * persistent launch (see ccl_label_batch), and so is a single image of at most the tuning
+ * table's single-image size (small images are bound by launch and barrier latency); larger
+ * single images take three kernels (tile pass, cooperative global pass, final pass).
+ * 1: always three kernels.  Labels are identical in both modes.  Process-wide; applies to
+ * calls made after it.  CCL_ERR_INVALID_ARGUMENT for other values.
+ */
+int32_t ccl_set_launch_mode(int32_t mode);
+
+/*
  * ccl_set_tile_policy - the tile shape of the 8-connected path (the partitions that
  * Algorithm 7 labels independently before its boundary merge).  policy 0 (the default)
  * chooses by size: images of at most 3072 x 3072 pixels take 64 x 128 tiles, larger ones
@@ -307,8 +327,9 @@ int32_t ccl_set_global_ctas_per_sm(int32_t n);
  * idle.  A batch takes one shape for all its images, by the same rule on its total pixel
  * count (a batch of 4096 images up to 2048 x 2048 takes wide tiles).  1 = always
  * 64 x 256, 2 = always 64 x 128 (for tests and tuning).  Labels are identical under every
- * policy.  Process-wide; applies to calls made after it.  CCL_ERR_INVALID_ARGUMENT for
- * other values.
+ * policy.  Under the persistent launch (ccl_set_launch_mode 0) policy 0 takes the tuning
+ * table's shape and 1 / 2 force one shape as here.  Process-wide; applies to calls made
+ * after it.  CCL_ERR_INVALID_ARGUMENT for other values.
  */
 int32_t ccl_set_tile_policy(int32_t policy);
 

@@ -8,6 +8,7 @@ out-of-range index sets a status bit and the access is skipped.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import json
 import os
 import shutil
 import subprocess
@@ -38,17 +39,53 @@ def _stale(target: str) -> bool:
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(HERE, "..", "include", "ccl.h"))
     deps.append(os.path.abspath(__file__))
+    deps.append(TUNING)
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
+
+
+TUNING = os.path.join(HERE, "tuning.json")
+SHAPES = {"64x128": 0, "64x256": 1}
+
+
+def tuning_source(path: str = TUNING) -> str:
+    """The tuning table as C (the initialisers ccl_kernels.cu includes)."""
+    with open(path) as f:
+        t = json.load(f)
+    lo, hi = (int(round(1024 * float(b))) for b in t["density_bounds"])
+    rows = []
+    for r in t["rows"]:
+        shape = [SHAPES[x] for x in r["shape"]]
+        assert len(shape) == 3 and int(r["ctas_per_sm"]) >= 1
+        mx = -1 if r["max_px"] is None else int(r["max_px"])
+        rows.append(f"    {{{mx}LL, {{{shape[0]}, {shape[1]}, {shape[2]}}}, {int(r['ctas_per_sm'])}}},")
+    assert rows and t["rows"][-1]["max_px"] is None, "the last row must have no bound"
+    return "\n".join([
+        "// written by paper_1606_05973_gb300/build.py from tuning.json; do not edit",
+        "static const TuneRow kTuneRows[] = {", *rows, "};",
+        f"static const int kTuneDensLo = {lo}, kTuneDensHi = {hi};",
+        f"static const int kTuneProbeSamples = {int(t['probe_samples'])};",
+        f"static const int64_t kTuneSingleFusedMaxPx = {int(t['single_fused_max_px'])}LL;", ""])
+
+
+def write_tuning_include() -> str:
+    os.makedirs(OUT, exist_ok=True)
+    path = os.path.join(OUT, "ccl_tuning.inc")
+    src = tuning_source()
+    if not os.path.exists(path) or open(path).read() != src:
+        with open(path, "w") as f:
+            f.write(src)
+    return path
 
 
 def build(debug: bool = False, force: bool = False, verbose: bool = False) -> str:
     target = lib_path(debug)
+    write_tuning_include()
     if not force and not _stale(target):
         return target
     os.makedirs(OUT, exist_ok=True)
     tag = "dbg" if debug else "rel"
     flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-             "--expt-relaxed-constexpr", *ARCH]
+             "--expt-relaxed-constexpr", "-I", OUT, *ARCH]
     if debug:
         flags.append("-DCCL_DEBUG")
     if verbose:

@@ -1,6 +1,7 @@
 // C ABI of the labelling library (declared in include/ccl.h): argument checks, workspace
 // management, the launch sequence per image, host-buffer and batch entry points, and the
 // kernel timing hooks.
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -138,6 +139,231 @@ int32_t enqueue_one(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int
     return map_cuda(launch_label(a, L, conn, s));
 }
 
+// ---- persistent single-launch path ---------------------------------------------------------
+// Workspace of a persistent launch over m images: header, rank offsets (imgBase), CTA sums,
+// for m > 1 the descriptors and prefix arrays of both tile shapes, then one region per
+// image large enough for the layout of either shape.
+int64_t fused_fixed_bytes(int32_t m)
+{
+    int64_t o = HDR + align256((int64_t)(m + 1) * 4) + align256((int64_t)MAX_GLOBAL_CTAS * 4);
+    if (m > 1)
+        o += 2 * (align256((int64_t)m * (int64_t)sizeof(Img)) + align256(3 * (int64_t)(m + 1) * 8));
+    return o;
+}
+
+int64_t fused_image_bytes(int32_t H, int32_t W, int conn)
+{
+    if (conn != 8)
+        return main_layout(H, W, conn).bytes;
+    const int64_t n = main_layout(H, W, 8 | CONN_NARROW).bytes, w = main_layout(H, W, 8 | CONN_WIDE).bytes;
+    return n > w ? n : w;
+}
+
+int64_t fused_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn)
+{
+    int64_t o = fused_fixed_bytes(m);
+    for (int32_t k = 0; k < m; k++)
+        o = align256(o + fused_image_bytes(imgs[keep[k]].H, imgs[keep[k]].W, conn));
+    return o;
+}
+
+static void fill_img(Img &a, const ccl_image &im, int thr, int32_t *k, char *dev)
+{
+    memset(&a, 0, sizeof(a));
+    a.img = im.img;
+    a.pitch = im.pitch_bytes;
+    a.H = im.H;
+    a.W = im.W;
+    a.thr = thr;
+    a.vec_in = ((reinterpret_cast<uintptr_t>(im.img) & 15) == 0) && (im.pitch_bytes % 16 == 0);
+    a.labels = im.labels;
+    a.vec_out = ((reinterpret_cast<uintptr_t>(im.labels) & 15) == 0) && (im.W % 4 == 0);
+    a.K = k;
+    a.status = reinterpret_cast<int *>(dev + 4);
+    a.gsync = nullptr;
+}
+
+// Enqueue one persistent launch for images imgs[keep[0..m)] (checked, non-empty; conn is the
+// caller's 8, 4 or either | CONN_CLASSES) on `s` with workspace `w` (at least fused_bytes).
+// Binary 8-connectivity compiles both tile shapes into the kernel; the tuning row of the
+// batch's pixel count says which shape each density class takes, and when they differ the
+// kernel's probe decides.  A single image travels inline in the kernel arguments (nothing
+// is uploaded); a batch's descriptors go up through the workspace's pinned staging buffer.
+int32_t enqueue_fused(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
+                      Workspace *w, cudaStream_t s)
+{
+    cudaError_t e = kernels_init();
+    if (e != cudaSuccess)
+        return map_cuda(e);
+    int64_t px = 0;
+    for (int32_t k = 0; k < m; k++)
+        px += (int64_t)imgs[keep[k]].H * imgs[keep[k]].W;
+    const TuneRow &row = tune_row(px);
+    FusedArgs f;
+    memset(&f, 0, sizeof(f));
+    const bool two = conn == 8;
+    for (int c = 0; c < 3; c++)
+        f.pick[c] = two ? (tile_policy() == 1 ? 1 : tile_policy() == 2 ? 0 : row.shape[c]) : 0;
+    const bool probe = f.pick[0] != f.pick[1] || f.pick[1] != f.pick[2];
+    f.probe_samples = probe ? tuning().probe_samples : 0;
+    f.dens_lo = tuning().dens_lo;
+    f.dens_hi = tuning().dens_hi;
+
+    char *dev = static_cast<char *>(w->dev);
+    const int64_t base_bytes = align256((int64_t)(m + 1) * 4);
+    int *imgBase = reinterpret_cast<int *>(dev + HDR);
+    int *bsum = reinterpret_cast<int *>(dev + HDR + base_bytes);
+    const int64_t desc_bytes = align256((int64_t)m * (int64_t)sizeof(Img));
+    const int64_t pre_bytes = align256(3 * (int64_t)(m + 1) * 8);
+    const int64_t set_bytes = desc_bytes + pre_bytes;
+    char *desc_dev = dev + HDR + base_bytes + align256((int64_t)MAX_GLOBAL_CTAS * 4);
+    int64_t o = fused_fixed_bytes(m);
+    const int nsets = two ? 2 : 1;
+    std::vector<Img> hd[2];
+    std::vector<int64_t> pre[2];
+    int64_t need_ctas = 1;
+    for (int k = 0; k < nsets; k++) {
+        hd[k].resize(m);
+        pre[k].assign(3 * (size_t)(m + 1), 0);
+    }
+    for (int32_t i = 0; i < m; i++) {
+        const ccl_image &im = imgs[keep[i]];
+        for (int k = 0; k < nsets; k++) {
+            const Layout L = main_layout(im.H, im.W, two ? (8 | (k ? CONN_WIDE : CONN_NARROW)) : conn);
+            Img &a = hd[k][i];
+            fill_img(a, im, thr, k_dev ? k_dev + keep[i] : nullptr, dev);
+            bind_workspace(a, L, dev + o);
+            int64_t *t = pre[k].data(), *it = t + (m + 1), *sg = t + 2 * (m + 1);
+            t[i + 1] = t[i] + (int64_t)L.nTX * L.nTY;
+            it[i + 1] = it[i] + (int64_t)(L.nTY - 1) * im.W + (int64_t)(L.nTX - 1) * im.H;
+            sg[i + 1] = sg[i] + L.nSeg;
+        }
+        o = align256(o + fused_image_bytes(im.H, im.W, conn));
+    }
+    if (o > w->bytes)
+        return CCL_ERR_OUT_OF_MEMORY;
+    for (int k = 0; k < nsets; k++) {
+        const int64_t *t = pre[k].data();
+        const int64_t tiles = t[m], items = t[2 * (m + 1) - 1], segs = t[3 * (m + 1) - 1];
+        const int64_t big = items > segs ? items : segs;
+        const int64_t c = std::max<int64_t>(tiles, (big + fused_threads() - 1) / fused_threads());
+        need_ctas = std::max(need_ctas, c);
+        if (tiles > 0x7FFFFFFF)
+            return CCL_ERR_UNSUPPORTED;
+    }
+    if (m > 1) {
+        // descriptors and prefixes of both shapes, one upload from the pinned staging buffer
+        int capturing = 0;
+        {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+                capturing = 1;
+        }
+        if (w->stage_pending && !capturing) {
+            e = cudaEventSynchronize(w->stage_done);
+            if (e != cudaSuccess)
+                return map_cuda(e);
+            w->stage_pending = false;
+        }
+        const int64_t stage_need = nsets * set_bytes;
+        if (w->stage_bytes < stage_need) {
+            if (w->stage)
+                cudaFreeHost(w->stage);
+            w->stage = nullptr;
+            w->stage_bytes = 0;
+            e = cudaMallocHost(&w->stage, (size_t)stage_need);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return CCL_ERR_OUT_OF_MEMORY;
+            }
+            w->stage_bytes = stage_need;
+        }
+        if (!w->stage_done) {
+            e = cudaEventCreateWithFlags(&w->stage_done, cudaEventDisableTiming);
+            if (e != cudaSuccess)
+                return map_cuda(e);
+        }
+        char *host = static_cast<char *>(w->stage);
+        for (int k = 0; k < nsets; k++) {
+            memcpy(host + k * set_bytes, hd[k].data(), (size_t)m * sizeof(Img));
+            memcpy(host + k * set_bytes + desc_bytes, pre[k].data(), 3 * (size_t)(m + 1) * 8);
+        }
+        e = cudaMemcpyAsync(desc_dev, host, (size_t)stage_need, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess)
+            return map_cuda(e);
+        if (!capturing) {
+            e = cudaEventRecord(w->stage_done, s);
+            if (e != cudaSuccess)
+                return map_cuda(e);
+            w->stage_pending = true;
+        }
+    }
+    for (int k = 0; k < 2; k++) {
+        const int src = k < nsets ? k : 0;
+        Batch &B = f.set[k];
+        B.n = m;
+        B.imgBase = imgBase;
+        B.bsum = bsum;
+        B.gsync = reinterpret_cast<GridSync *>(dev + 16);
+        B.status = reinterpret_cast<int *>(dev + 4);
+        if (m == 1) {
+            B.inl = 1;
+            B.one = hd[src][0];
+            B.one_tiles = pre[src][1];
+            B.one_items = pre[src][3];
+            B.one_segs = pre[src][5];
+        } else {
+            char *d = desc_dev + src * set_bytes;
+            B.imgs = reinterpret_cast<const Img *>(d);
+            const int64_t *dp = reinterpret_cast<const int64_t *>(d + desc_bytes);
+            B.tileStart = dp;
+            B.itemStart = dp + (m + 1);
+            B.segStart = dp + 2 * (m + 1);
+        }
+    }
+    e = cudaMemsetAsync(dev + 16, 0, sizeof(GridSync), s);  // barrier, counters, probe
+    if (e != cudaSuccess)
+        return map_cuda(e);
+    const int resident = fused_resident_ctas(conn);
+    if (resident < 1)
+        return CCL_ERR_CUDA;
+    int64_t grid = std::min<int64_t>(need_ctas, resident);
+    grid = std::min<int64_t>(grid, (int64_t)row.ctas_per_sm * sm_count());
+    return map_cuda(launch_fused(f, conn, (int)std::max<int64_t>(grid, 1), s));
+}
+
+// The single-image path for H x W under `conn` (the caller's connectivity): the persistent
+// launch for images up to the tuned size (unless three launches are forced), else the three
+// kernels with the tile shape of the size rule.  bytes includes the header.
+SinglePlan plan_single(int32_t H, int32_t W, int conn)
+{
+    SinglePlan p;
+    p.fused = launch_mode() == 0 && (int64_t)H * W <= tuning().single_fused_max_px;
+    if (p.fused) {
+        p.conn = conn;
+        p.bytes = fused_fixed_bytes(1) + fused_image_bytes(H, W, conn);
+    } else {
+        p.conn = resolve_conn(conn, H, W);
+        p.bytes = HDR + main_layout(H, W, p.conn).bytes;
+    }
+    return p;
+}
+
+int32_t enqueue_single(const SinglePlan &P, const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t thr,
+                       int32_t *labels, int32_t *k_dev, Workspace *w, cudaStream_t s)
+{
+    if (!P.fused)
+        return enqueue_one(img, H, W, pitch, P.conn, thr, labels, k_dev, w, static_cast<char *>(w->dev) + HDR, s);
+    ccl_image im;
+    im.img = img;
+    im.H = H;
+    im.W = W;
+    im.pitch_bytes = pitch;
+    im.labels = labels;
+    const int32_t keep = 0;
+    return enqueue_fused(&im, &keep, 1, P.conn, thr, k_dev, w, s);
+}
+
 int32_t read_k_and_status(Workspace *w, const int32_t *k_dev, int32_t *num_components, cudaStream_t s)
 {
     cudaError_t e = cudaMemcpyAsync(w->host_hdr, k_dev, 4, cudaMemcpyDeviceToHost, s);
@@ -235,19 +461,18 @@ int32_t ccl_label_async(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_
     int32_t rc = check_args(img, H, W, pitch_bytes, connectivity, labels);
     if (rc != CCL_OK)
         return rc;
-    connectivity = resolve_conn(connectivity, H, W);  // one tile shape for sizing and launch
     if (H == 0 || W == 0) {
         if (num_components_dev)
             return map_cuda(cudaMemsetAsync(num_components_dev, 0, 4, s));
         return CCL_OK;
     }
+    const SinglePlan P = plan_single(H, W, connectivity);  // one plan for sizing and launch
     Workspace *w = nullptr;
-    rc = get_workspace(s, HDR + main_layout(H, W, connectivity).bytes, &w);
+    rc = get_workspace(s, P.bytes, &w);
     if (rc != CCL_OK)
         return rc;
     int32_t *k_dev = num_components_dev ? num_components_dev : static_cast<int32_t *>(w->dev);
-    return enqueue_one(img, H, W, pitch_bytes, connectivity, 0, labels, k_dev, w,
-                       static_cast<char *>(w->dev) + HDR, s);
+    return enqueue_single(P, img, H, W, pitch_bytes, 0, labels, k_dev, w, s);
 }
 
 namespace {
@@ -261,19 +486,18 @@ int32_t label_sync(const uint8_t *img, int32_t H, int32_t W, int64_t pitch_bytes
     int32_t rc = check_args(img, H, W, pitch_bytes, connectivity, labels);
     if (rc != CCL_OK)
         return rc;
-    connectivity = resolve_conn(connectivity, H, W);  // one tile shape for sizing and launch
     if (H == 0 || W == 0) {
         if (num_components)
             *num_components = 0;
         return CCL_OK;
     }
+    const SinglePlan P = plan_single(H, W, connectivity);  // one plan for sizing and launch
     Workspace *w = nullptr;
-    rc = get_workspace(s, HDR + main_layout(H, W, connectivity).bytes, &w);
+    rc = get_workspace(s, P.bytes, &w);
     if (rc != CCL_OK)
         return rc;
     int32_t *k_dev = static_cast<int32_t *>(w->dev);
-    rc = enqueue_one(img, H, W, pitch_bytes, connectivity, thr, labels, k_dev, w, static_cast<char *>(w->dev) + HDR,
-                     s);
+    rc = enqueue_single(P, img, H, W, pitch_bytes, thr, labels, k_dev, w, s);
     if (rc != CCL_OK || !num_components)
         return rc;
     return read_k_and_status(w, k_dev, num_components, s);
@@ -312,23 +536,23 @@ namespace {
 int32_t host_enqueue(const uint8_t *img_host, int32_t H, int32_t W, int64_t pitch_bytes, int32_t connectivity,
                      int32_t *labels_host, cudaStream_t s, Workspace **w_out, int32_t **k_dev_out)
 {
-    const Layout L = main_layout(H, W, connectivity);
+    const SinglePlan P = plan_single(H, W, connectivity);
     const int64_t dpitch = (W + 15) & ~(int64_t)15;
     const int64_t img_bytes = align256((int64_t)H * dpitch);
     const int64_t lab_bytes = align256((int64_t)H * W * 4);
     Workspace *w = nullptr;
-    int32_t rc = get_workspace(s, HDR + L.bytes + img_bytes + lab_bytes, &w);
+    int32_t rc = get_workspace(s, align256(P.bytes) + img_bytes + lab_bytes, &w);
     if (rc != CCL_OK)
         return rc;
     char *base = static_cast<char *>(w->dev);
-    uint8_t *d_img = reinterpret_cast<uint8_t *>(base + HDR + L.bytes);
-    int32_t *d_lab = reinterpret_cast<int32_t *>(base + HDR + L.bytes + img_bytes);
+    uint8_t *d_img = reinterpret_cast<uint8_t *>(base + align256(P.bytes));
+    int32_t *d_lab = reinterpret_cast<int32_t *>(base + align256(P.bytes) + img_bytes);
     cudaError_t e = cudaMemcpy2DAsync(d_img, (size_t)dpitch, img_host, (size_t)pitch_bytes, (size_t)W,
                                       (size_t)H, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess)
         return map_cuda(e);
     int32_t *k_dev = reinterpret_cast<int32_t *>(base);
-    rc = enqueue_one(d_img, H, W, dpitch, connectivity, 0, d_lab, k_dev, w, base + HDR, s);
+    rc = enqueue_single(P, d_img, H, W, dpitch, 0, d_lab, k_dev, w, s);
     if (rc != CCL_OK)
         return rc;
     e = cudaMemcpyAsync(labels_host, d_lab, (size_t)H * W * 4, cudaMemcpyDeviceToHost, s);
@@ -351,7 +575,6 @@ int32_t ccl_label_host(const uint8_t *img_host, int32_t H, int32_t W, int64_t pi
     int32_t rc = check_args(img_host, H, W, pitch_bytes, connectivity, labels_host);
     if (rc != CCL_OK)
         return rc;
-    connectivity = resolve_conn(connectivity, H, W);  // one tile shape for sizing and launch
     if (H == 0 || W == 0) {
         if (num_components)
             *num_components = 0;
@@ -379,7 +602,6 @@ int32_t ccl_label_host_async(const uint8_t *img_host, int32_t H, int32_t W, int6
     int32_t rc = check_args(img_host, H, W, pitch_bytes, connectivity, labels_host);
     if (rc != CCL_OK)
         return rc;
-    connectivity = resolve_conn(connectivity, H, W);  // one tile shape for sizing and launch
     if (H == 0 || W == 0) {
         if (num_components_host)
             *num_components_host = 0;
@@ -520,6 +742,7 @@ int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int
         w->stage_pending = true;
     }
     Batch B;
+    memset(&B, 0, sizeof(B));
     B.n = m;
     B.imgs = reinterpret_cast<const Img *>(dev + HDR);
     const int64_t *dpre = reinterpret_cast<const int64_t *>(dev + HDR + desc_bytes);
@@ -531,6 +754,19 @@ int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int
     B.gsync = reinterpret_cast<GridSync *>(dev + 16);
     B.status = reinterpret_cast<int *>(dev + 4);
     return map_cuda(launch_batch(B, tileStart[m], itemStart[m], segStart[m], conn, s));
+}
+
+int64_t launch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn)
+{
+    return launch_mode() == 0 ? fused_bytes(imgs, keep, m, conn) : batch_bytes(imgs, keep, m, conn);
+}
+
+int32_t enqueue_launch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
+                       Workspace *w, cudaStream_t s)
+{
+    if (launch_mode() == 0)
+        return enqueue_fused(imgs, keep, m, conn, thr, k_dev, w, s);
+    return enqueue_batch(imgs, keep, m, conn, thr, k_dev, w, s);
 }
 
 }  // namespace ccl
@@ -570,10 +806,10 @@ int32_t label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, int3
     if (m == 0)
         return CCL_OK;
     Workspace *w = nullptr;
-    int32_t rc = get_workspace(s, batch_bytes(imgs, keep.data(), m, connectivity), &w);
+    int32_t rc = get_workspace(s, launch_bytes(imgs, keep.data(), m, connectivity), &w);
     if (rc != CCL_OK)
         return rc;
-    return enqueue_batch(imgs, keep.data(), m, connectivity, thr, num_components_dev, w, s);
+    return enqueue_launch(imgs, keep.data(), m, connectivity, thr, num_components_dev, w, s);
 }
 
 }  // namespace
@@ -647,6 +883,14 @@ int32_t ccl_set_tile_policy(int32_t policy)
     if (policy < 0 || policy > 2)
         return CCL_ERR_INVALID_ARGUMENT;
     set_tile_policy(policy);
+    return CCL_OK;
+}
+
+int32_t ccl_set_launch_mode(int32_t mode)
+{
+    if (mode < 0 || mode > 1)
+        return CCL_ERR_INVALID_ARGUMENT;
+    set_launch_mode(mode);
     return CCL_OK;
 }
 

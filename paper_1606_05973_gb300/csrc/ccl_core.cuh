@@ -1434,24 +1434,38 @@ constexpr int GNT = CCL_GLOBAL_NT;
 constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 constexpr int GNT_LOG = ilog2(GNT);
 static_assert((1 << GNT_LOG) == GNT, "global CTA size must be a power of two");
-struct ScanBuf {
-    int v[2][GNT];
+template <int N> struct ScanBufT {
+    int v[2][N];
 };
-CCL_HD void scan_put(ScanBuf &s, int tid, int x) { s.v[0][tid] = x; }
-CCL_HD void scan_step(ScanBuf &s, int tid, int k)
+using ScanBuf = ScanBufT<GNT>;
+template <int N> CCL_HD void scan_put(ScanBufT<N> &s, int tid, int x) { s.v[0][tid] = x; }
+template <int N> CCL_HD void scan_step(ScanBufT<N> &s, int tid, int k)
 {
     const int d = 1 << k;
     const int src = k & 1;
     s.v[src ^ 1][tid] = s.v[src][tid] + (tid >= d ? s.v[src][tid - d] : 0);
 }
-// inclusive result after GNT_LOG steps lives in buffer GNT_LOG & 1
-CCL_HD int scan_incl(const ScanBuf &s, int tid) { return s.v[GNT_LOG & 1][tid]; }
+// inclusive result after ilog2(N) steps lives in buffer ilog2(N) & 1
+template <int N> CCL_HD int scan_incl(const ScanBufT<N> &s, int tid) { return s.v[ilog2(N) & 1][tid]; }
+// the whole scan: every thread of the CTA (N threads) puts x and gets its inclusive sum
+template <int N> CCL_HD int cta_incl_scan(ScanBufT<N> &s, int tid, int x)
+{
+    scan_put(s, tid, x);
+    cta_sync();
+    for (int k = 0; k < ilog2(N); k++) {
+        scan_step(s, tid, k);
+        cta_sync();
+    }
+    return scan_incl(s, tid);
+}
 
 // Grid-wide state of the global kernel, in the workspace header.  k_tile_local zeroes it
 // before every use (it runs first on the same stream).
 struct GridSync {
     unsigned arrive;
     int round_more[MAX_ROUNDS];
+    int work_next[2];  // persistent kernel: next tile of its tile phase / of its final phase
+    int probe[2];      // persistent kernel: object bytes / bytes in the density probe
 };
 static_assert(16 + sizeof(GridSync) <= 256, "grid state must fit the 256-byte workspace header");
 
@@ -1685,6 +1699,16 @@ struct Batch {
     GridSync *gsync;
     int *bsum;
     int *status;
+    // A batch of one image may carry its descriptor and sizes inline (inl != 0): then
+    // imgs and the three prefix arrays are not used (and find_img never reads them for
+    // n == 1), so a single-image launch needs no descriptor upload.
+    int inl;
+    Img one;
+    int64_t one_tiles, one_items, one_segs;
+    CCL_HD const Img &img(int m) const { return inl ? one : imgs[m]; }
+    CCL_HD int64_t tile_start(int k) const { return inl ? (k ? one_tiles : 0) : tileStart[k]; }
+    CCL_HD int64_t item_start(int k) const { return inl ? (k ? one_items : 0) : itemStart[k]; }
+    CCL_HD int64_t seg_start(int k) const { return inl ? (k ? one_segs : 0) : segStart[k]; }
 };
 
 // largest i in [0, n) with start[i] <= x (empty images share their start with the next)
@@ -1711,8 +1735,8 @@ template <class C> CCL_HD void batch_tile_local_body(const Batch &B, TileCtx &ct
 {
     if (tid == 0) {
         const int m = find_img(B.tileStart, B.n, bid);
-        ctx.img = B.imgs[m];
-        ctx.tile = (int)(bid - B.tileStart[m]);
+        ctx.img = B.img(m);
+        ctx.tile = (int)(bid - B.tile_start(m));
     }
     if (bid == 0) {
         unsigned *g = reinterpret_cast<unsigned *>(B.gsync);
@@ -1727,8 +1751,8 @@ template <class C> CCL_HD void batch_final_body(const Batch &B, TileCtx &ctx, Sm
 {
     if (tid == 0) {
         const int m = find_img(B.tileStart, B.n, bid);
-        ctx.img = B.imgs[m];
-        ctx.tile = (int)(bid - B.tileStart[m]);
+        ctx.img = B.img(m);
+        ctx.tile = (int)(bid - B.tile_start(m));
         ctx.img.label_base = ld_g(&B.imgBase[m]);
         if (ctx.tile == 0 && ctx.img.K)
             *ctx.img.K = ld_g(&B.imgBase[m + 1]) - ctx.img.label_base;
@@ -1737,72 +1761,64 @@ template <class C> CCL_HD void batch_final_body(const Batch &B, TileCtx &ctx, Sm
     final_body<C>(ctx.img, s, ctx.tile, tid);
 }
 
-template <class C> CCL_HD void batch_global_body(const Batch &B, ScanBuf &sb, int &s_flag, int b, int G, int tid)
+// The global phases over a batch for CTA b of G CTAs of NTG threads; `epoch` counts the
+// grid barriers this CTA has passed (the persistent kernel continues its count).
+template <class C, int NTG>
+CCL_HD void batch_global_phase(const Batch &B, ScanBufT<NTG> &sb, int &s_flag, int b, int G, int tid,
+                               unsigned &epoch)
 {
-    unsigned epoch = 0;
     GridSync *g = B.gsync;
-    const int64_t stride = (int64_t)G * GNT;
+    const int64_t stride = (int64_t)G * NTG;
     const int n = B.n;
 
     // a3: boundary merge over the items of all images
-    const int64_t nitems = B.itemStart[n];
+    const int64_t nitems = B.item_start(n);
     int m = 0;
-    for (int64_t i = (int64_t)b * GNT + tid; i < nitems; i += stride) {
-        if (i >= B.itemStart[m + 1] || i < B.itemStart[m])
+    for (int64_t i = (int64_t)b * NTG + tid; i < nitems; i += stride) {
+        if (i >= B.item_start(m + 1) || i < B.item_start(m))
             m = find_img(B.itemStart, n, i);
-        const Img &a = B.imgs[m];
+        const Img &a = B.img(m);
         const int64_t nh = (int64_t)(a.nTY - 1) * a.W;
-        apply_edge_item<C>(a, load_edge_item<C>(a, i - B.itemStart[m], nh));
+        apply_edge_item<C>(a, load_edge_item<C>(a, i - B.item_start(m), nh));
     }
     grid_sync(g, (unsigned)G, epoch, B.status, tid);
 
     // a4 + a5: first jump round and root count over a contiguous range of the batch's
     // segments, then the scan across the CTA and across CTAs
-    const int64_t nsegs = B.segStart[n];
+    const int64_t nsegs = B.seg_start(n);
     int64_t s0, s1;
-    seg_range(nsegs, G, GNT, b, tid, &s0, &s1);
+    seg_range(nsegs, G, NTG, b, tid, &s0, &s1);
     const int m0 = (s0 < nsegs) ? find_img(B.segStart, n, s0) : n - 1;
     int c = 0;
     bool more = false;
     m = m0;
     for (int64_t seg = s0; seg < s1; seg++) {
-        while (seg >= B.segStart[m + 1])
+        while (seg >= B.seg_start(m + 1))
             m++;
-        more |= jump_segment<C>(B.imgs[m], seg - B.segStart[m], &c);
+        more |= jump_segment<C>(B.img(m), seg - B.seg_start(m), &c);
     }
     if (more)
         flag_status(&g->round_more[0], 1);
-    scan_put(sb, tid, c);
-    cta_sync();
-    for (int k = 0; k < GNT_LOG; k++) {
-        scan_step(sb, tid, k);
-        cta_sync();
-    }
-    const int incl = scan_incl(sb, tid);
-    if (tid == GNT - 1)
+    const int incl = cta_incl_scan(sb, tid, c);
+    if (tid == NTG - 1)
         st_g(&B.bsum[b], incl);
     grid_sync(g, (unsigned)G, epoch, B.status, tid);
     if (b == 0) {
-        const int per = (G + GNT - 1) / GNT;
+        const int per = (G + NTG - 1) / NTG;
         const int lo = tid * per < G ? tid * per : G;
         const int hi = lo + per < G ? lo + per : G;
         int acc = 0;
         for (int i = lo; i < hi; i++)
             acc += ld_g(&B.bsum[i]);
-        scan_put(sb, tid, acc);
-        cta_sync();
-        for (int k = 0; k < GNT_LOG; k++) {
-            scan_step(sb, tid, k);
-            cta_sync();
-        }
-        int run = scan_incl(sb, tid) - acc;
+        const int tot = cta_incl_scan(sb, tid, acc);
+        int run = tot - acc;
         for (int i = lo; i < hi; i++) {
             const int t = ld_g(&B.bsum[i]);
             st_g(&B.bsum[i], run);
             run += t;
         }
-        if (tid == GNT - 1)
-            st_g(&B.imgBase[n], scan_incl(sb, tid));
+        if (tid == NTG - 1)
+            st_g(&B.imgBase[n], tot);
     }
     grid_sync(g, (unsigned)G, epoch, B.status, tid);
     // roots get -(batch rank + 1); the thread that meets an image's first segment records
@@ -1810,12 +1826,12 @@ template <class C> CCL_HD void batch_global_body(const Batch &B, ScanBuf &sb, in
     int run = ld_g(&B.bsum[b]) + incl - c;
     m = m0;
     for (int64_t seg = s0; seg < s1; seg++) {
-        while (seg >= B.segStart[m + 1])
+        while (seg >= B.seg_start(m + 1))
             m++;
-        if (seg == B.segStart[m])
+        if (seg == B.seg_start(m))
             st_g(&B.imgBase[m], run);
-        const int64_t ls = seg - B.segStart[m];
-        run = label_roots<C>(B.imgs[m], ls, ls + 1, run);
+        const int64_t ls = seg - B.seg_start(m);
+        run = label_roots<C>(B.img(m), ls, ls + 1, run);
     }
 
     for (int r = 0; r < MAX_ROUNDS - 1; r++) {
@@ -1830,15 +1846,167 @@ template <class C> CCL_HD void batch_global_body(const Batch &B, ScanBuf &sb, in
         int dummy = 0;
         m = m0;
         for (int64_t seg = s0; seg < s1; seg++) {
-            while (seg >= B.segStart[m + 1])
+            while (seg >= B.seg_start(m + 1))
                 m++;
-            more_r |= jump_segment<C>(B.imgs[m], seg - B.segStart[m], &dummy);
+            more_r |= jump_segment<C>(B.img(m), seg - B.seg_start(m), &dummy);
         }
         if (more_r)
             flag_status(&g->round_more[r + 1], 1);
         grid_sync(g, (unsigned)G, epoch, B.status, tid);
         if (r == MAX_ROUNDS - 2 && tid == 0 && b == 0 && ld_g(&g->round_more[r + 1]))
             flag_status(B.status, ST_LOOP_CAP);
+    }
+}
+
+template <class C> CCL_HD void batch_global_body(const Batch &B, ScanBuf &sb, int &s_flag, int b, int G, int tid)
+{
+    unsigned epoch = 0;
+    batch_global_phase<C, GNT>(B, sb, s_flag, b, G, tid, epoch);
+}
+
+// ---- one persistent launch for a batch (or a single image) -------------------------------
+// The phases of k_tile_local, k_global and k_final run back to back in one cooperative grid
+// of CTAs of C::NT threads, separated by grid barriers.  Tiles are handed out one at a time
+// from a counter (work_next), so CTAs that draw cheap tiles take more of them.  Two tile
+// shapes CA and CB can be compiled into one kernel: a density probe at the start (the
+// object fraction of a few 16-byte samples of every image) picks the shape for the whole
+// launch from the classes the host passes (a row of the tuning table).
+template <class A, class B> struct same_t {
+    static constexpr bool value = false;
+};
+template <class A> struct same_t<A, A> {
+    static constexpr bool value = true;
+};
+
+struct FusedArgs {
+    Batch set[2];          // the batch laid out for tile shape CA (0) and CB (1)
+    int pick[3];           // shape (0 or 1) per density class: fraction < lo, < hi, >= hi
+    int dens_lo, dens_hi;  // class bounds: object fraction in 1/1024
+    int probe_samples;     // 16-byte samples per image; 0: no probe, shape pick[0]
+};
+
+template <class CA, class CB> union FusedSmemU {
+    SmemL<CA> la;
+    SmemF<CA> fa;
+    SmemL<CB> lb;
+    SmemF<CB> fb;
+    ScanBufT<CA::NT> sb;
+};
+template <class CA, class CB> struct FusedSmem {
+    FusedSmemU<CA, CB> u;
+    TileCtx ctx;
+    int next;
+    int flag;
+    int acc[2];
+};
+
+// Object fraction of the batch from probe_samples 16-byte samples per image (sample k of
+// an image: row k*H/samples, a column from a multiplicative hash of k); returns the shape
+// of its density class.  All CTAs take the same decision after one grid barrier.
+template <class CA, class CB>
+CCL_HD int fused_probe(const FusedArgs &f, FusedSmem<CA, CB> &sm, int b, int G, int tid, unsigned &epoch)
+{
+    const Batch &B = f.set[0];
+    if (f.probe_samples <= 0)
+        return f.pick[0];
+    if (tid == 0) {
+        sm.acc[0] = 0;
+        sm.acc[1] = 0;
+    }
+    cta_sync();
+    const int64_t total = (int64_t)B.n * f.probe_samples;
+    int fg = 0, all = 0;
+    for (int64_t j = (int64_t)b * CA::NT + tid; j < total; j += (int64_t)G * CA::NT) {
+        const int m = (int)(j / f.probe_samples), k = (int)(j % f.probe_samples);
+        const Img &a = B.img(m);
+        const int y = (int)((int64_t)k * a.H / f.probe_samples);
+        const int span = a.W < 16 ? a.W : 16;
+        const int x = a.W > 16 ? (int)(((uint32_t)k * 2654435761u) % (uint32_t)(a.W - 15)) : 0;
+        const uint8_t *src = a.img + (int64_t)y * a.pitch + x;
+        for (int i = 0; i < span; i++)
+            fg += (int)src[i] > a.thr ? 1 : 0;
+        all += span;
+    }
+    if (all)
+        at_add(&sm.acc[1], all);
+    if (fg)
+        at_add(&sm.acc[0], fg);
+    cta_sync();
+    if (tid == 0) {
+        at_add(&B.gsync->probe[0], sm.acc[0]);
+        at_add(&B.gsync->probe[1], sm.acc[1]);
+    }
+    grid_sync(B.gsync, (unsigned)G, epoch, B.status, tid);
+    const int64_t obj = ld_g(&B.gsync->probe[0]), seen = ld_g(&B.gsync->probe[1]);
+    const int64_t d = seen > 0 ? obj * 1024 / seen : 0;
+    const int cls = d < f.dens_lo ? 0 : (d < f.dens_hi ? 1 : 2);
+    return f.pick[cls];
+}
+
+// every phase of the path over batch B laid out for tile shape C
+template <class C, class S>
+CCL_HD void fused_run(const Batch &B, S &sm, SmemL<C> &sl, SmemF<C> &sf, int b, int G, int tid, unsigned &epoch)
+{
+    GridSync *g = B.gsync;
+    const int ntiles = (int)B.tile_start(B.n);
+    // rows a1, a2: tiles from the counter
+    for (;;) {
+        if (tid == 0) {
+            const int t = at_add(&g->work_next[0], 1);
+            sm.next = t;
+            if (t < ntiles) {
+                const int m = find_img(B.tileStart, B.n, t);
+                sm.ctx.img = B.img(m);
+                sm.ctx.img.gsync = nullptr;  // the grid state is in use: no reset by tile 0
+                sm.ctx.tile = (int)(t - B.tile_start(m));
+            }
+        }
+        cta_sync();
+        if (sm.next >= ntiles)
+            break;
+        tile_local_body<C>(sm.ctx.img, sl, sm.ctx.tile, tid);
+        cta_sync();
+    }
+    grid_sync(g, (unsigned)G, epoch, B.status, tid);
+    // rows a3, a4, a5 (global part)
+    batch_global_phase<C, C::NT>(B, sm.u.sb, sm.flag, b, G, tid, epoch);
+    grid_sync(g, (unsigned)G, epoch, B.status, tid);  // the root labels are written
+    // row a5 (final part): tiles from the second counter
+    for (;;) {
+        if (tid == 0) {
+            const int t = at_add(&g->work_next[1], 1);
+            sm.next = t;
+            if (t < ntiles) {
+                const int m = find_img(B.tileStart, B.n, t);
+                sm.ctx.img = B.img(m);
+                sm.ctx.tile = (int)(t - B.tile_start(m));
+                sm.ctx.img.label_base = ld_g(&B.imgBase[m]);
+                if (sm.ctx.tile == 0 && sm.ctx.img.K)
+                    *sm.ctx.img.K = ld_g(&B.imgBase[m + 1]) - sm.ctx.img.label_base;
+            }
+        }
+        cta_sync();
+        if (sm.next >= ntiles)
+            break;
+        final_body<C>(sm.ctx.img, sf, sm.ctx.tile, tid);
+        cta_sync();
+    }
+}
+
+template <class CA, class CB>
+CCL_HD void fused_body(const FusedArgs &f, FusedSmem<CA, CB> &sm, int b, int G, int tid)
+{
+    static_assert(CA::NT == CB::NT, "both tile shapes run with the same CTA size");
+    unsigned epoch = 0;
+    const int shape = fused_probe<CA, CB>(f, sm, b, G, tid, epoch);
+    if constexpr (same_t<CA, CB>::value) {
+        (void)shape;
+        fused_run<CA>(f.set[0], sm, sm.u.la, sm.u.fa, b, G, tid, epoch);
+    } else {
+        if (shape == 0)
+            fused_run<CA>(f.set[0], sm, sm.u.la, sm.u.fa, b, G, tid, epoch);
+        else
+            fused_run<CB>(f.set[1], sm, sm.u.lb, sm.u.fb, b, G, tid, epoch);
     }
 }
 

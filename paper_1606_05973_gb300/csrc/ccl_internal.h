@@ -15,6 +15,7 @@ enum KernelId {
     KID_TILE_LOCAL = 0,  // image -> bit tiles, local union-find, local roots, run codes, edges
     KID_GLOBAL,          // boundary merge, flatten, root scan and labels (cooperative grid)
     KID_FINAL,           // label of every strip run, int32 labels
+    KID_FUSED,           // all of the above in one persistent cooperative launch
     KID_COUNT
 };
 const char *kernel_name(int kid);
@@ -70,8 +71,39 @@ cudaError_t launch_label(const Img &a, const Layout &L, int conn, cudaStream_t s
 // Enqueue the batched path: tiles, boundary items and segments summed over the batch.
 cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, int conn, cudaStream_t s);
 
-// One-time per-process setup of kernel attributes (dynamic shared memory).
+// One-time per-device setup of kernel attributes (dynamic shared memory).
 cudaError_t kernels_init();
+
+// ---- persistent single-launch path (k_fused) ---------------------------------------------
+// A row of the tuning table: batches of at most max_px pixels in all (-1: no bound) take
+// tile shape shape[c] for density class c (0: 64 x 128, 1: 64 x 256; 8-connectivity only)
+// and a grid of ctas_per_sm CTAs per SM (at most what fits).
+struct TuneRow {
+    int64_t max_px;
+    int shape[3];
+    int ctas_per_sm;
+};
+struct Tuning {
+    const TuneRow *rows;
+    int nrows;
+    int dens_lo, dens_hi;     // density class bounds, object fraction in 1/1024
+    int probe_samples;        // 16-byte samples per image for the density probe
+    int64_t single_fused_max_px;  // single images up to this size take the persistent launch
+};
+const Tuning &tuning();
+const TuneRow &tune_row(int64_t px);
+// resident CTAs of the persistent kernel for `conn` on the current device (0 on error)
+int fused_resident_ctas(int conn);
+int fused_threads();
+// Enqueue one persistent launch of f (grid CTAs); conn selects the kernel (8: both binary
+// shapes; 4; classes).  The grid state in f.set[0].gsync must be zero.
+cudaError_t launch_fused(const FusedArgs &f, int conn, int grid, cudaStream_t s);
+// SMs of the current device
+int sm_count();
+// process-wide launch mode: 0 = automatic (persistent launch for batches and for single
+// images up to the tuned size), 1 = always the three kernels
+void set_launch_mode(int m);
+int launch_mode();
 
 // CTAs of the global kernel per SM (0: as many as fit); read at every launch.
 void set_global_ctas_per_sm(int n);
@@ -103,5 +135,25 @@ int64_t batch_fixed_bytes(int32_t m);
 int batch_conn(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn);
 int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
                       Workspace *w, cudaStream_t s);
+// the persistent launch: workspace bytes (fixed part and one image's region) and enqueue
+int64_t fused_fixed_bytes(int32_t m);
+int64_t fused_image_bytes(int32_t H, int32_t W, int conn);
+int64_t fused_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn);
+int32_t enqueue_fused(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
+                      Workspace *w, cudaStream_t s);
+// a batch launch in the current launch mode (persistent or three kernels)
+int64_t launch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn);
+int32_t enqueue_launch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
+                       Workspace *w, cudaStream_t s);
+// how one image is labelled: persistent launch or three kernels (conn then carries the tile
+// shape); bytes of workspace, header included
+struct SinglePlan {
+    bool fused;
+    int conn;
+    int64_t bytes;
+};
+SinglePlan plan_single(int32_t H, int32_t W, int conn);
+int32_t enqueue_single(const SinglePlan &P, const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t thr,
+                       int32_t *labels, int32_t *k_dev, Workspace *w, cudaStream_t s);
 
 }  // namespace ccl

@@ -19,6 +19,7 @@ const char *kernel_name(int kid)
     case KID_TILE_LOCAL: return "tile_local";
     case KID_GLOBAL: return "global_merge_flatten";
     case KID_FINAL: return "final_labels";
+    case KID_FUSED: return "persistent";
     default: return "?";
     }
 }
@@ -64,6 +65,14 @@ template <class C> __global__ void __launch_bounds__(C::NT, 2048 / C::NT) k_fina
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TileCtx ctx;
     batch_final_body<C>(B, ctx, *reinterpret_cast<SmemF<C> *>(smem_raw), blockIdx.x, threadIdx.x);
+}
+
+// One persistent cooperative launch for the whole path (a batch, or one image); CA and CB
+// are the two tile shapes it may take (the same type when there is one).
+template <class CA, class CB> __global__ void __launch_bounds__(CA::NT, 2048 / CA::NT) k_fused(FusedArgs f)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fused_body<CA, CB>(f, *reinterpret_cast<FusedSmem<CA, CB> *>(smem_raw), blockIdx.x, gridDim.x, threadIdx.x);
 }
 
 static std::atomic<int> g_tile_policy{0};
@@ -176,6 +185,28 @@ template <class C> static cudaError_t init_cfg(int dev)
     return err;
 }
 
+template <class CA, class CB> struct FusedState {
+    static int resident[MAX_DEVICES];
+};
+template <class CA, class CB> int FusedState<CA, CB>::resident[MAX_DEVICES] = {};
+
+template <class CA, class CB> static cudaError_t init_fused(int dev)
+{
+    const int smem = (int)sizeof(FusedSmem<CA, CB>);
+    cudaError_t err = cudaFuncSetAttribute(k_fused<CA, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_fused<CA, CB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int occ = 0;
+    if (err == cudaSuccess)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused<CA, CB>, CA::NT, smem);
+    if (err == cudaSuccess) {
+        FusedState<CA, CB>::resident[dev] = std::min(g_num_sms[dev] * occ, MAX_GLOBAL_CTAS);
+        if (FusedState<CA, CB>::resident[dev] < 1)
+            err = cudaErrorInvalidConfiguration;
+    }
+    return err;
+}
+
 // One-time setup per device, done on the first call made with that device current:
 // kernel attributes (dynamic shared memory, carveout) and the resident grid sizes.
 cudaError_t kernels_init()
@@ -205,6 +236,14 @@ cudaError_t kernels_init()
             r = init_cfg<MainCfgC8>(dev);
         if (r == cudaSuccess)
             r = init_cfg<MainCfgC4>(dev);
+        if (r == cudaSuccess)
+            r = init_fused<NarrowCfg, MainCfg>(dev);
+        if (r == cudaSuccess)
+            r = init_fused<MainCfg4, MainCfg4>(dev);
+        if (r == cudaSuccess)
+            r = init_fused<MainCfgC8, MainCfgC8>(dev);
+        if (r == cudaSuccess)
+            r = init_fused<MainCfgC4, MainCfgC4>(dev);
         err[dev] = r;
     });
     return err[dev];
@@ -289,6 +328,59 @@ cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t s
     case 8 | CONN_CLASSES: return launch_batch_t<MainCfgC8>(B, tiles, items, segs, s);
     case 4 | CONN_CLASSES: return launch_batch_t<MainCfgC4>(B, tiles, items, segs, s);
     default: return launch_batch_t<MainCfg>(B, tiles, items, segs, s);
+    }
+}
+
+// ---- persistent launch -------------------------------------------------------------------
+#include "ccl_tuning.inc"  // kTuneRows and the kTune* constants, written from tuning.json by build.py
+
+static const Tuning g_tuning = {kTuneRows, (int)(sizeof(kTuneRows) / sizeof(kTuneRows[0])), kTuneDensLo,
+                                kTuneDensHi, kTuneProbeSamples, kTuneSingleFusedMaxPx};
+const Tuning &tuning() { return g_tuning; }
+
+const TuneRow &tune_row(int64_t px)
+{
+    for (int i = 0; i < g_tuning.nrows; i++)
+        if (g_tuning.rows[i].max_px < 0 || px <= g_tuning.rows[i].max_px)
+            return g_tuning.rows[i];
+    return g_tuning.rows[g_tuning.nrows - 1];
+}
+
+static std::atomic<int> g_launch_mode{0};
+void set_launch_mode(int m) { g_launch_mode.store(m); }
+int launch_mode() { return g_launch_mode.load(); }
+int sm_count() { return g_num_sms[current_device()]; }
+
+int fused_threads() { return MainCfg::NT; }
+
+int fused_resident_ctas(int conn)
+{
+    const int dev = current_device();
+    switch (conn & ~(CONN_NARROW | CONN_WIDE)) {
+    case 4: return FusedState<MainCfg4, MainCfg4>::resident[dev];
+    case 8 | CONN_CLASSES: return FusedState<MainCfgC8, MainCfgC8>::resident[dev];
+    case 4 | CONN_CLASSES: return FusedState<MainCfgC4, MainCfgC4>::resident[dev];
+    default: return FusedState<NarrowCfg, MainCfg>::resident[dev];
+    }
+}
+
+template <class CA, class CB> static cudaError_t launch_fused_t(const FusedArgs &f, int grid, cudaStream_t s)
+{
+    FusedArgs arg = f;
+    void *args[] = {&arg};
+    CCL_LAUNCH(KID_FUSED, cudaLaunchCooperativeKernel((const void *)k_fused<CA, CB>, dim3(grid), dim3(CA::NT), args,
+                                                      sizeof(FusedSmem<CA, CB>), s));
+    return cudaSuccess;
+}
+
+cudaError_t launch_fused(const FusedArgs &f, int conn, int grid, cudaStream_t s)
+{
+    static_assert(NarrowCfg::NT == MainCfg::NT, "the two binary shapes share one persistent kernel");
+    switch (conn & ~(CONN_NARROW | CONN_WIDE)) {
+    case 4: return launch_fused_t<MainCfg4, MainCfg4>(f, grid, s);
+    case 8 | CONN_CLASSES: return launch_fused_t<MainCfgC8, MainCfgC8>(f, grid, s);
+    case 4 | CONN_CLASSES: return launch_fused_t<MainCfgC4, MainCfgC4>(f, grid, s);
+    default: return launch_fused_t<NarrowCfg, MainCfg>(f, grid, s);
     }
 }
 

@@ -172,6 +172,7 @@ bool try_launch_locked(ccl_server *s, Lane &L)
     L.keep.clear();
     L.ids.clear();
     const int conn = s->cfg.connectivity;
+    const bool fused = launch_mode() == 0;  // one persistent launch per batch
     const int64_t room = largest_free_locked(s);
     int64_t px = 0, sum_n = 0, sum_w = 0;
     while (!s->pending.empty() && (int32_t)L.ids.size() < s->cfg.max_batch) {
@@ -179,7 +180,10 @@ bool try_launch_locked(ccl_server *s, Lane &L)
         Request &r = s->reqs[id];
         const int32_t m = (int32_t)L.ids.size() + 1;
         int64_t need, add_n = 0, add_w = 0;
-        if (conn == 8) {
+        if (fused) {
+            add_n = add_w = fused_image_bytes(r.img.H, r.img.W, conn);
+            need = fused_fixed_bytes(m) + sum_n + add_n;
+        } else if (conn == 8) {
             add_n = main_layout(r.img.H, r.img.W, 8 | CONN_NARROW).bytes;
             add_w = main_layout(r.img.H, r.img.W, 8 | CONN_WIDE).bytes;
             const bool narrow = resolve_conn(8, px + r.pixels, 1) == (8 | CONN_NARROW);
@@ -207,7 +211,7 @@ bool try_launch_locked(ccl_server *s, Lane &L)
     const int32_t m = (int32_t)L.ids.size();
     if (m == 0)
         return false;
-    L.bytes = batch_bytes(L.imgs.data(), L.keep.data(), m, conn);
+    L.bytes = launch_bytes(L.imgs.data(), L.keep.data(), m, conn);
     L.offset = reserve_locked(s, L.bytes);
     int32_t rc = CCL_OK;
     if (L.offset < 0) {
@@ -219,7 +223,7 @@ bool try_launch_locked(ccl_server *s, Lane &L)
         cudaError_t e = cudaMemsetAsync(static_cast<char *>(L.ws.dev) + 4, 0, 4, L.stream);
         rc = map_cuda(e);
         if (rc == CCL_OK)
-            rc = enqueue_batch(L.imgs.data(), L.keep.data(), m, conn, 0, L.k_dev, &L.ws, L.stream);
+            rc = enqueue_launch(L.imgs.data(), L.keep.data(), m, conn, 0, L.k_dev, &L.ws, L.stream);
         if (rc == CCL_OK) {
             // K values and the status word back to the host
             e = cudaMemcpyAsync(L.k_host, L.k_dev, (size_t)m * 4, cudaMemcpyDeviceToHost, L.stream);
@@ -341,8 +345,8 @@ int32_t ccl_server_create(const ccl_server_config *cfg, ccl_server **out)
         // the descriptor staging buffer and its event exist before the scheduler runs, so a
         // launch never allocates (an allocation could wait for the device while a lane's
         // completion callback waits for the scheduler's lock)
-        const int64_t stage = ((int64_t)cfg->max_batch * (int64_t)sizeof(Img) + 255) / 256 * 256 +
-                              (3 * (int64_t)(cfg->max_batch + 1) * 8 + 255) / 256 * 256;
+        const int64_t stage = 2 * (((int64_t)cfg->max_batch * (int64_t)sizeof(Img) + 255) / 256 * 256 +
+                                   (3 * (int64_t)(cfg->max_batch + 1) * 8 + 255) / 256 * 256);
         if (e == cudaSuccess)
             e = cudaMallocHost(&L->ws.stage, (size_t)stage);
         if (e == cudaSuccess)

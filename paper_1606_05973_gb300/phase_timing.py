@@ -34,7 +34,8 @@ def build_timed() -> str:
 
     b = importlib.import_module("paper_1606_05973_gb300.build")
     os.makedirs(b.OUT, exist_ok=True)
-    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", *b.ARCH,
+    b.write_tuning_include()
+    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", b.OUT, *b.ARCH,
              "-DCCL_PHASE_TIMING"]
     objs = []
     for src in b.SOURCES:

@@ -38,8 +38,9 @@ def build_shape(th: int, tw: int) -> str:
     if (th, tw) == DEFAULT:
         return b.build()
     os.makedirs(b.OUT, exist_ok=True)
+    b.write_tuning_include()
     tag = f"tile_{th}x{tw}"
-    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", *b.ARCH,
+    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", b.OUT, *b.ARCH,
              f"-DCCL_TILE_H={th}", f"-DCCL_TILE_W={tw}"]
 
     def one(src):

@@ -320,6 +320,7 @@ template <class C> struct Emu {
             segStart[i + 1] = segStart[i] + L[i].nSeg;
         }
         Batch B;
+        memset(&B, 0, sizeof(B));
         B.n = n;
         B.imgs = descs.data();
         B.tileStart = tileStart.data();
@@ -399,9 +400,144 @@ template <class C> struct Emu {
     }
 };
 
+// Persistent single-launch path (fused_body): CA and CB are the two tile shapes compiled
+// into the kernel; G CTAs of NT threads all run at once.  pick/lo/hi/probe as FusedArgs.
+// n == 1 uses the inline single-image descriptor (no descriptor arrays).
+template <class CA, class CB> struct EmuFused {
+    std::mt19937_64 rng;
+    explicit EmuFused(uint64_t s) : rng(s) {}
+
+    template <class C> static void bind(Img &a, const Layout &L, char *b)
+    {
+        a.nTX = L.nTX;
+        a.nTY = L.nTY;
+        a.bitpack = (uint32_t *)(b + L.off_bitpack);
+        a.cstart = (uint32_t *)(b + L.off_cstart);
+        a.runinfo = (uint16_t *)(b + L.off_runinfo);
+        a.nRunInfo = L.nRunInfo;
+        a.P = (int *)(b + L.off_P);
+        a.nseg = (int *)(b + L.off_nseg);
+        a.cnt = (int *)(b + L.off_cnt);
+        a.edgeRow = (int *)(b + L.off_edgeRow);
+        a.edgeCol = (int *)(b + L.off_edgeCol);
+        a.bsum = (int *)(b + L.off_bsum);
+        a.nP = L.nP;
+        a.nSeg = L.nSeg;
+    }
+
+    void run(int n, const uint8_t *const *imgs, const int32_t *Hs, const int32_t *Ws, const int64_t *pitches,
+             int32_t *const *labels, int32_t *Ks, const int32_t *pick, int32_t lo, int32_t hi, int32_t probe,
+             int32_t G, int32_t *status)
+    {
+        std::vector<std::vector<unsigned char>> ws(n);
+        std::vector<Img> descs[2];
+        std::vector<int64_t> pre[2][3];
+        for (int k = 0; k < 2; k++) {
+            descs[k].resize(n);
+            for (int j = 0; j < 3; j++)
+                pre[k][j].assign(n + 1, 0);
+        }
+        std::vector<int> imgBase(n + 1, 0x7B7B7B7B), bsum(MAX_GLOBAL_CTAS, 0x7B7B7B7B);
+        std::vector<unsigned char> hdr(256, 0x7B);
+        memset(hdr.data() + 16, 0, sizeof(GridSync));  // the host clears the grid state
+        for (int i = 0; i < n; i++) {
+            const Layout LA = plan_layout<CA>(Hs[i], Ws[i]), LB = plan_layout<CB>(Hs[i], Ws[i]);
+            ws[i].assign((size_t)std::max(LA.bytes, LB.bytes) + 64, 0x7B);
+            for (int k = 0; k < 2; k++) {
+                Img &a = descs[k][i];
+                memset(&a, 0, sizeof(a));
+                a.img = imgs[i];
+                a.pitch = pitches[i];
+                a.H = Hs[i];
+                a.W = Ws[i];
+                a.thr = g_emu_thr;
+                a.vec_in = ((uintptr_t)imgs[i] % 16 == 0) && (pitches[i] % 16 == 0);
+                a.labels = labels[i];
+                a.vec_out = ((uintptr_t)labels[i] % 16 == 0) && (Ws[i] % 4 == 0);
+                a.K = Ks + i;
+                a.status = status;
+                const Layout &L = k ? LB : LA;
+                if (k)
+                    bind<CB>(a, L, (char *)ws[i].data());
+                else
+                    bind<CA>(a, L, (char *)ws[i].data());
+                pre[k][0][i + 1] = pre[k][0][i] + (int64_t)L.nTX * L.nTY;
+                pre[k][1][i + 1] = pre[k][1][i] + (int64_t)(L.nTY - 1) * Ws[i] + (int64_t)(L.nTX - 1) * Hs[i];
+                pre[k][2][i + 1] = pre[k][2][i] + L.nSeg;
+            }
+        }
+        FusedArgs f;
+        memset(&f, 0, sizeof(f));
+        for (int k = 0; k < 2; k++) {
+            Batch &B = f.set[k];
+            B.n = n;
+            B.imgs = descs[k].data();
+            B.tileStart = pre[k][0].data();
+            B.itemStart = pre[k][1].data();
+            B.segStart = pre[k][2].data();
+            B.imgBase = imgBase.data();
+            B.gsync = (GridSync *)(hdr.data() + 16);
+            B.bsum = bsum.data();
+            B.status = status;
+            if (n == 1) {
+                B.inl = 1;
+                B.one = descs[k][0];
+                B.one_tiles = pre[k][0][1];
+                B.one_items = pre[k][1][1];
+                B.one_segs = pre[k][2][1];
+                B.imgs = nullptr;
+                B.tileStart = B.itemStart = B.segStart = nullptr;
+            }
+        }
+        for (int c = 0; c < 3; c++)
+            f.pick[c] = pick[c];
+        f.dens_lo = lo;
+        f.dens_hi = hi;
+        f.probe_samples = probe;
+        std::vector<std::unique_ptr<FusedSmem<CA, CB>>> sm(G);
+        for (auto &p : sm) {
+            p.reset(new FusedSmem<CA, CB>);
+            memset(p.get(), 0x7F, sizeof(FusedSmem<CA, CB>));
+        }
+        Sched sch(G, CA::NT, rng(), [&](int b, int t) { fused_body<CA, CB>(f, *sm[b], b, G, t); });
+        g_sched = &sch;
+        sch.run();
+        g_sched = nullptr;
+    }
+};
+
 }  // namespace
 
 extern "C" {
+
+// the persistent single-launch path on n images (H, W > 0).  pair 0: 8x64 and 4x64 tiles of
+// 64 threads (8-connectivity), pair 1: 8x64 alone, pair 2: 4x32 alone under 4-connectivity,
+// pair 3: 4x32 alone, multi-class under 8-connectivity.
+void emu_label_fused(int32_t n, const uint8_t *const *imgs, const int32_t *H, const int32_t *W, const int64_t *pitch,
+                     int32_t *const *labels, int32_t *K, uint64_t seed, int32_t pair, const int32_t *pick,
+                     int32_t lo, int32_t hi, int32_t probe, int32_t G, int32_t *status)
+{
+    *status = 0;
+    switch (pair) {
+    case 0:
+        EmuFused<Cfg<8, 64, 64>, Cfg<4, 64, 64>>(seed).run(n, imgs, H, W, pitch, labels, K, pick, lo, hi, probe, G,
+                                                          status);
+        break;
+    case 1:
+        EmuFused<Cfg<8, 64, 64>, Cfg<8, 64, 64>>(seed).run(n, imgs, H, W, pitch, labels, K, pick, lo, hi, probe, G,
+                                                          status);
+        break;
+    case 2:
+        EmuFused<Cfg<4, 32, 32, 4>, Cfg<4, 32, 32, 4>>(seed).run(n, imgs, H, W, pitch, labels, K, pick, lo, hi,
+                                                                probe, G, status);
+        break;
+    default:
+        EmuFused<Cfg<4, 32, 32, 8, true>, Cfg<4, 32, 32, 8, true>>(seed).run(n, imgs, H, W, pitch, labels, K, pick,
+                                                                            lo, hi, probe, G, status);
+        break;
+    }
+}
+
 
 // threshold of the object test (object = byte > thr) for the following emu_label calls
 void emu_set_threshold(int32_t thr) { g_emu_thr = thr; }

@@ -51,6 +51,11 @@ class Emu:
         fb.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p]
         fb.restype = None
+        ff = self.lib.emu_label_fused
+        ff.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p,
+                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
+        ff.restype = None
         self.lib.emu_set_threshold.argtypes = [ctypes.c_int32]
         self.lib.emu_gt_mask16.argtypes = [ctypes.c_void_p, ctypes.c_int32]
         self.lib.emu_gt_mask16.restype = ctypes.c_uint32
@@ -95,4 +100,25 @@ class Emu:
         st = np.zeros(1, np.int32)
         self.lib.emu_label_batch(n, ip, H.ctypes.data, W.ctypes.data, pitch.ctypes.data, lp, K.ctypes.data,
                                  seed, shape, st.ctypes.data)
+        return labs, [int(k) for k in K], int(st[0])
+
+    def label_fused(self, imgs, seed: int = 1, pair: int = 0, pick=(0, 0, 0), lo: int = 0, hi: int = 0,
+                    probe: int = 0, ctas: int = 3, threshold: int = 0):
+        """Persistent single-launch path (fused_body) on a list of non-empty images; returns
+        (labels list, K list, status)."""
+        self.lib.emu_set_threshold(int(threshold))
+        n = len(imgs)
+        srcs = [np.ascontiguousarray(im) for im in imgs]
+        labs = [np.full(im.shape, -7, np.int32) for im in srcs]
+        P = ctypes.c_void_p * n
+        ip = P(*[im.ctypes.data for im in srcs])
+        lp = P(*[lb.ctypes.data for lb in labs])
+        H = np.array([im.shape[0] for im in srcs], np.int32)
+        W = np.array([im.shape[1] for im in srcs], np.int32)
+        pitch = np.array([im.shape[1] for im in srcs], np.int64)
+        K = np.full(n, -1, np.int32)
+        st = np.zeros(1, np.int32)
+        pk = np.array(pick, np.int32)
+        self.lib.emu_label_fused(n, ip, H.ctypes.data, W.ctypes.data, pitch.ctypes.data, lp, K.ctypes.data,
+                                 seed, pair, pk.ctypes.data, lo, hi, probe, ctas, st.ctypes.data)
         return labs, [int(k) for k in K], int(st[0])

@@ -155,3 +155,46 @@ def test_byte_equality_test_of_the_class_load():
                 got = e.lib.emu_eq_nibble(wa, wb)
                 exp = sum(1 << i for i in range(4) if (wa >> (8 * i)) & 255 == (wb >> (8 * i)) & 255)
                 assert got == exp, (pos, hex(wa), hex(wb), got, exp)
+
+
+def test_emulated_persistent_path():
+    """The persistent single-launch body (tile pass, global phases and final pass in one
+    grid, tiles from counters, the density probe choosing between two tile shapes) against
+    the oracle: single images (inline descriptor) and batches, both shapes, the probe's
+    three classes, 4-connectivity and multi-class, two to five CTAs."""
+    sys.path.insert(0, HERE)
+    import numpy as np
+
+    import oracle
+    import synth
+    from emu import emu
+
+    e = emu.Emu(emu.build(sanitize=False))
+    rng = np.random.Generator(np.random.PCG64(11))
+    for trial in range(24):
+        n = int(rng.integers(1, 5))
+        imgs = []
+        for i in range(n):
+            h, w = int(rng.integers(1, 70)), int(rng.integers(1, 150))
+            kind = int(rng.integers(0, 3))
+            if kind == 0:
+                imgs.append(synth.bernoulli(h, w, float(rng.uniform(0.05, 0.95)), trial * 10 + i))
+            elif kind == 1:
+                imgs.append(synth.serpentine(h, w))
+            else:
+                imgs.append(np.ones((h, w), np.uint8))
+        pick = tuple(int(x) for x in rng.integers(0, 2, 3))
+        probe = int(rng.choice([0, 4, 16]))
+        ctas = int(rng.integers(2, 6))
+        pair = int(rng.choice([0, 0, 1, 2, 3]))
+        if pair == 3:
+            imgs = [(im * rng.integers(1, 4, im.shape)).astype(np.uint8) for im in imgs]
+        labs, ks, st = e.label_fused(imgs, seed=trial, pair=pair, pick=pick, lo=300, hi=700, probe=probe,
+                                     ctas=ctas)
+        assert st == 0, (trial, st)
+        for im, lab, k in zip(imgs, labs, ks):
+            if pair == 3:
+                ref, rk = oracle.classes(im, 8)
+            else:
+                ref, rk = oracle.cclremsp(im, 4 if pair == 2 else 8)
+            assert k == rk and np.array_equal(lab, ref), (trial, pair, im.shape)
