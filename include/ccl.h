@@ -319,6 +319,14 @@ int32_t ccl_set_global_ctas_per_sm(int32_t n);
 int32_t ccl_set_launch_mode(int32_t mode);
 
 /*
+ * ccl_set_persistent_ctas_per_sm - CTAs per SM of the persistent launch's grid (256 threads
+ * each), in place of the tuning table's value; 0 (the default) takes the table's.  Values
+ * above what fits are clamped.  A tuning knob (the sweep that writes the table uses it).
+ * Process-wide; CCL_ERR_INVALID_ARGUMENT for n < 0.
+ */
+int32_t ccl_set_persistent_ctas_per_sm(int32_t n);
+
+/*
  * ccl_set_tile_policy - the tile shape of the 8-connected path (the partitions that
  * Algorithm 7 labels independently before its boundary merge).  policy 0 (the default)
  * chooses by size: images of at most 3072 x 3072 pixels take 64 x 128 tiles, larger ones

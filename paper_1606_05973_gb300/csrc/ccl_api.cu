@@ -328,7 +328,8 @@ int32_t enqueue_fused(const ccl_image *imgs, const int32_t *keep, int32_t m, int
     if (resident < 1)
         return CCL_ERR_CUDA;
     int64_t grid = std::min<int64_t>(need_ctas, resident);
-    grid = std::min<int64_t>(grid, (int64_t)row.ctas_per_sm * sm_count());
+    const int per_sm = fused_ctas_per_sm_override() > 0 ? fused_ctas_per_sm_override() : row.ctas_per_sm;
+    grid = std::min<int64_t>(grid, (int64_t)per_sm * sm_count());
     return map_cuda(launch_fused(f, conn, (int)std::max<int64_t>(grid, 1), s));
 }
 
@@ -891,6 +892,14 @@ int32_t ccl_set_launch_mode(int32_t mode)
     if (mode < 0 || mode > 1)
         return CCL_ERR_INVALID_ARGUMENT;
     set_launch_mode(mode);
+    return CCL_OK;
+}
+
+int32_t ccl_set_persistent_ctas_per_sm(int32_t n)
+{
+    if (n < 0)
+        return CCL_ERR_INVALID_ARGUMENT;
+    set_fused_ctas_per_sm(n);
     return CCL_OK;
 }
 

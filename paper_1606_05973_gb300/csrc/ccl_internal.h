@@ -100,6 +100,9 @@ int fused_threads();
 cudaError_t launch_fused(const FusedArgs &f, int conn, int grid, cudaStream_t s);
 // SMs of the current device
 int sm_count();
+// CTAs per SM of the persistent launch, overriding the tuning table (0: the table's)
+void set_fused_ctas_per_sm(int n);
+int fused_ctas_per_sm_override();
 // process-wide launch mode: 0 = automatic (persistent launch for batches and for single
 // images up to the tuned size), 1 = always the three kernels
 void set_launch_mode(int m);

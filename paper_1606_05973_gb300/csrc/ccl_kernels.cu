@@ -350,6 +350,9 @@ static std::atomic<int> g_launch_mode{0};
 void set_launch_mode(int m) { g_launch_mode.store(m); }
 int launch_mode() { return g_launch_mode.load(); }
 int sm_count() { return g_num_sms[current_device()]; }
+static std::atomic<int> g_fused_per_sm{0};
+void set_fused_ctas_per_sm(int n) { g_fused_per_sm.store(n); }
+int fused_ctas_per_sm_override() { return g_fused_per_sm.load(); }
 
 int fused_threads() { return MainCfg::NT; }
 

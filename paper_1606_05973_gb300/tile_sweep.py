@@ -1,6 +1,14 @@
-"""Offline tile-shape sweep (a tuning tool; the library compiles two shapes, picked by size).
+"""Offline tile-shape sweep and the autotuner of the persistent launch.
 
     python -m paper_1606_05973_gb300.tile_sweep [--out PATH]
+    python -m paper_1606_05973_gb300.tile_sweep --write-table [--table-out PATH] [--summary-out PATH]
+
+--write-table measures the persistent single launch over size classes x density classes x
+the two compiled tile shapes x grids of 4, 6 and 8 CTAs per SM, and single images under
+the persistent launch against the three kernels, and writes the library's tuning table
+(tuning.json, compiled into libccl by build.py) from the fastest entries.
+
+Without it:
 
 Builds the library once per tile shape TH x TW of the 8-connected path (compile-time
 CCL_TILE_H / CCL_TILE_W; 256 threads per CTA) into ``_build/libccl_tile_<TH>x<TW>.so``,
@@ -69,6 +77,118 @@ def images(dev):
     return out
 
 
+# ---- autotuner of the persistent launch (--write-table) ------------------------------------
+# Size classes (a batch's total pixels) and their representative batches: (count, side).
+SIZE_CLASSES = [(1 << 20, (1, 1024)), (1 << 22, (1, 2048)), (1 << 24, (1, 4096)), (1 << 26, (64, 1024)),
+                (None, (16, 4096))]
+DENSITIES = (0.1, 0.5, 0.9)  # one Bernoulli density inside each class of density_bounds (0.3, 0.7)
+CTAS = (4, 6, 8)
+SINGLE_SIDES = (256, 512, 1024, 1536, 2048, 3072, 4096, 8192)
+
+
+def _time(fn, sync, reps=10, warm=2):
+    import torch
+
+    for _ in range(warm):
+        fn()
+    sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream()
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def write_table(out_json, out_txt):
+    """Measures the persistent launch for every size class x density class x tile shape x
+    grid (CTAs per SM), and single images under the persistent launch against the three
+    kernels; writes tuning.json (the fastest shape per class, the grid with the smallest
+    sum over the densities, and the largest single-image size at which the persistent
+    launch wins on every content) and a text summary of the measurements."""
+    import torch
+
+    import paper_1606_05973_gb300 as ccl
+    import synth
+
+    lib = ccl.lib()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    sync = torch.cuda.synchronize
+    rows, lines = [], []
+    for bound, (count, side) in SIZE_CLASSES:
+        per = {}  # (density, shape, ctas) -> ms
+        for di, p in enumerate(DENSITIES):
+            imgs = [torch.from_numpy(synth.bernoulli(side, side, p, 300 + 7 * di + i)).to(dev) for i in range(count)]
+            outs = [torch.empty((side, side), dtype=torch.int32, device=dev) for _ in imgs]
+            kd = torch.zeros(count, dtype=torch.int32, device=dev)
+            ref = None
+            for shape, policy in (("64x128", 2), ("64x256", 1)):
+                lib.ccl_set_tile_policy(policy)
+                for c in CTAS:
+                    lib.ccl_set_persistent_ctas_per_sm(c)
+                    ms = _time(lambda: ccl.label_batch(imgs, outs=outs, k_out=kd), sync)
+                    k = kd.cpu().tolist()
+                    if ref is None:
+                        ref = k
+                    elif k != ref:
+                        raise RuntimeError(f"K differs across shapes: {side} p={p} {shape} {c}")
+                    per[(di, shape, c)] = ms
+            del imgs, outs
+            torch.cuda.empty_cache()
+        lib.ccl_set_tile_policy(0)
+        lib.ccl_set_persistent_ctas_per_sm(0)
+        best_shape = []
+        for di in range(3):
+            best_shape.append(min(("64x128", "64x256"), key=lambda sh: min(per[(di, sh, c)] for c in CTAS)))
+        best_c = min(CTAS, key=lambda c: sum(per[(di, best_shape[di], c)] for di in range(3)))
+        rows.append({"max_px": bound, "shape": best_shape, "ctas_per_sm": best_c})
+        lines.append(f"class <= {bound if bound else 'inf'} px ({count} x {side}^2):")
+        for di, p in enumerate(DENSITIES):
+            cells = "  ".join(f"{sh}/{c}: {per[(di, sh, c)]:.4f}" for sh in ("64x128", "64x256") for c in CTAS)
+            lines.append(f"  p={p}  {cells}  -> {best_shape[di]}")
+        lines.append(f"  grid: {best_c} CTAs per SM")
+    # single images: persistent launch (a batch of one) against the three kernels
+    single_max = 0
+    lines.append("single images, ms per call: persistent / three kernels")
+    for side in SINGLE_SIDES:
+        wins = True
+        for name, img in ((f"bernoulli p=0.5", torch.from_numpy(synth.bernoulli(side, side, 0.5, side)).to(dev)),
+                          (f"blobs sigma=4", synth.blobs_device(side, side, 4.0, side + 1, dev)),
+                          (f"bernoulli p=0.1", torch.from_numpy(synth.bernoulli(side, side, 0.1, side + 2)).to(dev))):
+            out = torch.empty((side, side), dtype=torch.int32, device=dev)
+            kd = torch.zeros(1, dtype=torch.int32, device=dev)
+            sp = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+            pers = _time(lambda: ccl.label_batch([img], outs=[out], k_out=kd), sync)
+            k1 = int(kd.item())
+            lib.ccl_set_launch_mode(1)
+            three = _time(lambda: lib.ccl_label_async(img.data_ptr(), side, side, img.stride(0), 8, out.data_ptr(),
+                                                      ctypes.c_void_p(kd.data_ptr()), sp), sync)
+            lib.ccl_set_launch_mode(0)
+            if int(kd.item()) != k1:
+                raise RuntimeError(f"K differs between the launch modes at {side}^2 {name}")
+            wins &= pers < three
+            lines.append(f"  {side}^2 {name}: {pers:.4f} / {three:.4f}")
+        if wins:
+            single_max = side * side
+    t = {"about": json.load(open(TUNING_PATH))["about"],
+         "written_by": "python -m paper_1606_05973_gb300.tile_sweep --write-table (GB300 measurements)",
+         "density_bounds": [0.3, 0.7], "probe_samples": 64, "single_fused_max_px": single_max, "rows": rows}
+    txt = json.dumps(t, indent=2)
+    with open(out_json, "w") as f:
+        f.write(txt + "\n")
+    lines.append(f"single images take the persistent launch up to {single_max} px")
+    with open(out_txt, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    print("\n".join(lines))
+    print(txt)
+
+
+TUNING_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
+
+
 def main():
     import torch
 
@@ -76,7 +196,14 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=None, help="also write the JSON object to this file")
+    ap.add_argument("--write-table", action="store_true",
+                    help="tune the persistent launch and write tuning.json (see write_table)")
+    ap.add_argument("--table-out", default=TUNING_PATH)
+    ap.add_argument("--summary-out", default=None)
     args = ap.parse_args()
+    if args.write_table:
+        write_table(args.table_out, args.summary_out or os.path.join(ROOT, "gpurun_out", "tuning_sweep.txt"))
+        return
     with cf.ThreadPoolExecutor(len(SHAPES)) as ex:
         libs = dict(zip(SHAPES, ex.map(lambda s: build_shape(*s), SHAPES)))
     dev = torch.device("cuda:0")
