@@ -621,8 +621,8 @@ def measure_plain(args, name, dev, lib):
         gms = g0.elapsed_time(g1) / reps
         res["graph_replay"] = {"us_per_image": round(gms * 1e3, 2), "value": round(px / (gms * 1e-3) / 1e9, 2),
                                "how": f"one ccl_label_async call captured in a CUDA graph, {reps} replays"}
-        # the same with the three-kernel path forced (ccl_set_launch_mode(1)), for comparison
-        lib.ccl_set_launch_mode(1)
+        # the same with the persistent launch forced (ccl_set_launch_mode(2)), for comparison
+        lib.ccl_set_launch_mode(2)
         g3 = torch.cuda.CUDAGraph()
         with torch.cuda.stream(main):
             step(1)
@@ -640,10 +640,10 @@ def measure_plain(args, name, dev, lib):
         lib.ccl_set_launch_mode(0)
         status()
         if int(kdev[0]) != ref_k:
-            raise RuntimeError("three-kernel graph replay changed K")
+            raise RuntimeError("persistent graph replay changed K")
         tms = h0.elapsed_time(h1) / reps
-        res["graph_replay_three_launches"] = {"us_per_image": round(tms * 1e3, 2),
-                                              "value": round(px / (tms * 1e-3) / 1e9, 2)}
+        res["graph_replay_persistent"] = {"us_per_image": round(tms * 1e3, 2),
+                                          "value": round(px / (tms * 1e-3) / 1e9, 2)}
     lib.ccl_set_global_ctas_per_sm(args.global_ctas_per_sm or 0)
     return res
 
@@ -867,7 +867,7 @@ def measure_batched(args, dev, lib, stream):
         ref_k = kd_single.clone()
         status()
         out = {}
-        for mode, tag in ((0, "persistent"), (1, "three_launches")):
+        for mode, tag in ((0, "tuned"), (2, "persistent"), (1, "three_launches")):
             lib.ccl_set_launch_mode(mode)
             kd_batch.fill_(-1)
             ms_b = timed(batched, reps)
@@ -882,7 +882,7 @@ def measure_batched(args, dev, lib, stream):
         sub_px = sum(t.numel() for t in sub)
         k64 = torch.zeros(64, dtype=torch.int32, device=dev)
         small = {}
-        for mode, tag in ((0, "persistent"), (1, "three_launches")):
+        for mode, tag in ((0, "tuned"), (2, "persistent"), (1, "three_launches")):
             lib.ccl_set_launch_mode(mode)
 
             def b64():
@@ -899,12 +899,13 @@ def measure_batched(args, dev, lib, stream):
         lib.ccl_set_launch_mode(0)
         status()
     res.update({"per_image_ms": round(ms_single, 3), "gpx_s_per_image": round(px / ms_single / 1e6, 2),
-                "batched_ms": out["persistent"]["ms"], "batched_graph_ms": out["persistent"]["graph_ms"],
-                "gpx_s_batched": out["persistent"]["gpx_s"], "gpx_s_batched_graph": out["persistent"]["gpx_s_graph"],
-                "speedup_batched_graph_vs_per_image": round(ms_single / out["persistent"]["graph_ms"], 2),
+                "batched_ms": out["tuned"]["ms"], "batched_graph_ms": out["tuned"]["graph_ms"],
+                "gpx_s_batched": out["tuned"]["gpx_s"], "gpx_s_batched_graph": out["tuned"]["gpx_s_graph"],
+                "speedup_batched_graph_vs_per_image": round(ms_single / out["tuned"]["graph_ms"], 2),
                 "modes": out, "batch64": {"pixels": int(sub_px), **small},
-                "how": "per-image: one ccl_label_async call per image; persistent: one ccl_label_batch call "
-                       "(one cooperative launch); three_launches: the same call with ccl_set_launch_mode(1)"})
+                "how": "per-image: one ccl_label_async call per image; tuned: one ccl_label_batch call in the "
+                       "launch form the tuning table gives its size class; persistent / three_launches: the same "
+                       "call forced to one cooperative launch (ccl_set_launch_mode(2)) or three launches (1)"})
     return res
 
 

@@ -153,20 +153,20 @@ typedef struct {
 } ccl_image;
 
 /*
- * ccl_label_batch - label n images (uneven sizes allowed) on one stream, in ONE persistent
- * cooperative kernel launch: the tile pass (Algorithms 6 and 2 per tile), the boundary
- * merge (Algorithms 7-8), flatten (Algorithm 3) and the labelling pass run back to back in
- * one grid, separated by grid barriers, with tiles handed out from a counter.  The tile
- * shape comes from the library's tuning table (written by an offline sweep,
- * paper_1606_05973_gb300/tuning.json): a row per size class (the batch's pixel count)
- * gives a shape per density class, and when they differ a probe at the start of the
- * launch (the object fraction of 64 samples of 16 bytes per image) picks the class.
+ * ccl_label_batch - label n images (uneven sizes allowed) on one stream.  The library's
+ * tuning table (written by an offline sweep, paper_1606_05973_gb300/tuning.json) has a row
+ * per size class (the batch's pixel count) that says whether the batch takes ONE persistent
+ * cooperative kernel launch (the tile pass of Algorithms 6 and 2, the boundary merge of
+ * Algorithms 7-8, flatten (Algorithm 3) and the labelling pass back to back in one grid,
+ * separated by grid barriers, tiles handed out from a counter) or three kernel launches,
+ * and, for the persistent launch, a tile shape per density class: when the shapes differ,
+ * a probe at the start of the launch (the object fraction of 64 samples of 16 bytes per
+ * image) picks the class.
  *   imgs               HOST array of n descriptors (device pointers inside)
  *   num_components_dev DEVICE int32[n] or NULL; entry i receives K of image i
  * Asynchronous and capturable in a CUDA graph once the stream's workspace is large enough
  * (make one uncaptured call of the same or a larger batch first); results are identical
- * to labelling each image alone.  ccl_set_launch_mode(1) selects the earlier form (three
- * kernel launches per batch) instead.
+ * to labelling each image alone.  ccl_set_launch_mode forces either form.
  */
 int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity,
                         int32_t *num_components_dev, ccl_stream_t stream);
@@ -309,12 +309,14 @@ int32_t ccl_shutdown(void);
 int32_t ccl_set_global_ctas_per_sm(int32_t n);
 
 /*
- * ccl_set_launch_mode - how the path is launched.  0 (the default): a batch is one
- * persistent launch (see ccl_label_batch), and so is a single image of at most the tuning
- * table's single-image size (small images are bound by launch and barrier latency); larger
- * single images take three kernels (tile pass, cooperative global pass, final pass).
- * 1: always three kernels.  Labels are identical in both modes.  Process-wide; applies to
- * calls made after it.  CCL_ERR_INVALID_ARGUMENT for other values.
+ * ccl_set_launch_mode - how the path is launched.  0 (the default): the tuning table
+ * decides: a batch takes the persistent single launch (see ccl_label_batch) in the size
+ * classes where the sweep measured it faster, else three kernels (tile pass, cooperative
+ * global pass, final pass); a single image takes the persistent launch up to the table's
+ * single-image size (on GB300 the sweep found three kernels faster at every size).
+ * 1: always three kernels.  2: always the persistent launch.  Labels are identical in every
+ * mode.  Process-wide; applies to calls made after it.  CCL_ERR_INVALID_ARGUMENT for other
+ * values.
  */
 int32_t ccl_set_launch_mode(int32_t mode);
 

@@ -57,7 +57,8 @@ def tuning_source(path: str = TUNING) -> str:
         shape = [SHAPES[x] for x in r["shape"]]
         assert len(shape) == 3 and int(r["ctas_per_sm"]) >= 1
         mx = -1 if r["max_px"] is None else int(r["max_px"])
-        rows.append(f"    {{{mx}LL, {{{shape[0]}, {shape[1]}, {shape[2]}}}, {int(r['ctas_per_sm'])}}},")
+        pers = 1 if r.get("persistent", True) else 0
+        rows.append(f"    {{{mx}LL, {{{shape[0]}, {shape[1]}, {shape[2]}}}, {int(r['ctas_per_sm'])}, {pers}}},")
     assert rows and t["rows"][-1]["max_px"] is None, "the last row must have no bound"
     return "\n".join([
         "// written by paper_1606_05973_gb300/build.py from tuning.json; do not edit",

@@ -339,7 +339,7 @@ int32_t enqueue_fused(const ccl_image *imgs, const int32_t *keep, int32_t m, int
 SinglePlan plan_single(int32_t H, int32_t W, int conn)
 {
     SinglePlan p;
-    p.fused = launch_mode() == 0 && (int64_t)H * W <= tuning().single_fused_max_px;
+    p.fused = launch_mode() == 2 || (launch_mode() == 0 && (int64_t)H * W <= tuning().single_fused_max_px);
     if (p.fused) {
         p.conn = conn;
         p.bytes = fused_fixed_bytes(1) + fused_image_bytes(H, W, conn);
@@ -757,15 +757,25 @@ int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int
     return map_cuda(launch_batch(B, tileStart[m], itemStart[m], segStart[m], conn, s));
 }
 
+bool batch_persistent(const ccl_image *imgs, const int32_t *keep, int32_t m)
+{
+    if (launch_mode() != 0)
+        return launch_mode() == 2;
+    int64_t px = 0;
+    for (int32_t k = 0; k < m; k++)
+        px += (int64_t)imgs[keep[k]].H * imgs[keep[k]].W;
+    return tune_row(px).persistent != 0;
+}
+
 int64_t launch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn)
 {
-    return launch_mode() == 0 ? fused_bytes(imgs, keep, m, conn) : batch_bytes(imgs, keep, m, conn);
+    return batch_persistent(imgs, keep, m) ? fused_bytes(imgs, keep, m, conn) : batch_bytes(imgs, keep, m, conn);
 }
 
 int32_t enqueue_launch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
                        Workspace *w, cudaStream_t s)
 {
-    if (launch_mode() == 0)
+    if (batch_persistent(imgs, keep, m))
         return enqueue_fused(imgs, keep, m, conn, thr, k_dev, w, s);
     return enqueue_batch(imgs, keep, m, conn, thr, k_dev, w, s);
 }
@@ -889,7 +899,7 @@ int32_t ccl_set_tile_policy(int32_t policy)
 
 int32_t ccl_set_launch_mode(int32_t mode)
 {
-    if (mode < 0 || mode > 1)
+    if (mode < 0 || mode > 2)
         return CCL_ERR_INVALID_ARGUMENT;
     set_launch_mode(mode);
     return CCL_OK;

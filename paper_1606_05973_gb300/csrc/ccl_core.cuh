@@ -31,6 +31,7 @@
 //    each root its rank + 1, and write every pixel's label.  The first kernel stores one
 //    16-bit root code per strip run, so the final kernel only maps runs to labels.
 #pragma once
+#include <stddef.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -107,6 +108,14 @@ CCL_HD int cta_count(bool p, int *slot, int tid)
 #endif
 }
 // all 32 lanes of the warp must call these together
+CCL_HD void warp_sync()
+{
+#if defined(__CUDA_ARCH__)
+    __syncwarp();
+#else
+    (void)emu_ballot(true);
+#endif
+}
 CCL_HD uint32_t warp_ballot(bool p)
 {
 #if defined(__CUDA_ARCH__)
@@ -466,11 +475,12 @@ template <class C> struct SmemCls<C, true> {
 };
 template <class C> struct SmemL : SmemRuns<C>, SmemCls<C> {
     uint32_t par[C::RMAX];           // union-find parents (see above)
-    int ucount[33];                  // union phase: units per event count, then bucket starts
     int red;                         // cta_count's slot (host emulation only)
-    uint16_t uorder[C::NT];          // union phase: units of a chunk by event count
-    uint32_t rootbits[C::TH][C::NW]; // first pixels of the local components
-    int rootpre[C::TH][C::NW];       // exclusive popcount prefix of rootbits along a row
+    uint32_t rootbits[C::TH][C::NW]; // first pixels of the local components (union phase: join lists)
+    int rootpre[C::TH][C::NW];       // exclusive popcount prefix of rootbits along a row (idem)
+    // more room for the join lists on tiles too small to hold 32 entries per warp there
+    static constexpr int JSPARE = (32 * (C::NT / 32) > 2 * C::TH * C::NW) ? 32 * (C::NT / 32) - 2 * C::TH * C::NW : 1;
+    uint32_t jspare[JSPARE];
 };
 template <class C> struct SmemF : SmemRuns<C> {
     int lab[C::RMAX];                // final label of every strip run
@@ -580,8 +590,6 @@ template <class C> struct Tile {
                 half[q] = (uint16_t)m;  // little-endian: half 2w is the low half of word w
             }
         }
-        for (int q = tid; q < C::TH * C::NW; q += C::NT)
-            (&s.rootbits[0][0])[q] = 0u;
     }
 
     template <bool NZ, int PER>
@@ -670,8 +678,6 @@ template <class C> struct Tile {
                 s.eq[1][r][w] = eqU;
                 s.eq[2][r][w] = eqUR;
             }
-            for (int q = tid; q < C::TH * C::NW; q += C::NT)
-                (&s.rootbits[0][0])[q] = 0u;
         } else {
             (void)a;
             (void)s;
@@ -942,77 +948,88 @@ template <class C> struct Tile {
             unions_bin(a, s, tid);
     }
 
+    // The joins of a warp's units go through a list in shared memory (the root arrays,
+    // unused until the roots phase): rounds append every lane's next event (its r-th), so
+    // neighbouring entries come from different units, and in every pass each lane without
+    // a join in progress takes the next listed one.  Lanes stay busy until the warp's
+    // joins run out, instead of idling once their own unit's events are done.
+    static constexpr int JCAP = (2 * C::TH * C::NW + SL::JSPARE) / (C::NT / 32);
+    static_assert(JCAP >= 32, "join list too short");
+
     CCL_HD static void unions_bin(const Img &a, SL &s, int tid)
     {
+        static_assert(offsetof(SL, rootpre) == offsetof(SL, rootbits) + sizeof(uint32_t) * C::TH * C::NW &&
+                          offsetof(SL, jspare) == offsetof(SL, rootpre) + sizeof(int) * C::TH * C::NW,
+                      "the join lists span rootbits, rootpre and jspare");
+        uint32_t *jl = reinterpret_cast<uint32_t *>(&s.rootbits[0][0]) + (tid / 32) * JCAP;
+        const uint32_t lt = mask_lt(lane_id());
         // every thread runs the same number of outer passes (NT is a multiple of 32), so
         // whole warps reach the votes below
         for (int u0 = 0; u0 < C::NS * C::NW; u0 += C::NT) {
-            // A warp's loop below runs as long as its busiest lane, so the chunk's units are
-            // first ordered by their number of events (a counting sort) and thread t takes
-            // the t-th: each warp then holds units of about the same length.
-            // The sort pays only when some units have several events; a chunk without
-            // events (sparse or run-aligned content) skips the loop altogether.
-            UnitEvents e = unit_events(s, u0 + tid);
-            const int key = popc32(e.ev1 | e.ev2);
-            if (cta_count(key > 2, &s.red, tid) > 0) {
-                for (int q = tid; q < 33; q += C::NT)
-                    s.ucount[q] = 0;
-                cta_sync();
-                const int rank = at_add(&s.ucount[key], 1);
-                cta_sync();
-                if (tid < 32) {
-                    const int c = s.ucount[tid];
-                    const int incl = warp_incl_sum(c, 32);
-                    s.ucount[tid] = incl - c;
-                    if (tid == 31)
-                        s.ucount[32] = incl;
-                }
-                cta_sync();
-                s.uorder[s.ucount[key] + rank] = (uint16_t)tid;
-                cta_sync();
-                e = unit_events(s, u0 + s.uorder[tid]);
-            } else if (cta_count(key > 0, &s.red, tid) == 0) {
-                continue;
-            }
+            const UnitEvents e = unit_events(s, u0 + tid);
             uint32_t ev1 = e.ev1, ev2 = e.ev2;
+            if (!warp_ballot((ev1 | ev2) != 0u))
+                continue;  // no joins in this warp's units
             const uint32_t A = e.A, sA = e.sA, sB = e.sB;
             const int baseA = e.baseA, baseB = e.baseB;
-            // One loop for all of this thread's joins, run in step by the whole warp: each
-            // pass takes the thread's next event if it has no join in progress, then runs
-            // one step of Rem's union (Algorithm 2 with Algorithm 8's compare-and-swap
-            // writes, as in rem_unite_g).  A warp vote ends the loop, so the lanes stay
-            // converged and each pass is one short predicated block per part.
             // An event at bit b joins the A run covering column b or b-1 with the B run
             // covering b or b-1; with m = 1 << b, the runs covering b and b-1 are counted
             // by the masks m | (m - 1) and m - 1 (b = 0: the word to the left).  An event
-            // that joins the same two runs as the thread's previous one is skipped (its pass
-            // is one the other lanes run anyway).
+            // that joins the same two runs as the lane's previous one is not listed.
             uint32_t last = 0xFFFFFFFFu;
+            int head = 0, tail = 0;  // the warp's list: entries [head, tail) not yet taken
             int rx = -1, ry = -1;
             for (int it = 0;; it++) {
-                if (rx < 0 && (ev1 | ev2)) {
-                    const uint32_t E = ev1 | ev2;
-                    const uint32_t m = E & (0u - E);
-                    const uint32_t below = m - 1u, upto = below | m;
-                    const bool first = (ev1 & m) != 0u;  // an event of the first kind
-                    ev1 &= ~m;
-                    ev2 &= ~m;
-                    const uint32_t mA = (C::CONN == 8 && first && !(A & m)) ? below : upto;
-                    const uint32_t mB = (C::CONN == 8 && !first) ? below : upto;
-                    const int na = baseA + popc32(sA & mA), nb = baseB + popc32(sB & mB);
-                    const uint32_t key = ((uint32_t)na << 16) | (uint32_t)nb;
-                    if (key != last) {
-                        last = key;
-                        rx = CCL_CHK(nb, C::RMAX, a.status);
-                        ry = CCL_CHK(na, C::RMAX, a.status);
+                if (head == tail && warp_ballot((ev1 | ev2) != 0u)) {
+                    // refill: every lane's next events, one round at a time
+                    warp_sync();  // the old entries have all been read
+                    head = tail = 0;
+                    for (;;) {
+                        bool has = (ev1 | ev2) != 0u;
+                        uint32_t key = 0;
+                        if (has) {
+                            const uint32_t E = ev1 | ev2;
+                            const uint32_t m = E & (0u - E);
+                            const uint32_t below = m - 1u, upto = below | m;
+                            const bool first = (ev1 & m) != 0u;  // an event of the first kind
+                            ev1 &= ~m;
+                            ev2 &= ~m;
+                            const uint32_t mA = (C::CONN == 8 && first && !(A & m)) ? below : upto;
+                            const uint32_t mB = (C::CONN == 8 && !first) ? below : upto;
+                            const int na = baseA + popc32(sA & mA), nb = baseB + popc32(sB & mB);
+                            key = ((uint32_t)na << 16) | (uint32_t)nb;
+                            has = key != last;
+                            last = key;
+                        }
+                        const uint32_t mk = warp_ballot(has);
+                        if (has)
+                            jl[tail + popc32(mk & lt)] = key;
+                        tail += popc32(mk);
+                        if (tail > JCAP - 32 || !warp_ballot((ev1 | ev2) != 0u))
+                            break;
+                    }
+                    warp_sync();  // the new entries are visible to every lane
+                }
+                // lanes without a join in progress take the next listed joins, in order
+                const uint32_t fr = warp_ballot(rx < 0);
+                const int avail = tail - head;
+                if (rx < 0) {
+                    const int r = popc32(fr & lt);
+                    if (r < avail) {
+                        const uint32_t key = jl[head + r];
+                        rx = CCL_CHK((int)(key & PAR_LO), C::RMAX, a.status);
+                        ry = CCL_CHK((int)(key >> 16), C::RMAX, a.status);
                     }
                 }
-                if (!warp_ballot(rx >= 0 || (ev1 | ev2) != 0u))
+                head += imin(popc32(fr), avail);
+                if (!warp_ballot(rx >= 0) && head == tail && !warp_ballot((ev1 | ev2) != 0u))
                     break;
                 if (it == SMEM_LOOP_CAP) {
                     flag_status(a.status, ST_LOOP_CAP);
                     break;
                 }
+                // one step of Rem's union (Algorithm 2 with Algorithm 8's compare-and-swap
+                // writes, as in rem_unite_g)
                 if (rx >= 0) {
                     const uint32_t px = ld_su(&s.par[rx]);
                     const uint32_t py = ld_su(&s.par[ry]);
@@ -1033,6 +1050,7 @@ template <class C> struct Tile {
                 }
             }
         }
+        warp_sync();
     }
 
     // -- phase: every run points at its root.  A component's first pixel lies in its
@@ -1040,6 +1058,10 @@ template <class C> struct Tile {
     // root's key (high half of its word) to the smallest first pixel among them.
     CCL_HD static void roots(const Img &a, SL &s, int tid)
     {
+        // the root bits held the union phase's join lists: clear them for mark_roots (a
+        // barrier separates this phase from mark_roots)
+        for (int q = tid; q < C::TH * C::NW; q += C::NT)
+            (&s.rootbits[0][0])[q] = 0u;
         for (int u = tid; u < C::NS * C::NW; u += C::NT) {
             const int st = u / C::NW, w = u % C::NW;
             uint32_t todo = s.starts[st][w];

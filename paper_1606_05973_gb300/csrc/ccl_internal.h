@@ -82,6 +82,7 @@ struct TuneRow {
     int64_t max_px;
     int shape[3];
     int ctas_per_sm;
+    int persistent;  // batches of this class take the persistent launch (else three kernels)
 };
 struct Tuning {
     const TuneRow *rows;
@@ -103,8 +104,8 @@ int sm_count();
 // CTAs per SM of the persistent launch, overriding the tuning table (0: the table's)
 void set_fused_ctas_per_sm(int n);
 int fused_ctas_per_sm_override();
-// process-wide launch mode: 0 = automatic (persistent launch for batches and for single
-// images up to the tuned size), 1 = always the three kernels
+// process-wide launch mode: 0 = automatic (the tuning table decides for batches and single
+// images), 1 = always the three kernels, 2 = always the persistent launch
 void set_launch_mode(int m);
 int launch_mode();
 
@@ -144,7 +145,9 @@ int64_t fused_image_bytes(int32_t H, int32_t W, int conn);
 int64_t fused_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn);
 int32_t enqueue_fused(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
                       Workspace *w, cudaStream_t s);
-// a batch launch in the current launch mode (persistent or three kernels)
+// a batch launch in the current launch mode and the tuning row of its pixel count
+// (persistent or three kernels)
+bool batch_persistent(const ccl_image *imgs, const int32_t *keep, int32_t m);
 int64_t launch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn);
 int32_t enqueue_launch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
                        Workspace *w, cudaStream_t s);

@@ -172,17 +172,20 @@ bool try_launch_locked(ccl_server *s, Lane &L)
     L.keep.clear();
     L.ids.clear();
     const int conn = s->cfg.connectivity;
-    const bool fused = launch_mode() == 0;  // one persistent launch per batch
     const int64_t room = largest_free_locked(s);
-    int64_t px = 0, sum_n = 0, sum_w = 0;
+    int64_t px = 0, sum_n = 0, sum_w = 0, sum_f = 0;
     while (!s->pending.empty() && (int32_t)L.ids.size() < s->cfg.max_batch) {
         const uint64_t id = s->pending.front();
         Request &r = s->reqs[id];
         const int32_t m = (int32_t)L.ids.size() + 1;
         int64_t need, add_n = 0, add_w = 0;
+        // the launch form follows the tuning row of the grown batch's pixel count
+        const int64_t add_f = fused_image_bytes(r.img.H, r.img.W, conn);
+        const bool fused = launch_mode() == 2 || (launch_mode() == 0 && tune_row(px + r.pixels).persistent != 0);
         if (fused) {
-            add_n = add_w = fused_image_bytes(r.img.H, r.img.W, conn);
-            need = fused_fixed_bytes(m) + sum_n + add_n;
+            add_n = main_layout(r.img.H, r.img.W, conn == 8 ? (8 | CONN_NARROW) : conn).bytes;
+            add_w = conn == 8 ? main_layout(r.img.H, r.img.W, 8 | CONN_WIDE).bytes : add_n;
+            need = fused_fixed_bytes(m) + sum_f + add_f;
         } else if (conn == 8) {
             add_n = main_layout(r.img.H, r.img.W, 8 | CONN_NARROW).bytes;
             add_w = main_layout(r.img.H, r.img.W, 8 | CONN_WIDE).bytes;
@@ -206,6 +209,7 @@ bool try_launch_locked(ccl_server *s, Lane &L)
         px += r.pixels;
         sum_n += add_n;
         sum_w += add_w;
+        sum_f += add_f;
         s->pending.pop_front();
     }
     const int32_t m = (int32_t)L.ids.size();

@@ -91,6 +91,8 @@ def main():
             out[kern]["Mcycles_per_launch"] = round(tot / n / 1e6, 2)
         print(name, json.dumps(out), flush=True)
 
+    for side in (256, 1024):
+        run(f"{side} bernoulli p=0.5", torch.from_numpy(synth.bernoulli(side, side, 0.5, 1)).to(dev))
     for kind, arg, seed in synth.SWEEP_8192:
         if kind == "bernoulli":
             run(f"8192 bernoulli p={arg}", torch.from_numpy(synth.bernoulli(8192, 8192, arg, seed)).to(dev))

@@ -120,6 +120,7 @@ def write_table(out_json, out_txt):
     rows, lines = [], []
     for bound, (count, side) in SIZE_CLASSES:
         per = {}  # (density, shape, ctas) -> ms
+        per3 = {}  # density -> ms of the three-launch batch
         for di, p in enumerate(DENSITIES):
             imgs = [torch.from_numpy(synth.bernoulli(side, side, p, 300 + 7 * di + i)).to(dev) for i in range(count)]
             outs = [torch.empty((side, side), dtype=torch.int32, device=dev) for _ in imgs]
@@ -136,6 +137,14 @@ def write_table(out_json, out_txt):
                     elif k != ref:
                         raise RuntimeError(f"K differs across shapes: {side} p={p} {shape} {c}")
                     per[(di, shape, c)] = ms
+            # the same batch in three launches (the size rule's tile shape)
+            lib.ccl_set_tile_policy(0)
+            lib.ccl_set_persistent_ctas_per_sm(0)
+            lib.ccl_set_launch_mode(1)
+            per3[di] = _time(lambda: ccl.label_batch(imgs, outs=outs, k_out=kd), sync)
+            lib.ccl_set_launch_mode(0)
+            if kd.cpu().tolist() != ref:
+                raise RuntimeError(f"K differs between the launch modes: {side} p={p}")
             del imgs, outs
             torch.cuda.empty_cache()
         lib.ccl_set_tile_policy(0)
@@ -144,12 +153,16 @@ def write_table(out_json, out_txt):
         for di in range(3):
             best_shape.append(min(("64x128", "64x256"), key=lambda sh: min(per[(di, sh, c)] for c in CTAS)))
         best_c = min(CTAS, key=lambda c: sum(per[(di, best_shape[di], c)] for di in range(3)))
-        rows.append({"max_px": bound, "shape": best_shape, "ctas_per_sm": best_c})
+        pers_ms = sum(per[(di, best_shape[di], best_c)] for di in range(3))
+        rows.append({"max_px": bound, "shape": best_shape, "ctas_per_sm": best_c,
+                     "persistent": bool(pers_ms < sum(per3.values()))})
         lines.append(f"class <= {bound if bound else 'inf'} px ({count} x {side}^2):")
         for di, p in enumerate(DENSITIES):
             cells = "  ".join(f"{sh}/{c}: {per[(di, sh, c)]:.4f}" for sh in ("64x128", "64x256") for c in CTAS)
             lines.append(f"  p={p}  {cells}  -> {best_shape[di]}")
-        lines.append(f"  grid: {best_c} CTAs per SM")
+        lines.append(f"  grid: {best_c} CTAs per SM; three launches: "
+                     + "  ".join(f"p={p}: {per3[di]:.4f}" for di, p in enumerate(DENSITIES))
+                     + f" -> {'persistent' if rows[-1]['persistent'] else 'three launches'}")
     # single images: persistent launch (a batch of one) against the three kernels
     single_max = 0
     lines.append("single images, ms per call: persistent / three kernels")

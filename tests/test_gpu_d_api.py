@@ -78,25 +78,22 @@ def test_profile_counts_launches(ccl):
     import torch
 
     img = torch.from_numpy(synth.bernoulli(512, 512, 0.5, 1)).cuda()
-    # default launch mode: a small image is one persistent launch
-    ccl.ccl_profile_reset()
-    ccl.ccl_profile_enable(1)
-    ccl.label(img)
-    ccl.label(img)
-    ccl.ccl_profile_enable(0)
-    kt = ccl.kernel_times()
+
+    def counts(mode):
+        assert ccl.lib().ccl_set_launch_mode(mode) == 0
+        try:
+            ccl.ccl_profile_reset()
+            ccl.ccl_profile_enable(1)
+            ccl.label(img)
+            ccl.label(img)
+            ccl.ccl_profile_enable(0)
+            return ccl.kernel_times()
+        finally:
+            ccl.lib().ccl_set_launch_mode(0)
+
+    kt = counts(2)  # forced persistent launch: one launch per image
     assert kt["persistent"][0] == 2 and kt["tile_local"][0] == 0 and kt["persistent"][1] > 0.0
-    # three kernels per image when forced
-    assert ccl.lib().ccl_set_launch_mode(1) == 0
-    try:
-        ccl.ccl_profile_reset()
-        ccl.ccl_profile_enable(1)
-        ccl.label(img)
-        ccl.label(img)
-        ccl.ccl_profile_enable(0)
-        kt = ccl.kernel_times()
-    finally:
-        ccl.lib().ccl_set_launch_mode(0)
+    kt = counts(1)  # three kernels per image
     assert kt["tile_local"][0] == 2 and kt["final_labels"][0] == 2 and kt["persistent"][0] == 0
     assert kt["final_labels"][1] > 0.0
     ccl.ccl_profile_reset()

@@ -1,9 +1,11 @@
 """The persistent single-launch path (one cooperative kernel for the tile pass, the boundary
-merge, flatten and the labelling pass) against the oracle and against the three-kernel
-path, element by element: single small images (which take it by default), batches of
+merge, flatten and the labelling pass; forced with ccl_set_launch_mode(2)) against the
+oracle and against the three-kernel path, element by element: single images, batches of
 uneven images under every tile policy and under each density class of the tuning table's
 probe, 4-connectivity, multi-class, and replay from a CUDA graph."""
 import ctypes
+import json
+import os
 
 import numpy as np
 import pytest
@@ -46,7 +48,7 @@ SHAPES = [(1, 1), (1, 300), (300, 1), (63, 255), (64, 256), (65, 257), (129, 100
 def test_single_images_persistent_equals_three_kernels_and_oracle(lib, h, w, p):
     img = synth.bernoulli(h, w, p, h * 7 + w)
     ref, rk = oracle.cclremsp(img)
-    a, ka = _label(lib, img, mode=0)
+    a, ka = _label(lib, img, mode=2)
     b, kb = _label(lib, img, mode=1)
     assert ka == kb == rk
     assert np.array_equal(a, ref) and np.array_equal(b, ref)
@@ -56,7 +58,7 @@ def test_single_images_persistent_equals_three_kernels_and_oracle(lib, h, w, p):
 def test_single_serpentine_and_blobs(lib, conn):
     for img in (synth.serpentine(999, 1501), synth.blobs(1200, 900, 6.0, 3)):
         ref, rk = oracle.cclremsp(img, conn)
-        got, k = _label(lib, img, conn=conn, mode=0)
+        got, k = _label(lib, img, conn=conn, mode=2)
         assert k == rk and np.array_equal(got, ref)
 
 
@@ -65,6 +67,7 @@ def _batch(lib, imgs, conn=8, classes=False):
 
     import paper_1606_05973_gb300 as ccl
 
+    assert lib.ccl_set_launch_mode(2) == 0
     dev = [torch.from_numpy(im).cuda() for im in imgs]
     labs, kd = ccl.label_batch(dev, connectivity=conn, classes=classes)
     torch.cuda.synchronize()
@@ -87,9 +90,13 @@ def test_batch_every_tile_policy(lib, policy):
 
 @pytest.mark.parametrize("p", [0.05, 0.5, 0.95])
 def test_batch_in_each_density_class(lib, p):
-    """Three 2048 x 2048 images (12.6 M pixels: the tuning row whose density classes take
-    different shapes, so the probe decides) at densities in each class."""
-    imgs = [synth.bernoulli(2048, 2048, p, 60 + i) for i in range(3)]
+    """Three 576 x 576 images (under 1 M pixels in all: the tuning row whose density classes
+    take different shapes, so the probe decides) at densities in each class."""
+    import paper_1606_05973_gb300 as ccl
+
+    t = json.load(open(os.path.join(os.path.dirname(ccl.__file__), "tuning.json")))
+    assert len(set(t["rows"][0]["shape"])) > 1, "the first row no longer exercises the probe"
+    imgs = [synth.bernoulli(576, 576, p, 60 + i) for i in range(3)]
     labs, ks = _batch(lib, imgs)
     for im, lab, k in zip(imgs, labs, ks):
         ref, rk = oracle.cclremsp(im)
@@ -120,6 +127,7 @@ def test_batch_graph_replay_persistent(lib):
     dev = [torch.from_numpy(im).cuda() for im in imgs]
     outs = [torch.full(im.shape, -1, dtype=torch.int32, device="cuda") for im in imgs]
     kd = torch.full((len(imgs),), -1, dtype=torch.int32, device="cuda")
+    assert lib.ccl_set_launch_mode(2) == 0
     st = torch.cuda.Stream()
     st.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(st):
