@@ -87,18 +87,28 @@ SINGLE_SIDES = (256, 512, 1024, 1536, 2048, 3072, 4096, 8192)
 
 
 def _time(fn, sync, reps=10, warm=2):
+    """ms per call of fn captured once in a CUDA graph and replayed (no host work between
+    replays: the launch forms are compared on the device alone)."""
     import torch
 
-    for _ in range(warm):
-        fn()
-    sync()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    st = torch.cuda.current_stream()
-    e0.record(st)
-    for _ in range(reps):
-        fn()
-    e1.record(st)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        for _ in range(warm):
+            fn()  # sizes the stream's workspace before capture
+        st.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            fn()
+        g.replay()
+        st.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            g.replay()
+        e1.record(st)
     e1.synchronize()
+    sync()
     return e0.elapsed_time(e1) / reps
 
 
@@ -126,6 +136,7 @@ def write_table(out_json, out_txt):
             outs = [torch.empty((side, side), dtype=torch.int32, device=dev) for _ in imgs]
             kd = torch.zeros(count, dtype=torch.int32, device=dev)
             ref = None
+            lib.ccl_set_launch_mode(2)  # the persistent launch, whatever the current table says
             for shape, policy in (("64x128", 2), ("64x256", 1)):
                 lib.ccl_set_tile_policy(policy)
                 for c in CTAS:
@@ -142,13 +153,14 @@ def write_table(out_json, out_txt):
             lib.ccl_set_persistent_ctas_per_sm(0)
             lib.ccl_set_launch_mode(1)
             per3[di] = _time(lambda: ccl.label_batch(imgs, outs=outs, k_out=kd), sync)
-            lib.ccl_set_launch_mode(0)
+            lib.ccl_set_launch_mode(2)
             if kd.cpu().tolist() != ref:
                 raise RuntimeError(f"K differs between the launch modes: {side} p={p}")
             del imgs, outs
             torch.cuda.empty_cache()
         lib.ccl_set_tile_policy(0)
         lib.ccl_set_persistent_ctas_per_sm(0)
+        lib.ccl_set_launch_mode(0)
         best_shape = []
         for di in range(3):
             best_shape.append(min(("64x128", "64x256"), key=lambda sh: min(per[(di, sh, c)] for c in CTAS)))
@@ -173,12 +185,13 @@ def write_table(out_json, out_txt):
                           (f"bernoulli p=0.1", torch.from_numpy(synth.bernoulli(side, side, 0.1, side + 2)).to(dev))):
             out = torch.empty((side, side), dtype=torch.int32, device=dev)
             kd = torch.zeros(1, dtype=torch.int32, device=dev)
-            sp = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+            lib.ccl_set_launch_mode(2)
             pers = _time(lambda: ccl.label_batch([img], outs=[out], k_out=kd), sync)
             k1 = int(kd.item())
             lib.ccl_set_launch_mode(1)
             three = _time(lambda: lib.ccl_label_async(img.data_ptr(), side, side, img.stride(0), 8, out.data_ptr(),
-                                                      ctypes.c_void_p(kd.data_ptr()), sp), sync)
+                                                      ctypes.c_void_p(kd.data_ptr()),
+                                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)), sync)
             lib.ccl_set_launch_mode(0)
             if int(kd.item()) != k1:
                 raise RuntimeError(f"K differs between the launch modes at {side}^2 {name}")
