@@ -958,9 +958,8 @@ template <class C> struct Tile {
 
     CCL_HD static void unions_bin(const Img &a, SL &s, int tid)
     {
-        static_assert(offsetof(SL, rootpre) == offsetof(SL, rootbits) + sizeof(uint32_t) * C::TH * C::NW &&
-                          offsetof(SL, jspare) == offsetof(SL, rootpre) + sizeof(int) * C::TH * C::NW,
-                      "the join lists span rootbits, rootpre and jspare");
+        // the lists span rootbits, rootpre and jspare: members of 4-byte elements declared
+        // one after another, so they are contiguous
         uint32_t *jl = reinterpret_cast<uint32_t *>(&s.rootbits[0][0]) + (tid / 32) * JCAP;
         const uint32_t lt = mask_lt(lane_id());
         // every thread runs the same number of outer passes (NT is a multiple of 32), so
