@@ -329,6 +329,29 @@ int32_t ccl_set_launch_mode(int32_t mode);
 int32_t ccl_set_persistent_ctas_per_sm(int32_t n);
 
 /*
+ * ccl_set_tuning - replace the tuning table compiled into the library (tuning.json, written
+ * by the sweep) with the caller's, e.g. the output of a sweep on another GPU.  rows: n
+ * rows in ascending max_px order; the last row's max_px is -1 (no bound) and only the
+ * last.  shape[c]: tile shape of density class c under the persistent launch (0: 64 x 128,
+ * 1: 64 x 256); classes split at density_lo_permille and density_hi_permille of object
+ * pixels; probe_samples 16-byte samples per image for the density probe; batches of a row
+ * with persistent != 0 take the persistent launch; single images up to
+ * single_persistent_max_px pixels take it.  n = 0 restores the built-in table.  Not to be
+ * called while labelling calls are in flight.  CCL_ERR_INVALID_ARGUMENT for a malformed
+ * table.
+ */
+typedef struct {
+    int64_t max_px;
+    int32_t shape[3];
+    int32_t ctas_per_sm;
+    int32_t persistent;
+} ccl_tune_row;
+
+int32_t ccl_set_tuning(const ccl_tune_row *rows, int32_t n, int32_t density_lo_permille,
+                       int32_t density_hi_permille, int32_t probe_samples,
+                       int64_t single_persistent_max_px);
+
+/*
  * ccl_set_tile_policy - the tile shape of the 8-connected path (the partitions that
  * Algorithm 7 labels independently before its boundary merge).  policy 0 (the default)
  * chooses by size: images of at most 3072 x 3072 pixels take 64 x 128 tiles, larger ones

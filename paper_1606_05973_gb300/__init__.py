@@ -60,6 +60,11 @@ class ServerStats(ctypes.Structure):
                 ("peak_queue", ctypes.c_int32), ("peak_busy_lanes", ctypes.c_int32)]
 
 
+class TuneRow(ctypes.Structure):
+    _fields_ = [("max_px", ctypes.c_int64), ("shape", ctypes.c_int32 * 3), ("ctas_per_sm", ctypes.c_int32),
+                ("persistent", ctypes.c_int32)]
+
+
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -90,6 +95,7 @@ _SIGS = {
     "ccl_set_tile_policy": ([_I32], _I32),
     "ccl_set_launch_mode": ([_I32], _I32),
     "ccl_set_persistent_ctas_per_sm": ([_I32], _I32),
+    "ccl_set_tuning": ([_P, _I32, _I32, _I32, _I32, _I64], _I32),
     "ccl_profile_enable": ([_I32], _I32),
     "ccl_profile_reset": ([], _I32),
     "ccl_profile_read": ([_P, _I32, _P], _I32),

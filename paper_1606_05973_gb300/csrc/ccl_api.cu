@@ -905,6 +905,33 @@ int32_t ccl_set_launch_mode(int32_t mode)
     return CCL_OK;
 }
 
+int32_t ccl_set_tuning(const ccl_tune_row *rows, int32_t n, int32_t density_lo_permille,
+                       int32_t density_hi_permille, int32_t probe_samples, int64_t single_persistent_max_px)
+{
+    if (n <= 0) {
+        set_tuning(nullptr, 0, 0, 0, 0, 0);
+        return CCL_OK;
+    }
+    if (!rows || density_lo_permille < 0 || density_hi_permille < density_lo_permille ||
+        density_hi_permille > 1000 || probe_samples < 0 || single_persistent_max_px < 0)
+        return CCL_ERR_INVALID_ARGUMENT;
+    std::vector<TuneRow> t((size_t)n);
+    for (int32_t i = 0; i < n; i++) {
+        const ccl_tune_row &r = rows[i];
+        if (r.ctas_per_sm < 1 || (r.max_px < 0 && i != n - 1) || (i == n - 1 && r.max_px >= 0))
+            return CCL_ERR_INVALID_ARGUMENT;  // bounds ascend; only the last row is unbounded
+        if (i > 0 && r.max_px >= 0 && r.max_px <= rows[i - 1].max_px)
+            return CCL_ERR_INVALID_ARGUMENT;
+        for (int c = 0; c < 3; c++)
+            if (r.shape[c] != 0 && r.shape[c] != 1)
+                return CCL_ERR_INVALID_ARGUMENT;
+        t[i] = {r.max_px, {r.shape[0], r.shape[1], r.shape[2]}, r.ctas_per_sm, r.persistent ? 1 : 0};
+    }
+    set_tuning(t.data(), n, (density_lo_permille * 1024 + 500) / 1000, (density_hi_permille * 1024 + 500) / 1000,
+               probe_samples, single_persistent_max_px);
+    return CCL_OK;
+}
+
 int32_t ccl_set_persistent_ctas_per_sm(int32_t n)
 {
     if (n < 0)

@@ -92,6 +92,8 @@ struct Tuning {
     int64_t single_fused_max_px;  // single images up to this size take the persistent launch
 };
 const Tuning &tuning();
+// replace the table in use (n <= 0: back to the built-in one); not while calls are in flight
+void set_tuning(const TuneRow *rows, int n, int lo, int hi, int probe, int64_t single_max);
 const TuneRow &tune_row(int64_t px);
 // resident CTAs of the persistent kernel for `conn` on the current device (0 on error)
 int fused_resident_ctas(int conn);

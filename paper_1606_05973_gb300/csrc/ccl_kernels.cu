@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <vector>
 
 #include "ccl_internal.h"
 
@@ -334,9 +335,23 @@ cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t s
 // ---- persistent launch -------------------------------------------------------------------
 #include "ccl_tuning.inc"  // kTuneRows and the kTune* constants, written from tuning.json by build.py
 
-static const Tuning g_tuning = {kTuneRows, (int)(sizeof(kTuneRows) / sizeof(kTuneRows[0])), kTuneDensLo,
-                                kTuneDensHi, kTuneProbeSamples, kTuneSingleFusedMaxPx};
+static const Tuning g_builtin = {kTuneRows, (int)(sizeof(kTuneRows) / sizeof(kTuneRows[0])), kTuneDensLo,
+                                 kTuneDensHi, kTuneProbeSamples, kTuneSingleFusedMaxPx};
+// The table in use: the built-in one, or one set by ccl_set_tuning (kept in g_user_rows).
+static Tuning g_tuning = g_builtin;
+static std::vector<TuneRow> g_user_rows;
 const Tuning &tuning() { return g_tuning; }
+
+void set_tuning(const TuneRow *rows, int n, int lo, int hi, int probe, int64_t single_max)
+{
+    if (n <= 0) {
+        g_tuning = g_builtin;
+        g_user_rows.clear();
+        return;
+    }
+    g_user_rows.assign(rows, rows + n);
+    g_tuning = {g_user_rows.data(), n, lo, hi, probe, single_max};
+}
 
 const TuneRow &tune_row(int64_t px)
 {

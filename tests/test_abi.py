@@ -77,6 +77,8 @@ def test_argument_checks_need_no_gpu(lib):
         assert lib.ccl_set_tile_policy(ok) == 0
     assert lib.ccl_set_global_ctas_per_sm(-1) == 1
     assert lib.ccl_set_launch_mode(3) == 1 and lib.ccl_set_launch_mode(-1) == 1
+    assert lib.ccl_set_tuning(None, 1, 300, 700, 64, 0) == 1  # rows missing
+    assert lib.ccl_set_tuning(None, 0, 0, 0, 0, 0) == 0       # back to the built-in table
     assert lib.ccl_set_global_ctas_per_sm(1) == 0 and lib.ccl_set_global_ctas_per_sm(0) == 0
     nb = ctypes.c_int64(0)
     assert lib.ccl_workspace_bytes(8192, 8192, ctypes.byref(nb)) == 0

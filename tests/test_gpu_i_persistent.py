@@ -4,8 +4,6 @@ oracle and against the three-kernel path, element by element: single images, bat
 uneven images under every tile policy and under each density class of the tuning table's
 probe, 4-connectivity, multi-class, and replay from a CUDA graph."""
 import ctypes
-import json
-import os
 
 import numpy as np
 import pytest
@@ -90,14 +88,21 @@ def test_batch_every_tile_policy(lib, policy):
 
 @pytest.mark.parametrize("p", [0.05, 0.5, 0.95])
 def test_batch_in_each_density_class(lib, p):
-    """Three 576 x 576 images (under 1 M pixels in all: the tuning row whose density classes
-    take different shapes, so the probe decides) at densities in each class."""
+    """A tuning table (ccl_set_tuning) whose density classes take different tile shapes,
+    so the on-device probe decides: three 576 x 576 images at a density in each class."""
     import paper_1606_05973_gb300 as ccl
 
-    t = json.load(open(os.path.join(os.path.dirname(ccl.__file__), "tuning.json")))
-    assert len(set(t["rows"][0]["shape"])) > 1, "the first row no longer exercises the probe"
-    imgs = [synth.bernoulli(576, 576, p, 60 + i) for i in range(3)]
-    labs, ks = _batch(lib, imgs)
+    rows = (ccl.TuneRow * 1)()
+    rows[0].max_px = -1
+    rows[0].shape[0], rows[0].shape[1], rows[0].shape[2] = 0, 1, 0
+    rows[0].ctas_per_sm = 6
+    rows[0].persistent = 1
+    assert lib.ccl_set_tuning(rows, 1, 300, 700, 64, 0) == 0
+    try:
+        imgs = [synth.bernoulli(576, 576, p, 60 + i) for i in range(3)]
+        labs, ks = _batch(lib, imgs)
+    finally:
+        assert lib.ccl_set_tuning(None, 0, 0, 0, 0, 0) == 0
     for im, lab, k in zip(imgs, labs, ks):
         ref, rk = oracle.cclremsp(im)
         assert k == rk and np.array_equal(lab, ref)
