@@ -58,6 +58,10 @@ int emu_shfl_up(int v, int delta, int width);
 int emu_lane();
 #endif
 
+#ifndef CCL_REFILL
+#define CCL_REFILL 1
+#endif
+
 namespace ccl {
 
 // ---- flags and sentinels ---------------------------------------------------------------
@@ -954,6 +958,8 @@ template <class C> struct Tile {
     // a join in progress takes the next listed one.  Lanes stay busy until the warp's
     // joins run out, instead of idling once their own unit's events are done.
     static constexpr int JCAP = (2 * C::TH * C::NW + SL::JSPARE) / (C::NT / 32);
+    // events a lane lists per refill round (fewer rounds, fewer votes)
+    static constexpr int REFILL = (JCAP >= 64 * CCL_REFILL) ? CCL_REFILL : 1;
     static_assert(JCAP >= 32, "join list too short");
 
     CCL_HD static void unions_bin(const Img &a, SL &s, int tid)
@@ -980,31 +986,40 @@ template <class C> struct Tile {
             int rx = -1, ry = -1;
             for (int it = 0;; it++) {
                 if (head == tail && warp_ballot((ev1 | ev2) != 0u)) {
-                    // refill: every lane's next events, one round at a time
+                    // refill: every lane's next REFILL events per round, the round's first
+                    // events of all lanes before its second ones
                     warp_sync();  // the old entries have all been read
                     head = tail = 0;
                     for (;;) {
-                        bool has = (ev1 | ev2) != 0u;
-                        uint32_t key = 0;
-                        if (has) {
-                            const uint32_t E = ev1 | ev2;
-                            const uint32_t m = E & (0u - E);
-                            const uint32_t below = m - 1u, upto = below | m;
-                            const bool first = (ev1 & m) != 0u;  // an event of the first kind
-                            ev1 &= ~m;
-                            ev2 &= ~m;
-                            const uint32_t mA = (C::CONN == 8 && first && !(A & m)) ? below : upto;
-                            const uint32_t mB = (C::CONN == 8 && !first) ? below : upto;
-                            const int na = baseA + popc32(sA & mA), nb = baseB + popc32(sB & mB);
-                            key = ((uint32_t)na << 16) | (uint32_t)nb;
-                            has = key != last;
-                            last = key;
+                        uint32_t key[REFILL];
+                        bool has[REFILL];
+                        CCL_UNROLL
+                        for (int q = 0; q < REFILL; q++) {
+                            has[q] = (ev1 | ev2) != 0u;
+                            key[q] = 0;
+                            if (has[q]) {
+                                const uint32_t E = ev1 | ev2;
+                                const uint32_t m = E & (0u - E);
+                                const uint32_t below = m - 1u, upto = below | m;
+                                const bool first = (ev1 & m) != 0u;  // an event of the first kind
+                                ev1 &= ~m;
+                                ev2 &= ~m;
+                                const uint32_t mA = (C::CONN == 8 && first && !(A & m)) ? below : upto;
+                                const uint32_t mB = (C::CONN == 8 && !first) ? below : upto;
+                                const int na = baseA + popc32(sA & mA), nb = baseB + popc32(sB & mB);
+                                key[q] = ((uint32_t)na << 16) | (uint32_t)nb;
+                                has[q] = key[q] != last;
+                                last = key[q];
+                            }
                         }
-                        const uint32_t mk = warp_ballot(has);
-                        if (has)
-                            jl[tail + popc32(mk & lt)] = key;
-                        tail += popc32(mk);
-                        if (tail > JCAP - 32 || !warp_ballot((ev1 | ev2) != 0u))
+                        CCL_UNROLL
+                        for (int q = 0; q < REFILL; q++) {
+                            const uint32_t mk = warp_ballot(has[q]);
+                            if (has[q])
+                                jl[tail + popc32(mk & lt)] = key[q];
+                            tail += popc32(mk);
+                        }
+                        if (tail > JCAP - 32 * REFILL || !warp_ballot((ev1 | ev2) != 0u))
                             break;
                     }
                     warp_sync();  // the new entries are visible to every lane
@@ -1366,7 +1381,10 @@ template <class C> CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it)
 // grows geometrically and a path of n nodes needs about log(n)/log(JUMP_HOPS+1) rounds
 // (the paper's sequential flatten needs one pass because it visits labels in increasing
 // order; that order is not available to parallel threads).
-constexpr int JUMP_HOPS = 16;
+#ifndef CCL_JUMP_HOPS
+#define CCL_JUMP_HOPS 16
+#endif
+constexpr int JUMP_HOPS = CCL_JUMP_HOPS;
 #ifndef CCL_MERGE_BATCH
 #define CCL_MERGE_BATCH 1
 #endif
