@@ -59,7 +59,7 @@ int emu_lane();
 #endif
 
 #ifndef CCL_REFILL
-#define CCL_REFILL 1
+#define CCL_REFILL 2
 #endif
 
 namespace ccl {
@@ -1382,7 +1382,7 @@ template <class C> CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it)
 // (the paper's sequential flatten needs one pass because it visits labels in increasing
 // order; that order is not available to parallel threads).
 #ifndef CCL_JUMP_HOPS
-#define CCL_JUMP_HOPS 16
+#define CCL_JUMP_HOPS 32
 #endif
 constexpr int JUMP_HOPS = CCL_JUMP_HOPS;
 #ifndef CCL_MERGE_BATCH
