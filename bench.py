@@ -11,7 +11,7 @@ resident in HBM.  ``sweep8192`` (six 8192 x 8192 images: Bernoulli p in
 can be timed the same way; the default run also reports both as extra keys, with the
 1024 x 1024 call replayed from a CUDA graph.
 
-The images of a step alternate over two streams (``--streams``) with the cooperative
+The images of a step go round robin over three streams (``--streams``) with the cooperative
 global kernel capped at one CTA per SM (``--global-ctas-per-sm``,
 ``ccl_set_global_ctas_per_sm``), so that one image's tile pass can run beside another's
 global pass.  The line also carries the same steps on one stream with the library's
@@ -437,6 +437,42 @@ def run_ours(args, rank, world, local_rank):
     # correctness spot check outside the timed region: K must match a fresh labelling
     ks = kdev.cpu().tolist()
 
+    # the same images per step in one ccl_label_batch call (one launch per kernel over all
+    # of them), replayed from a CUDA graph, for comparison with the per-image calls
+    same_batch = None
+    if len(imgs) > 1:
+        kb = torch.zeros(len(imgs), dtype=torch.int32, device=dev)
+        lib.ccl_set_global_ctas_per_sm(0)  # one stream: the global kernel may fill every SM
+        bst = torch.cuda.Stream(device=dev)
+        bst.wait_stream(stream)
+        with torch.cuda.stream(bst):
+            def bcall():
+                ccl.label_batch([t for _, t in imgs], connectivity=args.connectivity, outs=labels, stream=bst,
+                                k_out=kb)
+
+            bcall()
+            bst.synchronize()
+            gb = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gb, stream=bst):
+                bcall()
+            gb.replay()
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record(bst)
+            for _ in range(args.steps):
+                gb.replay()
+            b1.record(bst)
+        torch.cuda.synchronize()
+        if args.global_ctas_per_sm is not None:
+            lib.ccl_set_global_ctas_per_sm(args.global_ctas_per_sm)
+        check_status("the same-images batch pass", [ctypes.c_void_p(bst.cuda_stream)])
+        if kb.cpu().tolist() != ks:
+            raise RuntimeError("batched and per-image component counts differ")
+        bms = b0.elapsed_time(b1) / args.steps
+        same_batch = {"ms_per_step": round(bms, 4), "value": round(px_per_step / (bms * 1e-3) / 1e9, 2),
+                      "path_frac": round(PATH_BYTES_PER_PX * px_per_step / (bms * 1e-3) / 1e9 / hbm_peak()[0], 4),
+                      "how": "the step's images in one ccl_label_batch call (the tuning table's launch form), "
+                             "replayed from a CUDA graph"}
+
     # end to end through the host-buffer entry point (pinned memory), outside the timed region
     host_imgs = [t.cpu().pin_memory() for _, t in imgs]
     host_labs = [torch.empty(tuple(t.shape), dtype=torch.int32).pin_memory() for _, t in imgs]
@@ -467,6 +503,13 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
     check_status("the end-to-end pass", e2e_sptr)
+    # what bounds it: one stream's device-to-host copy of one image's labels into pinned memory
+    d2h0, d2h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d2h0.record(stream)
+    host_labs[0].copy_(labels[0], non_blocking=True)
+    d2h1.record(stream)
+    torch.cuda.synchronize()
+    d2h_gbs = 4 * labels[0].numel() / (d2h0.elapsed_time(d2h1) * 1e-3) / 1e9
     lib.ccl_set_global_ctas_per_sm(0)  # library default for the measurements below
     for i, hl in enumerate(host_labs):
         if int(hl.max()) != ks[i] or int(host_k[i]) != ks[i]:
@@ -511,6 +554,7 @@ def run_ours(args, rank, world, local_rank):
                            if k in KERNEL_BYTES_PER_PX else {})}
                     for k, v in kt.items() if v[0]},
         "per_image": per_image,
+        "same_images_batched": same_batch,
         "kernels_pass": {"steps": args.steps, "ms_per_step": round(prof_ms / args.steps, 4),
                          "how": "a second timed pass of the same steps with an event pair around every "
                                 "launch; `value` comes from the pass without them"},
@@ -520,7 +564,9 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": int(sum(t.numel() for t in host_imgs)),
                 "d2h_bytes_per_step": int(sum(4 * t.numel() + 4 for t in host_labs)),
                 "api": "ccl_label_host_async on two streams, images alternating (pinned host buffers, "
-                       "copies inside the timed region, both streams synchronised at the end of each step)"},
+                       "copies inside the timed region, both streams synchronised at the end of each step)",
+                "d2h_copy_gbs": round(d2h_gbs, 1),
+                "d2h_copy_how": "one image's labels, device to pinned host memory, one copy on one stream"},
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline:
@@ -1054,7 +1100,7 @@ def main():
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip the sweep8192 / small1024 extra keys")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--streams", type=int, default=2,
+    ap.add_argument("--streams", type=int, default=3,
                     help="streams the images of a step alternate over (timed pass)")
     ap.add_argument("--global-ctas-per-sm", type=int, default=1,
                     help="cap on the global kernel's CTAs per SM during the timed pass "
