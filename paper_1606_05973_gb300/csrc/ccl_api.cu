@@ -235,7 +235,7 @@ int32_t enqueue_fused(const ccl_image *imgs, const int32_t *keep, int32_t m, int
             bind_workspace(a, L, dev + o);
             int64_t *t = pre[k].data(), *it = t + (m + 1), *sg = t + 2 * (m + 1);
             t[i + 1] = t[i] + (int64_t)L.nTX * L.nTY;
-            it[i + 1] = it[i] + (int64_t)(L.nTY - 1) * im.W + (int64_t)(L.nTX - 1) * im.H;
+            it[i + 1] = it[i] + edge_item_count(conn, L, im.H, im.W);
             sg[i + 1] = sg[i] + L.nSeg;
         }
         o = align256(o + fused_image_bytes(im.H, im.W, conn));
@@ -730,7 +730,7 @@ int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int
         bind_workspace(a, L[k], dev + loff[k]);
         hd[k] = a;
         tileStart[k + 1] = tileStart[k] + (int64_t)L[k].nTX * L[k].nTY;
-        itemStart[k + 1] = itemStart[k] + (int64_t)(L[k].nTY - 1) * im.W + (int64_t)(L[k].nTX - 1) * im.H;
+        itemStart[k + 1] = itemStart[k] + edge_item_count(conn, L[k], im.H, im.W);
         segStart[k + 1] = segStart[k] + L[k].nSeg;
     }
     e = cudaMemcpyAsync(dev + HDR, host, (size_t)stage_need, cudaMemcpyHostToDevice, s);

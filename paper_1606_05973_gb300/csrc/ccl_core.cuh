@@ -1277,6 +1277,19 @@ struct EdgeItem {
                          // facing two pixels back (the previous pixel's other diagonal)
 };
 
+// Horizontal tile boundaries of binary images are merged from the bit pack in units of
+// HUNIT columns (multi-class images, whose contacts depend on the bytes, keep one item per
+// column).  Vertical boundaries take one item per row.
+constexpr int HUNIT = 8;
+template <class C> CCL_HD int64_t horizontal_items(int nTY, int W)
+{
+    return C::CLS ? (int64_t)(nTY - 1) * W : (int64_t)(nTY - 1) * ((W + HUNIT - 1) / HUNIT);
+}
+template <class C> CCL_HD int64_t edge_items(int nTX, int nTY, int H, int W)
+{
+    return horizontal_items<C>(nTY, W) + (int64_t)(nTX - 1) * H;
+}
+
 // item i < nh: horizontal boundary above band 1 + i / W at column i % W; else vertical
 // boundary left of tile column 1 + k / H at row k % H (k = i - nh)
 template <class C> CCL_HD EdgeItem load_edge_item(const Img &a, int64_t i, int64_t nh)
@@ -1373,6 +1386,80 @@ template <class C> CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it)
     }
 }
 
+// Unit u of the horizontal boundaries (binary images): the boundary above tile row
+// 1 + u / per, columns x0 .. x0 + HUNIT - 1.  Rows A (the last row of the tile row above) and
+// B (the first row of the tile row below) come from the bit pack as windows of 32 columns
+// starting at x0 - 1 (bit j = column x0 - 1 + j).  Every pair of single-row runs, one in A
+// and one in B, that touch is found once, at the column where the later of the two starts,
+// as the tile pass finds them between strips (8: the B run starts where A has a pixel at
+// that column or one to the left, or the A run starts one column right of a B pixel;
+// 4: the B run starts under an A pixel, or the A run starts over a B pixel that does not
+// start a B run).  Each pair is joined through the node ids of its two touching pixels
+// (the tile-edge ids); a pair with the same two ids as the unit's previous one is skipped.
+template <class C> CCL_HD void merge_hunit(const Img &a, int64_t u)
+{
+    const int64_t per = (a.W + HUNIT - 1) / HUNIT;
+    const int ty = 1 + (int)(u / per), x0 = (int)(u % per) * HUNIT;
+    const int64_t WW = (int64_t)a.nTX * C::NW;  // words per bit-pack row
+    const int64_t WP = (int64_t)a.nTX * C::TW;  // ids per tile-edge row
+    const int *top = a.edgeRow + (int64_t)(2 * ty) * WP;
+    const int *above = a.edgeRow + (int64_t)(2 * ty - 1) * WP;
+    auto window = [&](int y) -> uint32_t {
+        const uint32_t *row = a.bitpack + CCL_CHK((int64_t)y * WW, (int64_t)a.H * WW, a.status);
+        if (x0 == 0)
+            return row[0] << 1;  // column -1 is background
+        const int xs = x0 - 1, w = xs >> 5, sh = xs & 31;
+        uint32_t v = row[w] >> sh;
+        if (sh && w + 1 < WW)
+            v |= row[w + 1] << (32 - sh);
+        return v;
+    };
+    const uint32_t A = window(ty * C::TH - 1), B = window(ty * C::TH);
+    const uint32_t Ash = A << 1, Bsh = B << 1;  // bit j: the column to the left
+    const uint32_t sAr = A & ~Ash, sBr = B & ~Bsh;
+    const uint32_t cols = ((1u << HUNIT) - 1u) << 1;  // bits 1..HUNIT: columns x0 .. x0 + HUNIT - 1
+    uint32_t ev1 = ((C::CONN == 8) ? (sBr & (A | Ash)) : (sBr & A)) & cols;
+    uint32_t ev2 = ((C::CONN == 8) ? (sAr & Bsh) : (sAr & B & ~sBr)) & cols & ~ev1;
+    int pe = -1, pb = -1;
+    while (ev1 | ev2) {
+        const uint32_t E = ev1 | ev2;
+        const int j = ctz32(E);
+        const uint32_t m = 1u << j;
+        const bool first = (ev1 & m) != 0u;
+        ev1 &= ~m;
+        ev2 &= ~m;
+        const int x = x0 - 1 + j;
+        int xe = x, xb = x;  // the touching B and A pixels
+        if (C::CONN == 8) {
+            if (first)
+                xb = (A & m) ? x : x - 1;
+            else
+                xe = x - 1;
+        }
+        const int e = top[CCL_CHK((int64_t)xe, WP, a.status)], bb = above[CCL_CHK((int64_t)xb, WP, a.status)];
+#if defined(CCL_DEBUG)
+        if (e < 0 || bb < 0) {
+            flag_status(a.status, ST_BAD_VALUE);
+            continue;
+        }
+#endif
+        if (e == pe && bb == pb)
+            continue;
+        pe = e;
+        pb = bb;
+        rem_unite_g(a.P, a.nP, e, bb, a.status);
+    }
+}
+
+// boundary-merge item i of an image (nh = horizontal_items)
+template <class C> CCL_HD void merge_item(const Img &a, int64_t i, int64_t nh)
+{
+    if (!C::CLS && i < nh)
+        merge_hunit<C>(a, i);
+    else
+        apply_edge_item<C>(a, load_edge_item<C>(a, i, nh));
+}
+
 // ---- global phase: flatten (Algorithm 3) and canonical numbering ------------------------
 // After the boundary merge every component is a tree over global node ids in which a
 // parent always has a smaller id (raster order), and the root is the component's
@@ -1385,10 +1472,6 @@ template <class C> CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it)
 #define CCL_JUMP_HOPS 32
 #endif
 constexpr int JUMP_HOPS = CCL_JUMP_HOPS;
-#ifndef CCL_MERGE_BATCH
-#define CCL_MERGE_BATCH 1
-#endif
-constexpr int MERGE_BATCH = CCL_MERGE_BATCH;
 constexpr int MAX_ROUNDS = 40;
 
 // One round over the nodes of segment `seg`: every node that is not a root moves its
@@ -1605,25 +1688,11 @@ template <class C> CCL_HD void global_body(const Img &a, ScanBuf &sb, int &s_fla
     const int64_t stride = (int64_t)G * GNT;
     CCL_TICK(1, 0);
 
-    // a3: boundary merge (Algorithm 7's boundary loop with Algorithm 8's union), the edge
-    // ids of MERGE_BATCH items loaded before any union
-    constexpr int MB = MERGE_BATCH;
-    const int64_t nh = (int64_t)(a.nTY - 1) * a.W;
+    // a3: boundary merge (Algorithm 7's boundary loop with Algorithm 8's union)
+    const int64_t nh = horizontal_items<C>(a.nTY, a.W);
     const int64_t nv = (int64_t)(a.nTX - 1) * a.H;
-    for (int64_t i0 = (int64_t)b * GNT + tid; i0 < nh + nv; i0 += MB * stride) {
-        EdgeItem it[MB];
-        CCL_UNROLL
-        for (int k = 0; k < MB; k++) {
-            const int64_t i = i0 + k * stride;
-            if (i < nh + nv)
-                it[k] = load_edge_item<C>(a, i, nh);
-            else
-                it[k].e = -1;
-        }
-        CCL_UNROLL
-        for (int k = 0; k < MB; k++)
-            apply_edge_item<C>(a, it[k]);
-    }
+    for (int64_t i = (int64_t)b * GNT + tid; i < nh + nv; i += stride)
+        merge_item<C>(a, i, nh);
     grid_sync(g, (unsigned)G, epoch, a.status, tid);
     CCL_TICK(1, 1);
 
@@ -1817,8 +1886,7 @@ CCL_HD void batch_global_phase(const Batch &B, ScanBufT<NTG> &sb, int &s_flag, i
         if (i >= B.item_start(m + 1) || i < B.item_start(m))
             m = find_img(B.itemStart, n, i);
         const Img &a = B.img(m);
-        const int64_t nh = (int64_t)(a.nTY - 1) * a.W;
-        apply_edge_item<C>(a, load_edge_item<C>(a, i - B.item_start(m), nh));
+        merge_item<C>(a, i - B.item_start(m), horizontal_items<C>(a.nTY, a.W));
     }
     grid_sync(g, (unsigned)G, epoch, B.status, tid);
 

@@ -60,6 +60,8 @@ int tile_policy();
 int resolve_conn(int conn, int64_t H, int64_t W);
 
 Layout main_layout(int H, int W, int conn);
+// boundary-merge items of an image laid out as L under conn (see edge_items in ccl_core.cuh)
+int64_t edge_item_count(int conn, const Layout &L, int H, int W);
 
 // Fill the workspace pointers of `a` (everything but img, labels, K and status) from the
 // base of the image's part of a workspace.

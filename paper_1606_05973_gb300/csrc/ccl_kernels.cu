@@ -91,6 +91,12 @@ int resolve_conn(int conn, int64_t H, int64_t W)
     }
 }
 
+int64_t edge_item_count(int conn, const Layout &L, int H, int W)
+{
+    const int64_t h = (conn & CONN_CLASSES) ? (int64_t)(L.nTY - 1) * W : (int64_t)(L.nTY - 1) * ((W + HUNIT - 1) / HUNIT);
+    return h + (int64_t)(L.nTX - 1) * H;
+}
+
 Layout main_layout(int H, int W, int conn)
 {
     switch (resolve_conn(conn, H, W)) {
@@ -280,7 +286,7 @@ template <class C> static cudaError_t launch_label_t(const Img &a, const Layout 
     const int ntiles = L.nTX * L.nTY;
     CCL_LAUNCH(KID_TILE_LOCAL, launch_tiles(k_tile_local<C>, ntiles, C::NT, sizeof(SmemL<C>), s, a));
     // the global kernel needs enough threads for its largest phase, and every CTA resident
-    const int64_t work = (int64_t)(L.nTY - 1) * a.W + (int64_t)(L.nTX - 1) * a.H;
+    const int64_t work = edge_items<C>(L.nTX, L.nTY, a.H, a.W);
     const int64_t need = ((work > L.nSeg ? work : L.nSeg) + GNT - 1) / GNT;
     const int dev = current_device();
     const int grid = global_grid(need, KernState<C>::global_ctas[dev], dev);

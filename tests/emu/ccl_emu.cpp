@@ -316,7 +316,7 @@ template <class C> struct Emu {
             a.nP = L[i].nP;
             a.nSeg = L[i].nSeg;
             tileStart[i + 1] = tileStart[i] + (int64_t)L[i].nTX * L[i].nTY;
-            itemStart[i + 1] = itemStart[i] + (int64_t)(L[i].nTY - 1) * Ws[i] + (int64_t)(L[i].nTX - 1) * Hs[i];
+            itemStart[i + 1] = itemStart[i] + edge_items<C>(L[i].nTX, L[i].nTY, Hs[i], Ws[i]);
             segStart[i + 1] = segStart[i] + L[i].nSeg;
         }
         Batch B;
@@ -391,7 +391,7 @@ template <class C> struct Emu {
 
         const int ntiles = L.nTX * L.nTY;
         run_tiles<SmemL<C>>(ntiles, [&](SmemL<C> &s, int tile, int t) { tile_local_body<C>(a, s, tile, t); });
-        const int64_t work = (int64_t)(L.nTY - 1) * W + (int64_t)(L.nTX - 1) * H;
+        const int64_t work = edge_items<C>(L.nTX, L.nTY, H, W);
         const int64_t need = ((work > L.nSeg ? work : L.nSeg) + GNT - 1) / GNT;
         const int G = (int)std::max<int64_t>(1, std::min<int64_t>(3, need));
         run_global(a, G);
@@ -462,7 +462,8 @@ template <class CA, class CB> struct EmuFused {
                 else
                     bind<CA>(a, L, (char *)ws[i].data());
                 pre[k][0][i + 1] = pre[k][0][i] + (int64_t)L.nTX * L.nTY;
-                pre[k][1][i + 1] = pre[k][1][i] + (int64_t)(L.nTY - 1) * Ws[i] + (int64_t)(L.nTX - 1) * Hs[i];
+                pre[k][1][i + 1] = pre[k][1][i] + (k ? edge_items<CB>(L.nTX, L.nTY, Hs[i], Ws[i])
+                                                         : edge_items<CA>(L.nTX, L.nTY, Hs[i], Ws[i]));
                 pre[k][2][i + 1] = pre[k][2][i] + L.nSeg;
             }
         }
