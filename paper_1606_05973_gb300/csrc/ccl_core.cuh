@@ -1569,6 +1569,11 @@ template <int N> CCL_HD void scan_step(ScanBufT<N> &s, int tid, int k)
 }
 // inclusive result after ilog2(N) steps lives in buffer ilog2(N) & 1
 template <int N> CCL_HD int scan_incl(const ScanBufT<N> &s, int tid) { return s.v[ilog2(N) & 1][tid]; }
+// Roots before CTA b: every CTA sums the totals of the CTAs before it itself (after the
+// grid barrier that follows the counts), in place of one CTA scanning all totals between
+// two barriers.  Returns that sum to every thread; *all receives the grand total.
+template <int N> CCL_HD int ctas_before(ScanBufT<N> &s, const int *bsum, int b, int G, int tid, int *all);
+
 // the whole scan: every thread of the CTA (N threads) puts x and gets its inclusive sum
 template <int N> CCL_HD int cta_incl_scan(ScanBufT<N> &s, int tid, int x)
 {
@@ -1579,6 +1584,26 @@ template <int N> CCL_HD int cta_incl_scan(ScanBufT<N> &s, int tid, int x)
         cta_sync();
     }
     return scan_incl(s, tid);
+}
+
+template <int N> CCL_HD int ctas_before(ScanBufT<N> &s, const int *bsum, int b, int G, int tid, int *all)
+{
+    int x = 0, y = 0;
+    for (int i = tid; i < G; i += N) {
+        const int v = ld_g(&bsum[i]);
+        if (i < b)
+            x += v;
+        y += v;
+    }
+    // two sums in one scan: the totals are < 2^31 in all, so pack neither; run twice
+    const int before = cta_incl_scan(s, tid, x);
+    const int sb = s.v[ilog2(N) & 1][N - 1];
+    (void)before;
+    cta_sync();
+    cta_incl_scan(s, tid, y);
+    *all = s.v[ilog2(N) & 1][N - 1];
+    cta_sync();
+    return sb;
 }
 
 // Grid-wide state of the global kernel, in the workspace header.  k_tile_local zeroes it
@@ -1717,32 +1742,13 @@ template <class C> CCL_HD void global_body(const Img &a, ScanBuf &sb, int &s_fla
         st_g(&a.bsum[b], incl);
     grid_sync(g, (unsigned)G, epoch, a.status, tid);
     CCL_TICK(1, 2);
-    if (b == 0) {
-        const int per = (G + GNT - 1) / GNT;
-        const int lo = tid * per < G ? tid * per : G;
-        const int hi = lo + per < G ? lo + per : G;
-        int acc = 0;
-        for (int i = lo; i < hi; i++)
-            acc += ld_g(&a.bsum[i]);
-        scan_put(sb, tid, acc);
-        cta_sync();
-        for (int k = 0; k < GNT_LOG; k++) {
-            scan_step(sb, tid, k);
-            cta_sync();
-        }
-        int run = scan_incl(sb, tid) - acc;
-        for (int i = lo; i < hi; i++) {
-            const int t = ld_g(&a.bsum[i]);
-            st_g(&a.bsum[i], run);
-            run += t;
-        }
-        if (tid == GNT - 1)
-            *a.K = scan_incl(sb, tid);
-    }
-    grid_sync(g, (unsigned)G, epoch, a.status, tid);
+    int total = 0;
+    const int before = ctas_before(sb, a.bsum, b, G, tid, &total);
+    if (b == G - 1 && tid == 0)
+        *a.K = total;
     CCL_TICK(1, 3);
     // root k in raster order receives label k+1 (stored as -(k+1))
-    label_roots<C>(a, s0, s1, ld_g(&a.bsum[b]) + incl - c);
+    label_roots<C>(a, s0, s1, before + incl - c);
 
     // further jump rounds while some node has not reached its root
     for (int r = 0; r < MAX_ROUNDS - 1; r++) {
@@ -1910,27 +1916,13 @@ CCL_HD void batch_global_phase(const Batch &B, ScanBufT<NTG> &sb, int &s_flag, i
     if (tid == NTG - 1)
         st_g(&B.bsum[b], incl);
     grid_sync(g, (unsigned)G, epoch, B.status, tid);
-    if (b == 0) {
-        const int per = (G + NTG - 1) / NTG;
-        const int lo = tid * per < G ? tid * per : G;
-        const int hi = lo + per < G ? lo + per : G;
-        int acc = 0;
-        for (int i = lo; i < hi; i++)
-            acc += ld_g(&B.bsum[i]);
-        const int tot = cta_incl_scan(sb, tid, acc);
-        int run = tot - acc;
-        for (int i = lo; i < hi; i++) {
-            const int t = ld_g(&B.bsum[i]);
-            st_g(&B.bsum[i], run);
-            run += t;
-        }
-        if (tid == NTG - 1)
-            st_g(&B.imgBase[n], tot);
-    }
-    grid_sync(g, (unsigned)G, epoch, B.status, tid);
+    int total = 0;
+    const int before = ctas_before(sb, B.bsum, b, G, tid, &total);
+    if (b == G - 1 && tid == 0)
+        st_g(&B.imgBase[n], total);
     // roots get -(batch rank + 1); the thread that meets an image's first segment records
     // the ranks before it
-    int run = ld_g(&B.bsum[b]) + incl - c;
+    int run = before + incl - c;
     m = m0;
     for (int64_t seg = s0; seg < s1; seg++) {
         while (seg >= B.seg_start(m + 1))
