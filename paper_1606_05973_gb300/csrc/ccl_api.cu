@@ -444,7 +444,7 @@ int32_t ccl_workspace_bytes(int32_t H, int32_t W, int64_t *bytes)
         return CCL_OK;
     }
     int64_t mx = 0;
-    for (int conn : {8 | CONN_WIDE, 8 | CONN_NARROW, 4, 8 | CONN_CLASSES, 4 | CONN_CLASSES}) {
+    for (int conn : {8 | CONN_WIDE, 8 | CONN_NARROW, 8 | CONN_BIG, 4, 8 | CONN_CLASSES, 4 | CONN_CLASSES}) {
         const int64_t b = main_layout(H, W, conn).bytes;
         mx = b > mx ? b : mx;
     }
@@ -626,6 +626,12 @@ namespace ccl {
 // ones leave SMs idle, so under the automatic policy the batch's total pixel count decides,
 // with the single-image threshold: a batch that fills the GPU takes wide tiles however
 // small its images.
+int batch_conn_px(int64_t px)
+{
+    const int c = resolve_conn(8, px, 1);
+    return c == (8 | CONN_BIG) ? (8 | CONN_WIDE) : c;
+}
+
 int batch_conn(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn)
 {
     if (conn != 8)
@@ -633,7 +639,8 @@ int batch_conn(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn)
     int64_t all = 0;
     for (int32_t k = 0; k < m; k++)
         all += (int64_t)imgs[keep[k]].H * imgs[keep[k]].W;
-    return resolve_conn(conn, all, 1);
+    const int c = resolve_conn(conn, all, 1);
+    return c == (8 | CONN_BIG) ? (8 | CONN_WIDE) : c;  // the big tiles are for single images
 }
 
 int64_t batch_fixed_bytes(int32_t m)
@@ -891,7 +898,7 @@ int32_t ccl_release(void)
 
 int32_t ccl_set_tile_policy(int32_t policy)
 {
-    if (policy < 0 || policy > 2)
+    if (policy < 0 || policy > 3)
         return CCL_ERR_INVALID_ARGUMENT;
     set_tile_policy(policy);
     return CCL_OK;

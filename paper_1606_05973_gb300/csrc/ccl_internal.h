@@ -43,16 +43,26 @@ using MainCfgC4 = Cfg<CCL_TILE_H / 2, CCL_TILE_W, CCL_TILE_NT, 4, true>;
 // 8-connectivity on narrow tiles (64 x 128 by default): smaller images run faster on them
 // (tile-shape sweep, paper_1606_05973_gb300/tile_sweep.py)
 using NarrowCfg = Cfg<CCL_TILE_H, CCL_TILE_W / 2, CCL_TILE_NT, 8>;
+// 8-connectivity on tiles twice as wide, with twice the threads (64 x 512, 512 threads):
+// large single images run faster on them (half the vertical tile boundaries and global
+// nodes along rows, the same occupancy of 2048 threads per SM)
+using BigCfg = Cfg<CCL_TILE_H, CCL_TILE_W * 2, CCL_TILE_NT * 2, 8>;
 // Inside the library a connectivity value may carry this bit: multi-class labelling.
 constexpr int CONN_CLASSES = 0x100;
 // ... and, for 8-connectivity, one of these: the tile shape chosen (resolve_conn)
 constexpr int CONN_NARROW = 0x200;  // NarrowCfg
 constexpr int CONN_WIDE = 0x400;    // MainCfg
-// Images of at most this many pixels take narrow tiles under the automatic policy.
+constexpr int CONN_BIG = 0x800;     // BigCfg
+// Under the automatic policy single images of at most NARROW_MAX_PX pixels take narrow
+// tiles, those above BIG_MIN_PX the big ones, the rest MainCfg.
 constexpr int64_t NARROW_MAX_PX = (int64_t)3072 * 3072;
+#ifndef CCL_BIG_MIN_PX
+#define CCL_BIG_MIN_PX ((int64_t)12288 * 12288)
+#endif
+constexpr int64_t BIG_MIN_PX = CCL_BIG_MIN_PX;
 
 // Tile policy (ccl_set_tile_policy): 0 = by image size, 1 = always MainCfg, 2 = always
-// NarrowCfg.  Read at every call.
+// NarrowCfg, 3 = always BigCfg (single images; batches take MainCfg).  Read at every call.
 void set_tile_policy(int p);
 int tile_policy();
 // `conn` with the tile shape an image of H x W takes (8-connectivity only; other modes and
@@ -139,8 +149,10 @@ int32_t check_args(const void *img, int32_t H, int32_t W, int64_t pitch, int32_t
 int64_t batch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn);
 // the part of batch_bytes that does not depend on the images (header, descriptors, prefixes)
 int64_t batch_fixed_bytes(int32_t m);
-// the tile shape a batch of images takes (8-connectivity: by its total pixel count)
+// the tile shape a batch of images takes (8-connectivity: by its total pixel count; never
+// the big tiles, which are for single images)
 int batch_conn(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn);
+int batch_conn_px(int64_t px);
 int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
                       Workspace *w, cudaStream_t s);
 // the persistent launch: workspace bytes (fixed part and one image's region) and enqueue

@@ -87,7 +87,8 @@ int resolve_conn(int conn, int64_t H, int64_t W)
     switch (tile_policy()) {
     case 1: return 8 | CONN_WIDE;
     case 2: return 8 | CONN_NARROW;
-    default: return 8 | (H * W <= NARROW_MAX_PX ? CONN_NARROW : CONN_WIDE);
+    case 3: return 8 | CONN_BIG;
+    default: return 8 | (H * W <= NARROW_MAX_PX ? CONN_NARROW : (H * W > BIG_MIN_PX ? CONN_BIG : CONN_WIDE));
     }
 }
 
@@ -101,6 +102,7 @@ Layout main_layout(int H, int W, int conn)
 {
     switch (resolve_conn(conn, H, W)) {
     case 8 | CONN_NARROW: return plan_layout<NarrowCfg>(H, W);
+    case 8 | CONN_BIG: return plan_layout<BigCfg>(H, W);
     case 4: return plan_layout<MainCfg4>(H, W);
     case 8 | CONN_CLASSES: return plan_layout<MainCfgC8>(H, W);
     case 4 | CONN_CLASSES: return plan_layout<MainCfgC4>(H, W);
@@ -238,6 +240,8 @@ cudaError_t kernels_init()
         if (r == cudaSuccess)
             r = init_cfg<NarrowCfg>(dev);
         if (r == cudaSuccess)
+            r = init_cfg<BigCfg>(dev);
+        if (r == cudaSuccess)
             r = init_cfg<MainCfg4>(dev);
         if (r == cudaSuccess)
             r = init_cfg<MainCfgC8>(dev);
@@ -320,6 +324,7 @@ cudaError_t launch_label(const Img &a, const Layout &L, int conn, cudaStream_t s
 {
     switch (resolve_conn(conn, a.H, a.W)) {
     case 8 | CONN_NARROW: return launch_label_t<NarrowCfg>(a, L, s);
+    case 8 | CONN_BIG: return launch_label_t<BigCfg>(a, L, s);
     case 4: return launch_label_t<MainCfg4>(a, L, s);
     case 8 | CONN_CLASSES: return launch_label_t<MainCfgC8>(a, L, s);
     case 4 | CONN_CLASSES: return launch_label_t<MainCfgC4>(a, L, s);
@@ -331,6 +336,7 @@ cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t s
 {
     switch (conn) {  // a batch's shape is chosen once for all its images (batch_conn)
     case 8 | CONN_NARROW: return launch_batch_t<NarrowCfg>(B, tiles, items, segs, s);
+    case 8 | CONN_BIG: return launch_batch_t<BigCfg>(B, tiles, items, segs, s);
     case 4: return launch_batch_t<MainCfg4>(B, tiles, items, segs, s);
     case 8 | CONN_CLASSES: return launch_batch_t<MainCfgC8>(B, tiles, items, segs, s);
     case 4 | CONN_CLASSES: return launch_batch_t<MainCfgC4>(B, tiles, items, segs, s);
@@ -380,7 +386,7 @@ int fused_threads() { return MainCfg::NT; }
 int fused_resident_ctas(int conn)
 {
     const int dev = current_device();
-    switch (conn & ~(CONN_NARROW | CONN_WIDE)) {
+    switch (conn & ~(CONN_NARROW | CONN_WIDE | CONN_BIG)) {
     case 4: return FusedState<MainCfg4, MainCfg4>::resident[dev];
     case 8 | CONN_CLASSES: return FusedState<MainCfgC8, MainCfgC8>::resident[dev];
     case 4 | CONN_CLASSES: return FusedState<MainCfgC4, MainCfgC4>::resident[dev];
@@ -400,7 +406,7 @@ template <class CA, class CB> static cudaError_t launch_fused_t(const FusedArgs 
 cudaError_t launch_fused(const FusedArgs &f, int conn, int grid, cudaStream_t s)
 {
     static_assert(NarrowCfg::NT == MainCfg::NT, "the two binary shapes share one persistent kernel");
-    switch (conn & ~(CONN_NARROW | CONN_WIDE)) {
+    switch (conn & ~(CONN_NARROW | CONN_WIDE | CONN_BIG)) {
     case 4: return launch_fused_t<MainCfg4, MainCfg4>(f, grid, s);
     case 8 | CONN_CLASSES: return launch_fused_t<MainCfgC8, MainCfgC8>(f, grid, s);
     case 4 | CONN_CLASSES: return launch_fused_t<MainCfgC4, MainCfgC4>(f, grid, s);

@@ -189,7 +189,7 @@ bool try_launch_locked(ccl_server *s, Lane &L)
         } else if (conn == 8) {
             add_n = main_layout(r.img.H, r.img.W, 8 | CONN_NARROW).bytes;
             add_w = main_layout(r.img.H, r.img.W, 8 | CONN_WIDE).bytes;
-            const bool narrow = resolve_conn(8, px + r.pixels, 1) == (8 | CONN_NARROW);
+            const bool narrow = batch_conn_px(px + r.pixels) == (8 | CONN_NARROW);
             need = batch_fixed_bytes(m) + (narrow ? sum_n + add_n : sum_w + add_w);
         } else {
             add_n = add_w = main_layout(r.img.H, r.img.W, conn).bytes;

@@ -556,7 +556,7 @@ uint32_t emu_gt_mask16(const uint8_t *src, int32_t thr)
 // 3 = 128x256 (256); 4 = 64x512 (256).  4-connectivity: 5 = 32x256 (256); 6 = 4x32 (32);
 // 7 = 8x64 (64); 8 = 2x32 (32).  Multi-class, 8: 9 = 4x32, 10 = 8x64, 11 = 32x256;
 // multi-class, 4: 12 = 4x32, 13 = 32x256.  8-connectivity, other tile shapes of the
-// tile-shape sweep: 14 = 32x256 (256), 15 = 64x128 (256)
+// tile-shape sweep: 14 = 32x256 (256), 15 = 64x128 (256); 16 = 64x512 (512), the big tiles
 int64_t emu_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t *labels, uint64_t seed,
                   int32_t shape, int32_t *status)
 {
@@ -577,6 +577,7 @@ int64_t emu_label(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32
     case 12: return Emu<Cfg<4, 32, 32, 4, true>>(seed).run(img, H, W, pitch, labels, status);
     case 14: return Emu<Cfg<32, 256, 256>>(seed).run(img, H, W, pitch, labels, status);
     case 15: return Emu<Cfg<64, 128, 256>>(seed).run(img, H, W, pitch, labels, status);
+    case 16: return Emu<Cfg<64, 512, 512>>(seed).run(img, H, W, pitch, labels, status);
     default: return Emu<Cfg<32, 256, 256, 4, true>>(seed).run(img, H, W, pitch, labels, status);
     }
 }

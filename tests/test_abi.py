@@ -71,7 +71,7 @@ def test_argument_checks_need_no_gpu(lib):
         assert lib.ccl_label_threshold(p, 4, 4, 4, 8, t, p, ctypes.byref(k), None) == 1
     assert lib.ccl_label_threshold(p, 0, 9, 9, 8, 127, p, ctypes.byref(k), None) == 0 and k.value == 0
     # process-wide options: checked on the host, no GPU call (restored to the defaults)
-    for bad in (-1, 3):
+    for bad in (-1, 4):
         assert lib.ccl_set_tile_policy(bad) == 1
     for ok in (1, 2, 0):
         assert lib.ccl_set_tile_policy(ok) == 0

@@ -54,8 +54,12 @@ def test_emulated_path_tile_variants_quick():
     e = emu.Emu(emu.build(sanitize=False))
     img = synth.bernoulli(300, 700, 0.5, 1)
     ref, rk = oracle.cclremsp(img)
-    for shape in (0, 1, 2):
+    for shape in (0, 1, 2, 16):
         lab, k, st = e.label(img, seed=shape, shape=shape)
+        assert st == 0 and k == rk and np.array_equal(lab, ref)
+    for im in (synth.serpentine(130, 1100), synth.bernoulli(200, 1500, 0.6, 3)):  # big tiles, ragged
+        ref, rk = oracle.cclremsp(im)
+        lab, k, st = e.label(im, seed=5, shape=16)
         assert st == 0 and k == rk and np.array_equal(lab, ref)
 
 

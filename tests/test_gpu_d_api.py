@@ -200,23 +200,25 @@ def test_global_ctas_per_sm_cap_and_two_streams(ccl):
 
 
 def test_tile_policies_give_identical_labels(ccl):
-    """The 8-connected path on 64 x 256 tiles (policy 1), 64 x 128 tiles (policy 2) and the
-    size rule (policy 0): single images on both sides of the size threshold, ragged sizes
-    and a padded pitch, and a batch, all equal to the oracle under every policy."""
+    """The 8-connected path on 64 x 256 tiles (policy 1), 64 x 128 tiles (policy 2), 64 x 512
+    tiles of 512 threads (policy 3) and the size rule (policy 0): single images on both sides
+    of the size thresholds, ragged sizes and a padded pitch, and a batch, all equal to the
+    oracle under every policy."""
     import torch
 
     lib = ccl.lib()
-    assert lib.ccl_set_tile_policy(3) == 1 and lib.ccl_set_tile_policy(-1) == 1
+    assert lib.ccl_set_tile_policy(4) == 1 and lib.ccl_set_tile_policy(-1) == 1
     singles = [synth.bernoulli(h, w, p, 60 + i) for i, (h, w, p) in
                enumerate(((1, 1, 1.0), (63, 129, 0.5), (700, 1000, 0.3), (1500, 2333, 0.6),
-                          (3100, 3100, 0.45), (2000, 5000, 0.9)))]
+                          (3100, 3100, 0.45), (2000, 5000, 0.9), (1100, 12400, 0.55)))]
     singles.append(synth.serpentine(777, 3333))
+    singles.append(synth.serpentine(12300, 12300))  # above the size rule's big-tile threshold
     specs = synth.batch_specs(n=24, seed=101, lo=16, hi=1500)
     batch = [synth.make_batch_image(s) for s in specs]
     refs = [oracle.cclremsp(im) for im in singles]
     brefs = [oracle.cclremsp(im) for im in batch]
     try:
-        for policy in (1, 2, 0):
+        for policy in (1, 2, 3, 0):
             assert lib.ccl_set_tile_policy(policy) == 0
             for im, (ref, rk) in zip(singles, refs):
                 lab, k = ccl.label(torch.from_numpy(im).cuda())
