@@ -57,7 +57,7 @@ constexpr int CONN_BIG = 0x800;     // BigCfg
 // tiles, those above BIG_MIN_PX the big ones, the rest MainCfg.
 constexpr int64_t NARROW_MAX_PX = (int64_t)3072 * 3072;
 #ifndef CCL_BIG_MIN_PX
-#define CCL_BIG_MIN_PX ((int64_t)12288 * 12288)
+#define CCL_BIG_MIN_PX ((int64_t)6144 * 6144)
 #endif
 constexpr int64_t BIG_MIN_PX = CCL_BIG_MIN_PX;
 
