@@ -983,9 +983,10 @@ template <class C> struct Tile {
             // that joins the same two runs as the lane's previous one is not listed.
             uint32_t last = 0xFFFFFFFFu;
             int head = 0, tail = 0;  // the warp's list: entries [head, tail) not yet taken
+            bool unlisted = true;    // some lane has events not yet listed (warp-uniform)
             int rx = -1, ry = -1;
             for (int it = 0;; it++) {
-                if (head == tail && warp_ballot((ev1 | ev2) != 0u)) {
+                if (head == tail && unlisted) {
                     // refill: every lane's next REFILL events per round, the round's first
                     // events of all lanes before its second ones
                     warp_sync();  // the old entries have all been read
@@ -1019,7 +1020,8 @@ template <class C> struct Tile {
                                 jl[tail + popc32(mk & lt)] = key[q];
                             tail += popc32(mk);
                         }
-                        if (tail > JCAP - 32 * REFILL || !warp_ballot((ev1 | ev2) != 0u))
+                        unlisted = warp_ballot((ev1 | ev2) != 0u) != 0u;
+                        if (tail > JCAP - 32 * REFILL || !unlisted)
                             break;
                     }
                     warp_sync();  // the new entries are visible to every lane
@@ -1036,7 +1038,9 @@ template <class C> struct Tile {
                     }
                 }
                 head += imin(popc32(fr), avail);
-                if (!warp_ballot(rx >= 0) && head == tail && !warp_ballot((ev1 | ev2) != 0u))
+                // a lane is busy if it was already or has just taken an entry: with no lane
+                // busy, nothing listed and nothing left to list, the warp is done
+                if (fr == 0xFFFFFFFFu && avail == 0 && !unlisted)
                     break;
                 if (it == SMEM_LOOP_CAP) {
                     flag_status(a.status, ST_LOOP_CAP);
