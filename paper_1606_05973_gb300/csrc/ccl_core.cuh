@@ -1344,7 +1344,13 @@ template <class C> CCL_HD EdgeItem load_edge_item(const Img &a, int64_t i, int64
     return it;
 }
 
-template <class C> CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it)
+// the union of two global node ids in the global parent table
+struct UniteGlobal {
+    const Img &a;
+    CCL_HD void operator()(int x, int y) const { rem_unite_g(a.P, a.nP, x, y, a.status); }
+};
+
+template <class C, class U> CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it, const U &unite)
 {
     if (it.e < 0)
         return;
@@ -1360,15 +1366,15 @@ template <class C> CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it)
         };
         const bool jb = it.b >= 0 && it.cb == it.ce;
         if (jb && (C::CONN == 8 ? fresh(it.b) : !(prev && it.b == it.aa)))
-            rem_unite_g(a.P, a.nP, it.e, it.b, a.status);
+            unite(it.e, it.b);
         if (C::CONN == 8) {
             const bool ja = it.aa >= 0 && it.ca == it.ce && !(jb && it.aa == it.b);
             if (ja && fresh(it.aa))
-                rem_unite_g(a.P, a.nP, it.e, it.aa, a.status);
+                unite(it.e, it.aa);
             const bool jc = it.c >= 0 && it.cc == it.ce && !(jb && it.c == it.b) &&
                             !(it.aa >= 0 && it.ca == it.ce && it.c == it.aa);
             if (jc && fresh(it.c))
-                rem_unite_g(a.P, a.nP, it.e, it.c, a.status);
+                unite(it.e, it.c);
         }
         return;
     }
@@ -1376,17 +1382,17 @@ template <class C> CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it)
         // 4-connectivity: only the facing pixel; the previous edge pixel (same node) has
         // already joined through its own facing pixel if that one is an object pixel
         if (it.b >= 0 && !(it.same_prev && it.aa >= 0))
-            rem_unite_g(a.P, a.nP, it.e, it.b, a.status);
+            unite(it.e, it.b);
         return;
     }
     if (it.b >= 0) {
         if (!it.same_prev)
-            rem_unite_g(a.P, a.nP, it.e, it.b, a.status);
+            unite(it.e, it.b);
     } else {
         if (it.aa >= 0 && !it.same_prev)
-            rem_unite_g(a.P, a.nP, it.e, it.aa, a.status);
+            unite(it.e, it.aa);
         if (it.c >= 0)
-            rem_unite_g(a.P, a.nP, it.e, it.c, a.status);
+            unite(it.e, it.c);
     }
 }
 
@@ -1400,7 +1406,7 @@ template <class C> CCL_HD void apply_edge_item(const Img &a, const EdgeItem &it)
 // 4: the B run starts under an A pixel, or the A run starts over a B pixel that does not
 // start a B run).  Each pair is joined through the node ids of its two touching pixels
 // (the tile-edge ids); a pair with the same two ids as the unit's previous one is skipped.
-template <class C> CCL_HD void merge_hunit(const Img &a, int64_t u)
+template <class C, class U> CCL_HD void merge_hunit(const Img &a, int64_t u, const U &unite)
 {
     const int64_t per = (a.W + HUNIT - 1) / HUNIT;
     const int ty = 1 + (int)(u / per), x0 = (int)(u % per) * HUNIT;
@@ -1451,17 +1457,21 @@ template <class C> CCL_HD void merge_hunit(const Img &a, int64_t u)
             continue;
         pe = e;
         pb = bb;
-        rem_unite_g(a.P, a.nP, e, bb, a.status);
+        unite(e, bb);
     }
 }
 
-// boundary-merge item i of an image (nh = horizontal_items)
-template <class C> CCL_HD void merge_item(const Img &a, int64_t i, int64_t nh)
+// boundary-merge item i of an image (nh = horizontal_items), joined by `unite`
+template <class C, class U> CCL_HD void merge_item(const Img &a, int64_t i, int64_t nh, const U &unite)
 {
     if (!C::CLS && i < nh)
-        merge_hunit<C>(a, i);
+        merge_hunit<C>(a, i, unite);
     else
-        apply_edge_item<C>(a, load_edge_item<C>(a, i, nh));
+        apply_edge_item<C>(a, load_edge_item<C>(a, i, nh), unite);
+}
+template <class C> CCL_HD void merge_item(const Img &a, int64_t i, int64_t nh)
+{
+    merge_item<C>(a, i, nh, UniteGlobal{a});
 }
 
 // ---- global phase: flatten (Algorithm 3) and canonical numbering ------------------------
@@ -1772,6 +1782,148 @@ template <class C> CCL_HD void global_body(const Img &a, ScanBuf &sb, int &s_fla
         grid_sync(g, (unsigned)G, epoch, a.status, tid);
         if (r == MAX_ROUNDS - 2 && tid == 0 && b == 0 && ld_g(&g->round_more[r + 1]))
             flag_status(a.status, ST_LOOP_CAP);
+    }
+#if defined(CCL_PHASE_TIMING)
+    cta_sync();
+    CCL_TICK(1, 4);
+#endif
+}
+
+// ---- small images: the global phases in one CTA, in shared memory ----------------------
+// When an image's segments and nodes fit, one CTA of GNT threads runs rows a3-a5 on a copy
+// of the node table in shared memory.  Nodes are numbered densely in raster order (the
+// prefix over segments of their root counts); the boundary merge joins them with Rem's
+// union on shared words; one find per node flattens; a scan numbers the roots in that
+// order (raster order of first pixels, as in global_body); and every node's entry of the
+// global table receives -(label).  Each dependent step costs a shared-memory access
+// instead of an L2 one, and there is no grid barrier.  An image whose nodes do not fit
+// runs global_body in the same CTA (G = 1) on the global table.
+constexpr int SMALL_SEG_CAP = 16384;   // segments (image rows x tile columns)
+constexpr int SMALL_NODE_CAP = 32768;  // nodes (local components)
+
+struct SmallSmem {
+    int pre[SMALL_SEG_CAP + 1];  // nodes before each segment
+    int D[SMALL_NODE_CAP];       // dense parents, then -(label)
+    ScanBuf sb;
+    int flag, n;
+};
+
+// Rem's union with splicing on dense ids in shared memory (as rem_unite_g)
+CCL_HD void rem_unite_s(int *D, int x, int y, int *st)
+{
+    int rx = x, ry = y;
+    for (int it = 0; it < SMEM_LOOP_CAP; it++) {
+        const int px = ld_s(&D[rx]), py = ld_s(&D[ry]);
+        if (px == py)
+            return;
+        if (px > py) {
+            if (at_cas(&D[rx], px, py) != px)
+                continue;
+            if (px == rx)
+                return;
+            rx = px;
+        } else {
+            if (at_cas(&D[ry], py, px) != py)
+                continue;
+            if (py == ry)
+                return;
+            ry = py;
+        }
+    }
+    flag_status(st, ST_LOOP_CAP);
+}
+
+template <class C> struct UniteShared {
+    const Img &a;
+    int *D;
+    const int *pre;
+    CCL_HD int dense(int gid) const
+    {
+        return CCL_CHK(pre[CCL_CHK(gid / C::ROWCAP, (int)a.nSeg, a.status)] + gid % C::ROWCAP, SMALL_NODE_CAP, a.status);
+    }
+    CCL_HD void operator()(int x, int y) const { rem_unite_s(D, dense(x), dense(y), a.status); }
+};
+
+template <class C> CCL_HD void small_global_body(const Img &a, SmallSmem &sm, int tid)
+{
+    CCL_TICK(1, 0);
+    const int nSeg = (int)a.nSeg;
+    if (nSeg > SMALL_SEG_CAP) {
+        global_body<C>(a, sm.sb, sm.flag, 0, 1, tid);
+        return;
+    }
+    // nodes before each segment
+    const int per = (nSeg + GNT - 1) / GNT;
+    const int s0 = imin(tid * per, nSeg), s1 = imin(s0 + per, nSeg);
+    int c = 0;
+    for (int sg = s0; sg < s1; sg++)
+        c += a.nseg[sg];
+    const int incl = cta_incl_scan(sm.sb, tid, c);
+    int run = incl - c;
+    for (int sg = s0; sg < s1; sg++) {
+        sm.pre[sg] = run;
+        run += a.nseg[sg];
+    }
+    if (tid == GNT - 1) {
+        sm.pre[nSeg] = incl;
+        sm.n = incl;
+    }
+    cta_sync();
+    const int N = sm.n;
+    if (N > SMALL_NODE_CAP) {  // the same decision in every thread
+        global_body<C>(a, sm.sb, sm.flag, 0, 1, tid);
+        return;
+    }
+    for (int k = tid; k < N; k += GNT)
+        sm.D[k] = k;
+    cta_sync();
+    // a3: boundary merge
+    const int64_t nh = horizontal_items<C>(a.nTY, a.W);
+    const int64_t nv = (int64_t)(a.nTX - 1) * a.H;
+    const UniteShared<C> unite{a, sm.D, sm.pre};
+    for (int64_t i = tid; i < nh + nv; i += GNT)
+        merge_item<C>(a, i, nh, unite);
+    cta_sync();
+    CCL_TICK(1, 1);
+    // a4: every node to its root (a node read on the way may already hold its root)
+    for (int k = tid; k < N; k += GNT) {
+        int r = k;
+        for (int it = 0; it < SMEM_LOOP_CAP; it++) {
+            const int p = ld_s(&sm.D[r]);
+            if (p == r)
+                break;
+            r = p;
+        }
+        sm.D[k] = r;
+    }
+    cta_sync();
+    CCL_TICK(1, 2);
+    // a5: roots in dense (raster) order get labels 1..K; then every node takes its root's
+    const int per2 = (N + GNT - 1) / GNT;
+    const int k0 = imin(tid * per2, N), k1 = imin(k0 + per2, N);
+    int nr = 0;
+    for (int k = k0; k < k1; k++)
+        nr += sm.D[k] == k ? 1 : 0;
+    const int incl2 = cta_incl_scan(sm.sb, tid, nr);
+    int lab = incl2 - nr;
+    for (int k = k0; k < k1; k++)
+        if (sm.D[k] == k)
+            sm.D[k] = -(++lab);
+    if (tid == GNT - 1)
+        *a.K = incl2;
+    cta_sync();
+    for (int k = tid; k < N; k += GNT) {
+        const int r = sm.D[k];
+        if (r >= 0)
+            sm.D[k] = sm.D[CCL_CHK(r, N, a.status)];
+    }
+    cta_sync();
+    CCL_TICK(1, 3);
+    // every node's entry of the global table, segment by segment
+    for (int sg = tid; sg < nSeg; sg += GNT) {
+        const int b0 = sm.pre[sg], n = sm.pre[sg + 1] - b0;
+        for (int j = 0; j < n; j++)
+            a.P[CCL_CHK((int64_t)sg * C::ROWCAP + j, a.nP, a.status)] = sm.D[b0 + j];
     }
 #if defined(CCL_PHASE_TIMING)
     cta_sync();

@@ -60,6 +60,12 @@ constexpr int64_t NARROW_MAX_PX = (int64_t)3072 * 3072;
 #define CCL_BIG_MIN_PX ((int64_t)6144 * 6144)
 #endif
 constexpr int64_t BIG_MIN_PX = CCL_BIG_MIN_PX;
+// Single images of at most this many pixels (and at most SMALL_SEG_CAP segments) run the
+// global phases in one CTA in shared memory (k_global_small).
+#ifndef CCL_SMALL_MAX_PX
+#define CCL_SMALL_MAX_PX ((int64_t)1536 * 1536)
+#endif
+constexpr int64_t SMALL_MAX_PX = CCL_SMALL_MAX_PX;
 
 // Tile policy (ccl_set_tile_policy): 0 = by image size, 1 = always MainCfg, 2 = always
 // NarrowCfg, 3 = always BigCfg (single images; batches take MainCfg).  Read at every call.

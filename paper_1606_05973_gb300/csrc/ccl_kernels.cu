@@ -41,6 +41,13 @@ template <class C> __global__ void __launch_bounds__(GNT, CCL_GLOBAL_MIN_CTAS) k
     global_body<C>(a, sb, s_flag, blockIdx.x, gridDim.x, threadIdx.x);
 }
 
+// the global phases of a small image in one CTA, in shared memory (small_global_body)
+template <class C> __global__ void __launch_bounds__(GNT, 1) k_global_small(Img a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    small_global_body<C>(a, *reinterpret_cast<SmallSmem *>(smem_raw), threadIdx.x);
+}
+
 template <class C> __global__ void __launch_bounds__(C::NT, 2048 / C::NT) k_final(Img a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -175,6 +182,9 @@ template <class C> static cudaError_t init_cfg(int dev)
     if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_final<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmemF<C>));
     if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_global_small<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(SmallSmem));
+    if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_tile_local_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)sizeof(SmemL<C>));
     if (err == cudaSuccess)
@@ -290,6 +300,12 @@ template <class C> static cudaError_t launch_label_t(const Img &a, const Layout 
     const int ntiles = L.nTX * L.nTY;
     CCL_LAUNCH(KID_TILE_LOCAL, launch_tiles(k_tile_local<C>, ntiles, C::NT, sizeof(SmemL<C>), s, a));
     // the global kernel needs enough threads for its largest phase, and every CTA resident
+    if (L.nSeg <= SMALL_SEG_CAP && (int64_t)a.H * a.W <= SMALL_MAX_PX) {
+        // small image: the global phases in one CTA in shared memory, no grid barrier
+        CCL_LAUNCH(KID_GLOBAL, launch_tiles(k_global_small<C>, 1, GNT, sizeof(SmallSmem), s, a));
+        CCL_LAUNCH(KID_FINAL, launch_tiles(k_final<C>, ntiles, C::NT, sizeof(SmemF<C>), s, a));
+        return cudaSuccess;
+    }
     const int64_t work = edge_items<C>(L.nTX, L.nTY, a.H, a.W);
     const int64_t need = ((work > L.nSeg ? work : L.nSeg) + GNT - 1) / GNT;
     const int dev = current_device();

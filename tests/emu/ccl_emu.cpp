@@ -394,7 +394,17 @@ template <class C> struct Emu {
         const int64_t work = edge_items<C>(L.nTX, L.nTY, H, W);
         const int64_t need = ((work > L.nSeg ? work : L.nSeg) + GNT - 1) / GNT;
         const int G = (int)std::max<int64_t>(1, std::min<int64_t>(3, need));
-        run_global(a, G);
+        if ((seed & 1) == 0 && L.nSeg <= SMALL_SEG_CAP) {
+            // the small-image form: one CTA, the node table in shared memory
+            auto sm = std::make_unique<SmallSmem>();
+            memset(sm.get(), 0x7F, sizeof(SmallSmem));
+            Sched sch(1, GNT, rng(), [&](int, int t) { small_global_body<C>(a, *sm, t); });
+            g_sched = &sch;
+            sch.run();
+            g_sched = nullptr;
+        } else {
+            run_global(a, G);
+        }
         run_tiles<SmemF<C>>(ntiles, [&](SmemF<C> &s, int tile, int t) { final_body<C>(a, s, tile, t); });
         return *a.K;
     }
