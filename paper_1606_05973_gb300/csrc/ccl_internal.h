@@ -63,7 +63,7 @@ constexpr int64_t BIG_MIN_PX = CCL_BIG_MIN_PX;
 // Single images of at most this many pixels (and at most SMALL_SEG_CAP segments) run the
 // global phases in one CTA in shared memory (k_global_small).
 #ifndef CCL_SMALL_MAX_PX
-#define CCL_SMALL_MAX_PX ((int64_t)1536 * 1536)
+#define CCL_SMALL_MAX_PX ((int64_t)512 * 512)
 #endif
 constexpr int64_t SMALL_MAX_PX = CCL_SMALL_MAX_PX;
 
