@@ -354,13 +354,15 @@ int32_t ccl_set_tuning(const ccl_tune_row *rows, int32_t n, int32_t density_lo_p
 /*
  * ccl_set_tile_policy - the tile shape of the 8-connected path (the partitions that
  * Algorithm 7 labels independently before its boundary merge).  policy 0 (the default)
- * chooses by size: images of at most 3072 x 3072 pixels take 64 x 128 tiles, larger ones
- * 64 x 256 (an offline sweep of tile shapes over sizes and contents:
- * paper_1606_05973_gb300/tile_sweep.py): narrow tiles pay while wide ones would leave SMs
- * idle.  A batch takes one shape for all its images, by the same rule on its total pixel
- * count (a batch of 4096 images up to 2048 x 2048 takes wide tiles).  1 = always
- * 64 x 256, 2 = always 64 x 128 (for tests and tuning).  Labels are identical under every
- * policy.  Under the persistent launch (ccl_set_launch_mode 0) policy 0 takes the tuning
+ * chooses by size: images of at most 3072 x 3072 pixels take 64 x 128 tiles, those above
+ * 6144 x 6144 take 64 x 512 tiles of 512 threads, the others 64 x 256 (offline sweeps of
+ * tile shapes over sizes and contents, paper_1606_05973_gb300/tile_sweep.py): narrow tiles
+ * pay while wide ones would leave SMs idle, and on large images the wide ones halve the
+ * vertical tile boundaries.  A batch takes one shape for all its images by the same rule
+ * on its total pixel count, never the 64 x 512 one (a batch of 4096 images up to
+ * 2048 x 2048 takes 64 x 256 tiles).  1 = always 64 x 256, 2 = always 64 x 128, 3 = always
+ * 64 x 512 for single images (64 x 256 for batches): for tests and tuning.  Labels are
+ * identical under every policy.  Under the persistent launch, policy 0 takes the tuning
  * table's shape and 1 / 2 force one shape as here.  Process-wide; applies to calls made
  * after it.  CCL_ERR_INVALID_ARGUMENT for other values.
  */
