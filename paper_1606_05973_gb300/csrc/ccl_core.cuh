@@ -1289,20 +1289,9 @@ template <class C> CCL_HD int64_t horizontal_items(int nTY, int W)
 {
     return C::CLS ? (int64_t)(nTY - 1) * W : (int64_t)(nTY - 1) * ((W + HUNIT - 1) / HUNIT);
 }
-// vertical boundaries of binary images: items of VUNIT rows (the edge ids of a unit's rows
-// are loaded together); multi-class images keep one item per row
-constexpr int VUNIT = 4;
-// rows of a vertical unit under tile shape C: VUNIT, or the tile height of shorter tiles, so
-// that a unit never crosses a tile row
-template <class C> constexpr int vunit_rows() { return C::TH < VUNIT ? C::TH : VUNIT; }
-template <class C> CCL_HD int64_t vertical_items(int nTX, int H)
-{
-    static_assert(C::TH % vunit_rows<C>() == 0, "vertical units tile the tile rows");
-    return C::CLS ? (int64_t)(nTX - 1) * H : (int64_t)(nTX - 1) * ((H + vunit_rows<C>() - 1) / vunit_rows<C>());
-}
 template <class C> CCL_HD int64_t edge_items(int nTX, int nTY, int H, int W)
 {
-    return horizontal_items<C>(nTY, W) + vertical_items<C>(nTX, H);
+    return horizontal_items<C>(nTY, W) + (int64_t)(nTX - 1) * H;
 }
 
 // item i < nh: horizontal boundary above band 1 + i / W at column i % W; else vertical
@@ -1472,50 +1461,13 @@ template <class C, class U> CCL_HD void merge_hunit(const Img &a, int64_t u, con
     }
 }
 
-// Unit k of the vertical boundaries (binary images): the boundary left of tile column
-// 1 + k / per, rows y0 .. y0 + VUNIT - 1 (within one tile row).  The edge ids of those rows
-// and of the rows next to them are loaded first, then each row is joined as in
-// apply_edge_item (the facing pixel, else the two diagonal ones; a pair already joined
-// through the row above is skipped).
-template <class C, class U> CCL_HD void merge_vunit(const Img &a, int64_t k, const U &unite)
-{
-    constexpr int VU = vunit_rows<C>();
-    const int64_t per = (a.H + VU - 1) / VU;
-    const int tx = 1 + (int)(k / per), y0 = (int)(k % per) * VU;
-    const int64_t HP = (int64_t)a.nTY * C::TH;
-    const int *left = a.edgeCol + (int64_t)(2 * tx - 1) * HP;
-    const int *me = a.edgeCol + (int64_t)(2 * tx) * HP;
-    const int yb0 = (y0 / C::TH) * C::TH, yb1 = imin(yb0 + C::TH, a.H);
-    int L[VU + 2], M[VU + 1];  // L[j]: left of row y0 - 1 + j; M[j]: right of it (-1 outside)
-    CCL_UNROLL
-    for (int j = 0; j < VU + 2; j++) {
-        const int y = y0 - 1 + j;
-        const bool in = y >= yb0 && y < yb1;
-        L[j] = in ? left[y] : -1;
-        if (j < VU + 1)
-            M[j] = in ? me[y] : -1;
-    }
-    CCL_UNROLL
-    for (int r = 0; r < VU; r++) {
-        EdgeItem it;
-        it.e = M[r + 1];
-        it.b = L[r + 1];
-        it.aa = L[r];
-        it.c = L[r + 2];
-        it.same_prev = it.e >= 0 && M[r] == it.e;
-        apply_edge_item<C>(a, it, unite);
-    }
-}
-
 // boundary-merge item i of an image (nh = horizontal_items), joined by `unite`
 template <class C, class U> CCL_HD void merge_item(const Img &a, int64_t i, int64_t nh, const U &unite)
 {
-    if (C::CLS)
-        apply_edge_item<C>(a, load_edge_item<C>(a, i, nh), unite);
-    else if (i < nh)
+    if (!C::CLS && i < nh)
         merge_hunit<C>(a, i, unite);
     else
-        merge_vunit<C>(a, i - nh, unite);
+        apply_edge_item<C>(a, load_edge_item<C>(a, i, nh), unite);
 }
 template <class C> CCL_HD void merge_item(const Img &a, int64_t i, int64_t nh)
 {
@@ -1777,7 +1729,7 @@ template <class C> CCL_HD void global_body(const Img &a, ScanBuf &sb, int &s_fla
 
     // a3: boundary merge (Algorithm 7's boundary loop with Algorithm 8's union)
     const int64_t nh = horizontal_items<C>(a.nTY, a.W);
-    const int64_t nv = vertical_items<C>(a.nTX, a.H);
+    const int64_t nv = (int64_t)(a.nTX - 1) * a.H;
     for (int64_t i = (int64_t)b * GNT + tid; i < nh + nv; i += stride)
         merge_item<C>(a, i, nh);
     grid_sync(g, (unsigned)G, epoch, a.status, tid);
@@ -1927,7 +1879,7 @@ template <class C> CCL_HD void small_global_body(const Img &a, SmallSmem &sm, in
     cta_sync();
     // a3: boundary merge
     const int64_t nh = horizontal_items<C>(a.nTY, a.W);
-    const int64_t nv = vertical_items<C>(a.nTX, a.H);
+    const int64_t nv = (int64_t)(a.nTX - 1) * a.H;
     const UniteShared<C> unite{a, sm.D, sm.pre};
     for (int64_t i = tid; i < nh + nv; i += GNT)
         merge_item<C>(a, i, nh, unite);

@@ -99,15 +99,10 @@ int resolve_conn(int conn, int64_t H, int64_t W)
     }
 }
 
-// every compiled tile shape is at least VUNIT rows high, so its vertical units are VUNIT rows
-static_assert(vunit_rows<MainCfg>() == VUNIT && vunit_rows<NarrowCfg>() == VUNIT && vunit_rows<BigCfg>() == VUNIT &&
-                  vunit_rows<MainCfg4>() == VUNIT,
-              "vertical unit rows");
 int64_t edge_item_count(int conn, const Layout &L, int H, int W)
 {
-    if (conn & CONN_CLASSES)
-        return (int64_t)(L.nTY - 1) * W + (int64_t)(L.nTX - 1) * H;
-    return (int64_t)(L.nTY - 1) * ((W + HUNIT - 1) / HUNIT) + (int64_t)(L.nTX - 1) * ((H + VUNIT - 1) / VUNIT);
+    const int64_t h = (conn & CONN_CLASSES) ? (int64_t)(L.nTY - 1) * W : (int64_t)(L.nTY - 1) * ((W + HUNIT - 1) / HUNIT);
+    return h + (int64_t)(L.nTX - 1) * H;
 }
 
 Layout main_layout(int H, int W, int conn)
