@@ -487,7 +487,9 @@ template <class C> struct SmemL : SmemRuns<C>, SmemCls<C> {
     uint32_t jspare[JSPARE];
 };
 template <class C> struct SmemF : SmemRuns<C> {
-    int lab[C::RMAX];                // final label of every strip run
+    // final label of strip run v at lab[v + 1]; the entry below run 0 and the three above
+    // the last run pad the reads of write_labels (read, never used)
+    int lab[C::RMAX + 4];
 };
 
 constexpr uint32_t PAR_HI = 0xFFFF0000u;
@@ -1232,38 +1234,67 @@ template <class C> struct Tile {
                         }
 #endif
                     }
-                    s.lab[v0 + k0 + k] = prev_lab;
+                    s.lab[v0 + k0 + k + 1] = prev_lab;
                 }
                 prev_code = code[3 < n - k0 - 1 ? 3 : n - k0 - 1];
             }
         }
     }
 
+    // One item: four columns x..x+3 of one strip, i.e. 4 pixels of each of its RPS rows.
+    // With S the strip's run starts in word w and o = x % 32, the run covering column x + k
+    // (if any) is i0 + c_k, where i0 counts the runs starting at or before x (rpre and a
+    // popcount) and c_k the starts in columns x+1..x+k.  Runs of one strip are separated by
+    // background (binary images), so c_k <= 2 and three label reads serve the item's 4 or 8
+    // pixels; multi-class runs may touch (c_k <= k, four reads).
     CCL_HD static void write_labels(const Img &a, const SF &s, int ty, int tx, int tid)
     {
         const int y0 = ty * C::TH, x0 = tx * C::TW;
         constexpr int G = C::TW / 4;
-        for (int q = tid; q < C::TH * G; q += C::NT) {
-            const int r = q / G, x = (q % G) * 4;
-            const int y = y0 + r, gx = x0 + x;
-            if (y >= a.H || gx >= a.W)
-                continue;
-            const int st = r / C::RPS, w = x >> 5;
-            const uint32_t row = s.bits[r][w];
-            const uint32_t starts = s.starts[st][w];
-            const int base = st * C::RC + s.rpre[st][w] - 1;
-            int v[4];
-            for (int k = 0; k < 4; k++) {
-                const int b = (x & 31) + k;
-                v[k] = ((row >> b) & 1u) ? s.lab[CCL_CHK(base + popc32(starts & mask_le(b)), C::RMAX, a.status)] : 0;
-            }
-            int *dst = a.labels + (int64_t)y * a.W + gx;
-            if (a.vec_out && gx + 4 <= a.W) {
-                store4(dst, v);
+        const bool full = a.vec_out && y0 + C::TH <= a.H && x0 + C::TW <= a.W;
+        for (int q = tid; q < C::NS * G; q += C::NT) {
+            const int st = q / G, x = (q % G) * 4;
+            const int w = x >> 5, o = x & 31;
+            const uint32_t S = s.starts[st][w];
+            const uint32_t Sx = S >> o;
+            // lab index (labels are stored one entry up) of the run at or before column x
+            const int i0 = CCL_CHK(st * C::RC + s.rpre[st][w] + popc32(S & mask_le(o)), C::RMAX + 1, a.status);
+            const int c1 = (int)((Sx >> 1) & 1u);
+            const int c2 = c1 + (int)((Sx >> 2) & 1u);
+            const int c3 = c2 + (int)((Sx >> 3) & 1u);
+            const int L0 = s.lab[i0], L1 = s.lab[i0 + 1], L2 = s.lab[i0 + 2];
+            int cand[4];
+            cand[0] = L0;
+            cand[1] = c1 ? L1 : L0;
+            if constexpr (C::CLS) {
+                const int L3 = s.lab[i0 + 3];
+                cand[2] = c2 == 0 ? L0 : (c2 == 1 ? L1 : L2);
+                cand[3] = c3 == 0 ? L0 : (c3 == 1 ? L1 : (c3 == 2 ? L2 : L3));
             } else {
+                cand[2] = c2 ? L1 : L0;
+                cand[3] = c3 == 0 ? L0 : (c3 == 1 ? L1 : L2);
+            }
+            CCL_UNROLL
+            for (int rr = 0; rr < C::RPS; rr++) {
+                const int r = C::RPS * st + rr;
+                const int y = y0 + r, gx = x0 + x;
+                const uint32_t R = s.bits[r][w] >> o;
+                int v[4];
+                CCL_UNROLL
                 for (int k = 0; k < 4; k++)
-                    if (gx + k < a.W)
-                        dst[k] = v[k];
+                    v[k] = ((R >> k) & 1u) ? cand[k] : 0;
+                int *dst = a.labels + (int64_t)y * a.W + gx;
+                if (full) {
+                    store4(dst, v);
+                } else if (y < a.H && gx < a.W) {
+                    if (a.vec_out && gx + 4 <= a.W) {
+                        store4(dst, v);
+                    } else {
+                        for (int k = 0; k < 4; k++)
+                            if (gx + k < a.W)
+                                dst[k] = v[k];
+                    }
+                }
             }
         }
     }
