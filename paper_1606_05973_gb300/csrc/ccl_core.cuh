@@ -61,6 +61,14 @@ int emu_lane();
 #ifndef CCL_REFILL
 #define CCL_REFILL 2
 #endif
+// L2 prefetch of the successor tile's inputs in the tile pass and in the final pass (1: its
+// bit pack, 2: also its run codes), for launches that set Img::pf_dist
+#ifndef CCL_PF_TILE
+#define CCL_PF_TILE 1
+#endif
+#ifndef CCL_PF_FINAL
+#define CCL_PF_FINAL 1
+#endif
 
 namespace ccl {
 
@@ -285,6 +293,18 @@ CCL_HD int ld_g(const int *a)
     return __atomic_load_n(a, __ATOMIC_RELAXED);
 #endif
 }
+// A hint to bring the 128-byte line holding p into L2 ahead of its use; callers pass only
+// addresses inside their buffers.  No effect on results.  The host emulation reads the
+// byte instead, so that an address sanitizer checks the address.
+CCL_HD void prefetch_l2(const void *p)
+{
+#if defined(__CUDA_ARCH__)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+#else
+    const volatile char c = *static_cast<const volatile char *>(p);
+    (void)c;
+#endif
+}
 // four consecutive ints from a 16-byte aligned address (one strong vector load; each
 // element is read atomically, the four together are not)
 CCL_HD void ld_g4(const int *a, int v[4])
@@ -419,6 +439,8 @@ struct Img {
     int label_base;      // subtracted from the global rank labels (batch: ranks before this image)
     int *status;         // device status word (ST_* bits)
     int64_t nP, nSeg, nRunInfo;  // array sizes (for checked builds)
+    int pf_dist;         // > 0: a tile-pass or final-pass CTA prefetches into L2 the inputs of
+                         // tile (its tile + pf_dist), the tile the CTA replacing it will take
 };
 
 // Workspace layout for one image (byte offsets, each 256-byte aligned).
@@ -596,6 +618,41 @@ template <class C> struct Tile {
                 half[q] = (uint16_t)m;  // little-endian: half 2w is the low half of word w
             }
         }
+    }
+
+    // L2 prefetch of the image rows of tile t (nothing when pf_dist is 0 or t is past the
+    // last tile)
+    CCL_HD static void prefetch_image(const Img &a, int t, int tid)
+    {
+        if (a.pf_dist <= 0 || t >= a.nTX * a.nTY)
+            return;
+        const int y0 = (t / a.nTX) * C::TH, x0 = (t % a.nTX) * C::TW;
+        constexpr int LPR = (C::TW + 127) / 128;  // 128-byte lines per tile row
+        for (int q = tid; q < C::TH * LPR; q += C::NT) {
+            const int y = y0 + q / LPR, x = x0 + 128 * (q % LPR);
+            if (y < a.H && x < a.W)
+                prefetch_l2(a.img + (int64_t)y * a.pitch + x);
+        }
+    }
+
+    // L2 prefetch of the bit-pack rows of tile t (and, CCL_PF_FINAL 2, its run codes)
+    CCL_HD static void prefetch_final(const Img &a, int t, int tid)
+    {
+        if (a.pf_dist <= 0 || t >= a.nTX * a.nTY)
+            return;
+        const int y0 = (t / a.nTX) * C::TH, tx = t % a.nTX;
+        const int64_t WW = (int64_t)a.nTX * C::NW;
+        constexpr int LPR = (C::NW * 4 + 127) / 128;
+        for (int q = tid; q < C::TH * LPR; q += C::NT) {
+            const int y = y0 + q / LPR;
+            if (y < a.H)
+                prefetch_l2(a.bitpack + (int64_t)y * WW + tx * C::NW + 32 * (q % LPR));
+        }
+#if CCL_PF_FINAL >= 2
+        const uint16_t *ri = a.runinfo + (int64_t)t * C::RMAX;
+        for (int q = tid; q < C::RMAX / 64; q += C::NT)
+            prefetch_l2(ri + 64 * q);
+#endif
     }
 
     template <bool NZ, int PER>
@@ -1721,6 +1778,9 @@ template <class C> CCL_HD void tile_local_body(const Img &a, SmemL<C> &s, int ti
             g[i] = 0u;
     }
     CCL_TICK(0, 0);
+#if CCL_PF_TILE
+    T::prefetch_image(a, tile + a.pf_dist, tid);
+#endif
     T::load_image(a, s, ty, tx, tid);
     cta_sync();
     CCL_TICK(0, 1);
@@ -1968,6 +2028,9 @@ template <class C> CCL_HD void final_body(const Img &a, SmemF<C> &s, int tile, i
     using T = Tile<C>;
     const int ty = tile / a.nTX, tx = tile % a.nTX;
     CCL_TICK(2, 0);
+#if CCL_PF_FINAL
+    T::prefetch_final(a, tile + a.pf_dist, tid);
+#endif
     T::load_bitpack(a, s, ty, tx, tid);
     cta_sync();
     CCL_TICK(2, 1);

@@ -66,6 +66,12 @@ constexpr int64_t BIG_MIN_PX = CCL_BIG_MIN_PX;
 #define CCL_SMALL_MAX_PX ((int64_t)512 * 512)
 #endif
 constexpr int64_t SMALL_MAX_PX = CCL_SMALL_MAX_PX;
+// Single images of at least this many pixels prefetch successor tiles (Img::pf_dist): on
+// GB300 +3% per 21568^2 image, -0.7% per 8192^2 image.
+#ifndef CCL_PF_MIN_PX
+#define CCL_PF_MIN_PX ((int64_t)16384 * 16384)
+#endif
+constexpr int64_t PF_MIN_PX = CCL_PF_MIN_PX;
 
 // Tile policy (ccl_set_tile_policy): 0 = by image size, 1 = always MainCfg, 2 = always
 // NarrowCfg, 3 = always BigCfg (single images; batches take MainCfg).  Read at every call.

@@ -164,10 +164,11 @@ static int global_grid(int64_t need, int fit, int dev)
 }
 
 template <class C> struct KernState {
-    static int global_ctas[MAX_DEVICES], global_batch_ctas[MAX_DEVICES];
+    static int global_ctas[MAX_DEVICES], global_batch_ctas[MAX_DEVICES], tile_ctas[MAX_DEVICES];
 };
 template <class C> int KernState<C>::global_ctas[MAX_DEVICES] = {};
 template <class C> int KernState<C>::global_batch_ctas[MAX_DEVICES] = {};
+template <class C> int KernState<C>::tile_ctas[MAX_DEVICES] = {};
 
 template <class C> static cudaError_t init_cfg(int dev)
 {
@@ -190,7 +191,11 @@ template <class C> static cudaError_t init_cfg(int dev)
     if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_final_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)sizeof(SmemF<C>));
-    int occ = 0, occb = 0;
+    int occ = 0, occb = 0, occt = 0;
+    if (err == cudaSuccess)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occt, k_tile_local<C>, C::NT, sizeof(SmemL<C>));
+    if (err == cudaSuccess)
+        KernState<C>::tile_ctas[dev] = g_num_sms[dev] * occt;
     if (err == cudaSuccess)
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_global<C>, GNT, 0);
     if (err == cudaSuccess)
@@ -295,9 +300,15 @@ template <class K> static cudaError_t launch_tiles_b(K kern, int ntiles, int nt,
     return cudaSuccess;
 }
 
-template <class C> static cudaError_t launch_label_t(const Img &a, const Layout &L, cudaStream_t s)
+template <class C> static cudaError_t launch_label_t(const Img &a_in, const Layout &L, cudaStream_t s)
 {
     const int ntiles = L.nTX * L.nTY;
+    // large single images: each tile-pass and final-pass CTA prefetches the inputs of the
+    // tile that the CTA replacing it will take (tiles are dispatched in order, as many at a
+    // time as are resident)
+    Img a = a_in;
+    if ((int64_t)a.H * a.W >= PF_MIN_PX)
+        a.pf_dist = KernState<C>::tile_ctas[current_device()];
     CCL_LAUNCH(KID_TILE_LOCAL, launch_tiles(k_tile_local<C>, ntiles, C::NT, sizeof(SmemL<C>), s, a));
     // the global kernel needs enough threads for its largest phase, and every CTA resident
     if (L.nSeg <= SMALL_SEG_CAP && (int64_t)a.H * a.W <= SMALL_MAX_PX) {

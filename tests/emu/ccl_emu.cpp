@@ -388,6 +388,7 @@ template <class C> struct Emu {
         a.bsum = (int *)(b + L.off_bsum);
         a.nP = L.nP;
         a.nSeg = L.nSeg;
+        a.pf_dist = (int)(seed % 4);  // successor-tile prefetch distance (0: none)
 
         const int ntiles = L.nTX * L.nTY;
         run_tiles<SmemL<C>>(ntiles, [&](SmemL<C> &s, int tile, int t) { tile_local_body<C>(a, s, tile, t); });
