@@ -162,11 +162,20 @@ typedef struct {
  * and, for the persistent launch, a tile shape per density class: when the shapes differ,
  * a probe at the start of the launch (the object fraction of 64 samples of 16 bytes per
  * image) picks the class.
+ * A batch of two or more images whose smallest image has at least the table's
+ * streams_min_px pixels (ccl_set_streams_min_px) takes a third form: every image is
+ * labelled as by ccl_label_async (three kernels, the single-image tile shape, the global
+ * kernel at one CTA per SM) on one of three streams the library creates for `stream`
+ * (created on the first such call, kept until ccl_release), which wait for the work
+ * enqueued on `stream` before the call, and which `stream` then waits for.  Large images
+ * gain nothing from one launch per kernel over the batch, but one image's tile pass
+ * overlaps another's global pass.  Device status bits of every image go to `stream`'s
+ * status word (ccl_device_status(stream)).
  *   imgs               HOST array of n descriptors (device pointers inside)
  *   num_components_dev DEVICE int32[n] or NULL; entry i receives K of image i
  * Asynchronous and capturable in a CUDA graph once the stream's workspace is large enough
  * (make one uncaptured call of the same or a larger batch first); results are identical
- * to labelling each image alone.  ccl_set_launch_mode forces either form.
+ * to labelling each image alone.  ccl_set_launch_mode forces any of the forms.
  */
 int32_t ccl_label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity,
                         int32_t *num_components_dev, ccl_stream_t stream);
@@ -313,12 +322,24 @@ int32_t ccl_set_global_ctas_per_sm(int32_t n);
  * decides: a batch takes the persistent single launch (see ccl_label_batch) in the size
  * classes where the sweep measured it faster, else three kernels (tile pass, cooperative
  * global pass, final pass); a single image takes the persistent launch up to the table's
- * single-image size (on GB300 the sweep found three kernels faster at every size).
- * 1: always three kernels.  2: always the persistent launch.  Labels are identical in every
- * mode.  Process-wide; applies to calls made after it.  CCL_ERR_INVALID_ARGUMENT for other
- * values.
+ * single-image size (on GB300 the sweep found three kernels faster at every size), and a
+ * batch whose images all have at least streams_min_px pixels is fanned out over streams.
+ * 1: always three kernels.  2: always the persistent launch.  3: batches of two or more
+ * images always fanned out over streams (single images and the server's batches as in
+ * mode 0).  Labels are identical in every mode.  Process-wide; applies to calls made after
+ * it.  CCL_ERR_INVALID_ARGUMENT for other values.
  */
 int32_t ccl_set_launch_mode(int32_t mode);
+
+/*
+ * ccl_set_streams_min_px - under launch mode 0, batches of two or more images whose
+ * smallest image has at least px pixels are fanned out over streams (see ccl_label_batch);
+ * px < 0: never.  Replaces the tuning table's value until the next ccl_set_tuning call.
+ * The continuous-batching server never fans out (its admission sizes each batch's
+ * workspace for the other two forms).  Process-wide; not while labelling calls are in
+ * flight.  Returns CCL_OK.
+ */
+int32_t ccl_set_streams_min_px(int64_t px);
 
 /*
  * ccl_set_persistent_ctas_per_sm - CTAs per SM of the persistent launch's grid (256 threads
@@ -336,9 +357,9 @@ int32_t ccl_set_persistent_ctas_per_sm(int32_t n);
  * 1: 64 x 256); classes split at density_lo_permille and density_hi_permille of object
  * pixels; probe_samples 16-byte samples per image for the density probe; batches of a row
  * with persistent != 0 take the persistent launch; single images up to
- * single_persistent_max_px pixels take it.  n = 0 restores the built-in table.  Not to be
- * called while labelling calls are in flight.  CCL_ERR_INVALID_ARGUMENT for a malformed
- * table.
+ * single_persistent_max_px pixels take it.  n = 0 restores the built-in table (and its
+ * streams_min_px); n > 0 keeps the streams_min_px in use.  Not to be called while labelling
+ * calls are in flight.  CCL_ERR_INVALID_ARGUMENT for a malformed table.
  */
 typedef struct {
     int64_t max_px;

@@ -94,6 +94,7 @@ _SIGS = {
     "ccl_set_global_ctas_per_sm": ([_I32], _I32),
     "ccl_set_tile_policy": ([_I32], _I32),
     "ccl_set_launch_mode": ([_I32], _I32),
+    "ccl_set_streams_min_px": ([_I64], _I32),
     "ccl_set_persistent_ctas_per_sm": ([_I32], _I32),
     "ccl_set_tuning": ([_P, _I32, _I32, _I32, _I32, _I64], _I32),
     "ccl_profile_enable": ([_I32], _I32),

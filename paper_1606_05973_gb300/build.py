@@ -65,7 +65,8 @@ def tuning_source(path: str = TUNING) -> str:
         "static const TuneRow kTuneRows[] = {", *rows, "};",
         f"static const int kTuneDensLo = {lo}, kTuneDensHi = {hi};",
         f"static const int kTuneProbeSamples = {int(t['probe_samples'])};",
-        f"static const int64_t kTuneSingleFusedMaxPx = {int(t['single_fused_max_px'])}LL;", ""])
+        f"static const int64_t kTuneSingleFusedMaxPx = {int(t['single_fused_max_px'])}LL;",
+        f"static const int64_t kTuneStreamsMinPx = {int(t.get('streams_min_px', -1))}LL;", ""])
 
 
 def write_tuning_include() -> str:

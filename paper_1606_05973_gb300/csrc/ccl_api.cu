@@ -116,7 +116,8 @@ int32_t check_args(const void *img, int32_t H, int32_t W, int64_t pitch, int32_t
 // Enqueue the path for one image whose K goes to k_dev (device) and whose status bits go
 // to the workspace header.  `layout_base` is the workspace area for the per-image arrays.
 int32_t enqueue_one(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t conn, int32_t thr,
-                    int32_t *labels, int32_t *k_dev, Workspace *w, char *layout_base, cudaStream_t s)
+                    int32_t *labels, int32_t *k_dev, Workspace *w, char *layout_base, cudaStream_t s,
+                    const LaunchOpts &o = LaunchOpts())
 {
     cudaError_t e = kernels_init();
     if (e != cudaSuccess)
@@ -133,10 +134,10 @@ int32_t enqueue_one(const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int
     a.labels = labels;
     a.vec_out = ((reinterpret_cast<uintptr_t>(labels) & 15) == 0) && (W % 4 == 0);
     a.K = k_dev;
-    a.status = reinterpret_cast<int *>(static_cast<char *>(w->dev) + 4);
+    a.status = o.status ? o.status : reinterpret_cast<int *>(static_cast<char *>(w->dev) + 4);
     a.gsync = reinterpret_cast<GridSync *>(static_cast<char *>(w->dev) + 16);
     bind_workspace(a, L, layout_base);
-    return map_cuda(launch_label(a, L, conn, s));
+    return map_cuda(launch_label(a, L, conn, s, o.global_per_sm));
 }
 
 // ---- persistent single-launch path ---------------------------------------------------------
@@ -351,10 +352,10 @@ SinglePlan plan_single(int32_t H, int32_t W, int conn)
 }
 
 int32_t enqueue_single(const SinglePlan &P, const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t thr,
-                       int32_t *labels, int32_t *k_dev, Workspace *w, cudaStream_t s)
+                       int32_t *labels, int32_t *k_dev, Workspace *w, cudaStream_t s, const LaunchOpts &o)
 {
     if (!P.fused)
-        return enqueue_one(img, H, W, pitch, P.conn, thr, labels, k_dev, w, static_cast<char *>(w->dev) + HDR, s);
+        return enqueue_one(img, H, W, pitch, P.conn, thr, labels, k_dev, w, static_cast<char *>(w->dev) + HDR, s, o);
     ccl_image im;
     im.img = img;
     im.H = H;
@@ -774,17 +775,148 @@ bool batch_persistent(const ccl_image *imgs, const int32_t *keep, int32_t m)
     return tune_row(px).persistent != 0;
 }
 
-int64_t launch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn)
+static int64_t smallest_px(const ccl_image *imgs, const int32_t *keep, int32_t m)
 {
-    return batch_persistent(imgs, keep, m) ? fused_bytes(imgs, keep, m, conn) : batch_bytes(imgs, keep, m, conn);
+    int64_t lo = INT64_MAX;
+    for (int32_t k = 0; k < m; k++)
+        lo = std::min(lo, (int64_t)imgs[keep[k]].H * imgs[keep[k]].W);
+    return lo;
+}
+
+int batch_form(const ccl_image *imgs, const int32_t *keep, int32_t m, bool allow_streams)
+{
+    if (allow_streams && m >= 2) {
+        if (launch_mode() == 3)
+            return FORM_STREAMS;
+        const int64_t min_px = tuning().streams_min_px;
+        if (launch_mode() == 0 && min_px >= 0 && smallest_px(imgs, keep, m) >= min_px)
+            return FORM_STREAMS;
+    }
+    return batch_persistent(imgs, keep, m) ? FORM_PERSISTENT : FORM_THREE;
+}
+
+int64_t launch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, bool allow_streams)
+{
+    switch (batch_form(imgs, keep, m, allow_streams)) {
+    case FORM_STREAMS: return HDR;  // the status word; the images use the fan-out streams' workspaces
+    case FORM_PERSISTENT: return fused_bytes(imgs, keep, m, conn);
+    default: return batch_bytes(imgs, keep, m, conn);
+    }
 }
 
 int32_t enqueue_launch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
-                       Workspace *w, cudaStream_t s)
+                       Workspace *w, cudaStream_t s, bool allow_streams)
 {
-    if (batch_persistent(imgs, keep, m))
-        return enqueue_fused(imgs, keep, m, conn, thr, k_dev, w, s);
-    return enqueue_batch(imgs, keep, m, conn, thr, k_dev, w, s);
+    switch (batch_form(imgs, keep, m, allow_streams)) {
+    case FORM_STREAMS: return enqueue_streams(imgs, keep, m, conn, thr, k_dev, w, s);
+    case FORM_PERSISTENT: return enqueue_fused(imgs, keep, m, conn, thr, k_dev, w, s);
+    default: return enqueue_batch(imgs, keep, m, conn, thr, k_dev, w, s);
+    }
+}
+
+// ---- batches of large images, fanned out over streams -------------------------------------
+// Large images gain nothing from one launch per kernel over the batch (each kernel fills the
+// GPU on its own), but overlap when labelled on several streams: one image's tile pass
+// (bound by instruction issue) beside another's global pass (bound by latency, one CTA per
+// SM, which leaves half of each SM to the tile pass).  The library streams of a caller
+// stream are created on first use and kept until ccl_release.
+struct Fanout {
+    cudaStream_t st[FAN_STREAMS] = {};
+    cudaEvent_t fork = nullptr, join[FAN_STREAMS] = {};
+};
+std::map<std::pair<int, cudaStream_t>, Fanout> g_fan;  // guarded by g_ws_mu
+
+static void destroy_fanout(Fanout &f)
+{
+    for (int j = 0; j < FAN_STREAMS; j++) {
+        if (f.join[j])
+            cudaEventDestroy(f.join[j]);
+        if (f.st[j])
+            cudaStreamDestroy(f.st[j]);
+    }
+    if (f.fork)
+        cudaEventDestroy(f.fork);
+    f = Fanout();
+}
+
+static int32_t get_fanout(cudaStream_t s, Fanout *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return map_cuda(e);
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    auto it = g_fan.find({dev, s});
+    if (it == g_fan.end()) {
+        Fanout f;
+        e = cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming);
+        for (int j = 0; j < FAN_STREAMS && e == cudaSuccess; j++) {
+            e = cudaStreamCreateWithFlags(&f.st[j], cudaStreamNonBlocking);
+            if (e == cudaSuccess)
+                e = cudaEventCreateWithFlags(&f.join[j], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            destroy_fanout(f);
+            return map_cuda(e);
+        }
+        it = g_fan.emplace(std::make_pair(dev, s), f).first;
+    }
+    *out = it->second;
+    return CCL_OK;
+}
+
+int32_t enqueue_streams(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
+                        Workspace *w, cudaStream_t s)
+{
+    cudaError_t e = kernels_init();
+    if (e != cudaSuccess)
+        return map_cuda(e);
+    Fanout f;
+    int32_t rc = get_fanout(s, &f);
+    if (rc != CCL_OK)
+        return rc;
+    // three kernels per image with the single-image tile shape; every stream's workspace
+    // sized once for the largest of its images
+    std::vector<SinglePlan> P((size_t)m);
+    int64_t need[FAN_STREAMS] = {};
+    for (int32_t k = 0; k < m; k++) {
+        const ccl_image &im = imgs[keep[k]];
+        P[k].fused = false;
+        P[k].conn = resolve_conn(conn, im.H, im.W);
+        P[k].bytes = HDR + main_layout(im.H, im.W, P[k].conn).bytes;
+        need[k % FAN_STREAMS] = std::max(need[k % FAN_STREAMS], P[k].bytes);
+    }
+    const int used = std::min<int32_t>(m, FAN_STREAMS);
+    Workspace *ws[FAN_STREAMS] = {};
+    for (int j = 0; j < used; j++) {
+        rc = get_workspace(f.st[j], need[j], &ws[j]);
+        if (rc != CCL_OK)
+            return rc;
+    }
+    e = cudaEventRecord(f.fork, s);
+    for (int j = 0; j < used && e == cudaSuccess; j++)
+        e = cudaStreamWaitEvent(f.st[j], f.fork, 0);
+    if (e != cudaSuccess)
+        return map_cuda(e);
+    LaunchOpts o;
+    o.status = reinterpret_cast<int *>(static_cast<char *>(w->dev) + 4);
+    o.global_per_sm = 1;
+    for (int32_t k = 0; k < m && rc == CCL_OK; k++) {
+        const ccl_image &im = imgs[keep[k]];
+        const int j = k % FAN_STREAMS;
+        int32_t *kd = k_dev ? k_dev + keep[k] : static_cast<int32_t *>(ws[j]->dev);  // else the K slot
+        rc = enqueue_single(P[k], im.img, im.H, im.W, im.pitch_bytes, thr, im.labels, kd, ws[j], f.st[j], o);
+    }
+    // the caller's stream waits for every library stream (also after a failed enqueue, so
+    // that nothing is left running unordered)
+    for (int j = 0; j < used; j++) {
+        e = cudaEventRecord(f.join[j], f.st[j]);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(s, f.join[j], 0);
+        if (e != cudaSuccess && rc == CCL_OK)
+            rc = map_cuda(e);
+    }
+    return rc;
 }
 
 }  // namespace ccl
@@ -824,10 +956,10 @@ int32_t label_batch(const ccl_image *imgs, int32_t n, int32_t connectivity, int3
     if (m == 0)
         return CCL_OK;
     Workspace *w = nullptr;
-    int32_t rc = get_workspace(s, launch_bytes(imgs, keep.data(), m, connectivity), &w);
+    int32_t rc = get_workspace(s, launch_bytes(imgs, keep.data(), m, connectivity, true), &w);
     if (rc != CCL_OK)
         return rc;
-    return enqueue_launch(imgs, keep.data(), m, connectivity, thr, num_components_dev, w, s);
+    return enqueue_launch(imgs, keep.data(), m, connectivity, thr, num_components_dev, w, s, true);
 }
 
 }  // namespace
@@ -893,6 +1025,9 @@ int32_t ccl_release(void)
             cudaEventDestroy(kv.second.stage_done);
     }
     g_ws.clear();
+    for (auto &kv : g_fan)
+        destroy_fanout(kv.second);
+    g_fan.clear();
     return map_cuda(e);
 }
 
@@ -906,7 +1041,7 @@ int32_t ccl_set_tile_policy(int32_t policy)
 
 int32_t ccl_set_launch_mode(int32_t mode)
 {
-    if (mode < 0 || mode > 2)
+    if (mode < 0 || mode > 3)
         return CCL_ERR_INVALID_ARGUMENT;
     set_launch_mode(mode);
     return CCL_OK;
@@ -936,6 +1071,12 @@ int32_t ccl_set_tuning(const ccl_tune_row *rows, int32_t n, int32_t density_lo_p
     }
     set_tuning(t.data(), n, (density_lo_permille * 1024 + 500) / 1000, (density_hi_permille * 1024 + 500) / 1000,
                probe_samples, single_persistent_max_px);
+    return CCL_OK;
+}
+
+int32_t ccl_set_streams_min_px(int64_t px)
+{
+    set_streams_min_px(px < 0 ? -1 : px);
     return CCL_OK;
 }
 

@@ -90,7 +90,8 @@ int64_t edge_item_count(int conn, const Layout &L, int H, int W);
 void bind_workspace(Img &a, const Layout &L, void *ws);
 
 // Enqueue the whole labelling path for one image on `s`.  `a` must be fully bound.
-cudaError_t launch_label(const Img &a, const Layout &L, int conn, cudaStream_t s);
+// global_per_sm >= 0 replaces the process-wide CTAs per SM of the global kernel.
+cudaError_t launch_label(const Img &a, const Layout &L, int conn, cudaStream_t s, int global_per_sm = -1);
 
 // Enqueue the batched path: tiles, boundary items and segments summed over the batch.
 cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, int conn, cudaStream_t s);
@@ -114,10 +115,13 @@ struct Tuning {
     int dens_lo, dens_hi;     // density class bounds, object fraction in 1/1024
     int probe_samples;        // 16-byte samples per image for the density probe
     int64_t single_fused_max_px;  // single images up to this size take the persistent launch
+    int64_t streams_min_px;       // batches whose smallest image has at least this many
+                                  // pixels are fanned out over streams (-1: never)
 };
 const Tuning &tuning();
 // replace the table in use (n <= 0: back to the built-in one); not while calls are in flight
 void set_tuning(const TuneRow *rows, int n, int lo, int hi, int probe, int64_t single_max);
+void set_streams_min_px(int64_t px);
 const TuneRow &tune_row(int64_t px);
 // resident CTAs of the persistent kernel for `conn` on the current device (0 on error)
 int fused_resident_ctas(int conn);
@@ -131,7 +135,8 @@ int sm_count();
 void set_fused_ctas_per_sm(int n);
 int fused_ctas_per_sm_override();
 // process-wide launch mode: 0 = automatic (the tuning table decides for batches and single
-// images), 1 = always the three kernels, 2 = always the persistent launch
+// images), 1 = always the three kernels, 2 = always the persistent launch, 3 = batches of
+// two or more images always fanned out over streams (otherwise as 0)
 void set_launch_mode(int m);
 int launch_mode();
 
@@ -173,12 +178,22 @@ int64_t fused_image_bytes(int32_t H, int32_t W, int conn);
 int64_t fused_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn);
 int32_t enqueue_fused(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
                       Workspace *w, cudaStream_t s);
-// a batch launch in the current launch mode and the tuning row of its pixel count
-// (persistent or three kernels)
+// The form of a batch launch in the current launch mode: fanned out over streams by the
+// size of its smallest image (allow_streams: not for the server, whose admission sizes
+// batches for the other two forms), else persistent or three kernels by the tuning row of
+// its pixel count.
+enum BatchForm { FORM_THREE = 0, FORM_PERSISTENT = 1, FORM_STREAMS = 2 };
+int batch_form(const ccl_image *imgs, const int32_t *keep, int32_t m, bool allow_streams);
 bool batch_persistent(const ccl_image *imgs, const int32_t *keep, int32_t m);
-int64_t launch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn);
+// workspace bytes of the caller's stream, and the enqueue, for the form batch_form chooses
+int64_t launch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, bool allow_streams);
 int32_t enqueue_launch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
-                       Workspace *w, cudaStream_t s);
+                       Workspace *w, cudaStream_t s, bool allow_streams);
+// the fan-out form: every image on one of FAN_STREAMS library streams (each with its own
+// workspace), joined back to `s`; status bits go to w's header
+constexpr int FAN_STREAMS = 3;
+int32_t enqueue_streams(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
+                        Workspace *w, cudaStream_t s);
 // how one image is labelled: persistent launch or three kernels (conn then carries the tile
 // shape); bytes of workspace, header included
 struct SinglePlan {
@@ -187,7 +202,14 @@ struct SinglePlan {
     int64_t bytes;
 };
 SinglePlan plan_single(int32_t H, int32_t W, int conn);
+// per-call overrides of a three-kernel single-image launch: the status word (nullptr: the
+// workspace's) and the global kernel's CTAs per SM (-1: the process-wide setting)
+struct LaunchOpts {
+    int *status = nullptr;
+    int global_per_sm = -1;
+};
 int32_t enqueue_single(const SinglePlan &P, const uint8_t *img, int32_t H, int32_t W, int64_t pitch, int32_t thr,
-                       int32_t *labels, int32_t *k_dev, Workspace *w, cudaStream_t s);
+                       int32_t *labels, int32_t *k_dev, Workspace *w, cudaStream_t s,
+                       const LaunchOpts &o = LaunchOpts());
 
 }  // namespace ccl

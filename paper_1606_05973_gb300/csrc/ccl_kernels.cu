@@ -153,10 +153,10 @@ static int current_device()
 }
 
 // grid of the cooperative global kernel: `need` CTAs, at most `fit` (all resident), and at
-// most the per-SM cap times the SM count when a cap is set
-static int global_grid(int64_t need, int fit, int dev)
+// most the per-SM cap times the SM count when a cap is set (cap_override >= 0: that cap)
+static int global_grid(int64_t need, int fit, int dev, int cap_override = -1)
 {
-    const int cap = g_global_per_sm.load();
+    const int cap = cap_override >= 0 ? cap_override : g_global_per_sm.load();
     int64_t g = need < fit ? need : fit;
     if (cap > 0 && g > (int64_t)cap * g_num_sms[dev])
         g = (int64_t)cap * g_num_sms[dev];
@@ -300,7 +300,8 @@ template <class K> static cudaError_t launch_tiles_b(K kern, int ntiles, int nt,
     return cudaSuccess;
 }
 
-template <class C> static cudaError_t launch_label_t(const Img &a_in, const Layout &L, cudaStream_t s)
+template <class C>
+static cudaError_t launch_label_t(const Img &a_in, const Layout &L, cudaStream_t s, int global_per_sm)
 {
     const int ntiles = L.nTX * L.nTY;
     // large single images: each tile-pass and final-pass CTA prefetches the inputs of the
@@ -320,7 +321,7 @@ template <class C> static cudaError_t launch_label_t(const Img &a_in, const Layo
     const int64_t work = edge_items<C>(L.nTX, L.nTY, a.H, a.W);
     const int64_t need = ((work > L.nSeg ? work : L.nSeg) + GNT - 1) / GNT;
     const int dev = current_device();
-    const int grid = global_grid(need, KernState<C>::global_ctas[dev], dev);
+    const int grid = global_grid(need, KernState<C>::global_ctas[dev], dev, global_per_sm);
     Img arg = a;
     void *args[] = {&arg};
     CCL_LAUNCH(KID_GLOBAL, cudaLaunchCooperativeKernel((const void *)k_global<C>, dim3(grid), dim3(GNT), args, 0, s));
@@ -347,15 +348,15 @@ static cudaError_t launch_batch_t(const Batch &B, int64_t tiles, int64_t items, 
     return cudaSuccess;
 }
 
-cudaError_t launch_label(const Img &a, const Layout &L, int conn, cudaStream_t s)
+cudaError_t launch_label(const Img &a, const Layout &L, int conn, cudaStream_t s, int global_per_sm)
 {
     switch (resolve_conn(conn, a.H, a.W)) {
-    case 8 | CONN_NARROW: return launch_label_t<NarrowCfg>(a, L, s);
-    case 8 | CONN_BIG: return launch_label_t<BigCfg>(a, L, s);
-    case 4: return launch_label_t<MainCfg4>(a, L, s);
-    case 8 | CONN_CLASSES: return launch_label_t<MainCfgC8>(a, L, s);
-    case 4 | CONN_CLASSES: return launch_label_t<MainCfgC4>(a, L, s);
-    default: return launch_label_t<MainCfg>(a, L, s);
+    case 8 | CONN_NARROW: return launch_label_t<NarrowCfg>(a, L, s, global_per_sm);
+    case 8 | CONN_BIG: return launch_label_t<BigCfg>(a, L, s, global_per_sm);
+    case 4: return launch_label_t<MainCfg4>(a, L, s, global_per_sm);
+    case 8 | CONN_CLASSES: return launch_label_t<MainCfgC8>(a, L, s, global_per_sm);
+    case 4 | CONN_CLASSES: return launch_label_t<MainCfgC4>(a, L, s, global_per_sm);
+    default: return launch_label_t<MainCfg>(a, L, s, global_per_sm);
     }
 }
 
@@ -375,7 +376,7 @@ cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t s
 #include "ccl_tuning.inc"  // kTuneRows and the kTune* constants, written from tuning.json by build.py
 
 static const Tuning g_builtin = {kTuneRows, (int)(sizeof(kTuneRows) / sizeof(kTuneRows[0])), kTuneDensLo,
-                                 kTuneDensHi, kTuneProbeSamples, kTuneSingleFusedMaxPx};
+                                 kTuneDensHi, kTuneProbeSamples, kTuneSingleFusedMaxPx, kTuneStreamsMinPx};
 // The table in use: the built-in one, or one set by ccl_set_tuning (kept in g_user_rows).
 static Tuning g_tuning = g_builtin;
 static std::vector<TuneRow> g_user_rows;
@@ -389,8 +390,10 @@ void set_tuning(const TuneRow *rows, int n, int lo, int hi, int probe, int64_t s
         return;
     }
     g_user_rows.assign(rows, rows + n);
-    g_tuning = {g_user_rows.data(), n, lo, hi, probe, single_max};
+    g_tuning = {g_user_rows.data(), n, lo, hi, probe, single_max, g_tuning.streams_min_px};
 }
+
+void set_streams_min_px(int64_t px) { g_tuning.streams_min_px = px; }
 
 const TuneRow &tune_row(int64_t px)
 {

@@ -215,7 +215,7 @@ bool try_launch_locked(ccl_server *s, Lane &L)
     const int32_t m = (int32_t)L.ids.size();
     if (m == 0)
         return false;
-    L.bytes = launch_bytes(L.imgs.data(), L.keep.data(), m, conn);
+    L.bytes = launch_bytes(L.imgs.data(), L.keep.data(), m, conn, false);
     L.offset = reserve_locked(s, L.bytes);
     int32_t rc = CCL_OK;
     if (L.offset < 0) {
@@ -227,7 +227,7 @@ bool try_launch_locked(ccl_server *s, Lane &L)
         cudaError_t e = cudaMemsetAsync(static_cast<char *>(L.ws.dev) + 4, 0, 4, L.stream);
         rc = map_cuda(e);
         if (rc == CCL_OK)
-            rc = enqueue_launch(L.imgs.data(), L.keep.data(), m, conn, 0, L.k_dev, &L.ws, L.stream);
+            rc = enqueue_launch(L.imgs.data(), L.keep.data(), m, conn, 0, L.k_dev, &L.ws, L.stream, false);
         if (rc == CCL_OK) {
             // K values and the status word back to the host
             e = cudaMemcpyAsync(L.k_host, L.k_dev, (size_t)m * 4, cudaMemcpyDeviceToHost, L.stream);

@@ -4,9 +4,11 @@
     python -m paper_1606_05973_gb300.tile_sweep --write-table [--table-out PATH] [--summary-out PATH]
 
 --write-table measures the persistent single launch over size classes x density classes x
-the two compiled tile shapes x grids of 4, 6 and 8 CTAs per SM, and single images under
-the persistent launch against the three kernels, and writes the library's tuning table
+the two compiled tile shapes x grids of 4, 6 and 8 CTAs per SM, single images under the
+persistent launch against the three kernels, and batches of large images fanned out over
+streams against three launches over the batch, and writes the library's tuning table
 (tuning.json, compiled into libccl by build.py) from the fastest entries.
+--streams-only measures only the last and updates streams_min_px in the table.
 
 Without it:
 
@@ -84,6 +86,53 @@ SIZE_CLASSES = [(1 << 20, (1, 1024)), (1 << 22, (1, 2048)), (1 << 24, (1, 4096))
 DENSITIES = (0.1, 0.5, 0.9)  # one Bernoulli density inside each class of density_bounds (0.3, 0.7)
 CTAS = (4, 6, 8)
 SINGLE_SIDES = (256, 512, 1024, 1536, 2048, 3072, 4096, 8192)
+STREAM_SIDES = (4096, 6144, 8192, 12288, 16384)
+
+
+def streams_threshold(lines):
+    """Batches of six images of each side in STREAM_SIDES (two each of sigma = 16 blobs,
+    Bernoulli(0.6) and the serpentine; more images favour the launches over the whole batch),
+    fanned out over streams (launch mode 3) against three launches over the batch (mode 1);
+    returns the smallest side^2 from which the fan-out is at least 5% faster at that side
+    and every larger one (-1: at none); below, the winner depends on the number of images."""
+    import torch
+
+    import paper_1606_05973_gb300 as ccl
+    import synth
+
+    lib = ccl.lib()
+    dev = torch.device("cuda:0")
+    sync = torch.cuda.synchronize
+    wins = {}
+    lines.append("batches of six images, ms per call: fanned out over streams / three launches")
+    for side in STREAM_SIDES:
+        imgs = []
+        for r in range(2):
+            imgs += [synth.blobs_device(side, side, 16.0, 8 + 3 * r, dev),
+                     torch.from_numpy(synth.bernoulli(side, side, 0.6, 9 + 3 * r)).to(dev),
+                     torch.from_numpy(synth.serpentine(side, side)).to(dev)]
+        outs = [torch.empty((side, side), dtype=torch.int32, device=dev) for _ in imgs]
+        kd = torch.zeros(len(imgs), dtype=torch.int32, device=dev)
+        ms = {}
+        ks = {}
+        for mode in (3, 1):
+            lib.ccl_set_launch_mode(mode)
+            ms[mode] = _time(lambda: ccl.label_batch(imgs, outs=outs, k_out=kd), sync)
+            ks[mode] = kd.cpu().tolist()
+        lib.ccl_set_launch_mode(0)
+        if ks[3] != ks[1]:
+            raise RuntimeError(f"K differs between the batch forms at {side}^2")
+        wins[side] = ms[3] < 0.95 * ms[1]
+        lines.append(f"  {side}^2: {ms[3]:.4f} / {ms[1]:.4f}")
+        del imgs, outs
+        torch.cuda.empty_cache()
+    best = -1
+    for side in reversed(STREAM_SIDES):
+        if not wins[side]:
+            break
+        best = side * side
+    lines.append(f"batches whose smallest image has at least {best} px are fanned out over streams")
+    return best
 
 
 def _time(fn, sync, reps=10, warm=2):
@@ -199,9 +248,11 @@ def write_table(out_json, out_txt):
             lines.append(f"  {side}^2 {name}: {pers:.4f} / {three:.4f}")
         if wins:
             single_max = side * side
+    streams_min = streams_threshold(lines)
     t = {"about": json.load(open(TUNING_PATH))["about"],
          "written_by": "python -m paper_1606_05973_gb300.tile_sweep --write-table (GB300 measurements)",
-         "density_bounds": [0.3, 0.7], "probe_samples": 64, "single_fused_max_px": single_max, "rows": rows}
+         "density_bounds": [0.3, 0.7], "probe_samples": 64, "single_fused_max_px": single_max,
+         "streams_min_px": streams_min, "rows": rows}
     txt = json.dumps(t, indent=2)
     with open(out_json, "w") as f:
         f.write(txt + "\n")
@@ -224,9 +275,23 @@ def main():
     ap.add_argument("--out", default=None, help="also write the JSON object to this file")
     ap.add_argument("--write-table", action="store_true",
                     help="tune the persistent launch and write tuning.json (see write_table)")
+    ap.add_argument("--streams-only", action="store_true",
+                    help="measure only the fan-out threshold and update streams_min_px in the table")
     ap.add_argument("--table-out", default=TUNING_PATH)
     ap.add_argument("--summary-out", default=None)
     args = ap.parse_args()
+    if args.streams_only:
+        lines = []
+        t = json.load(open(TUNING_PATH))
+        t["streams_min_px"] = streams_threshold(lines)
+        with open(args.table_out, "w") as f:
+            f.write(json.dumps(t, indent=2) + "\n")
+        txt = "\n".join(lines) + "\n"
+        print(txt)
+        if args.summary_out:
+            with open(args.summary_out, "w") as f:
+                f.write(txt)
+        return
     if args.write_table:
         write_table(args.table_out, args.summary_out or os.path.join(ROOT, "gpurun_out", "tuning_sweep.txt"))
         return

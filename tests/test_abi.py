@@ -76,7 +76,7 @@ def test_argument_checks_need_no_gpu(lib):
     for ok in (1, 2, 0):
         assert lib.ccl_set_tile_policy(ok) == 0
     assert lib.ccl_set_global_ctas_per_sm(-1) == 1
-    assert lib.ccl_set_launch_mode(3) == 1 and lib.ccl_set_launch_mode(-1) == 1
+    assert lib.ccl_set_launch_mode(4) == 1 and lib.ccl_set_launch_mode(-1) == 1
     assert lib.ccl_set_tuning(None, 1, 300, 700, 64, 0) == 1  # rows missing
     assert lib.ccl_set_tuning(None, 0, 0, 0, 0, 0) == 0       # back to the built-in table
     assert lib.ccl_set_global_ctas_per_sm(1) == 0 and lib.ccl_set_global_ctas_per_sm(0) == 0
