@@ -597,8 +597,8 @@ def run_ours(args, rank, world, local_rank):
 
 
 def measure_plain(args, name, dev, lib):
-    """Another plain-path workload as an extra key: images alternating over two streams
-    with the global kernel at one CTA per SM (as the headline), CUDA events around 10 steps
+    """Another plain-path workload as an extra key: images round robin over the headline's
+    streams with the global kernel at one CTA per SM (as the headline), CUDA events around 10 steps
     after 3 warm-up steps; for single-image workloads also one call captured in a CUDA graph
     and replayed (a small image is launch-bound and L2-resident).  K is checked against
     the plain call, and the device status after each pass."""
@@ -609,12 +609,13 @@ def measure_plain(args, name, dev, lib):
     imgs, desc = make_workload(name, dev)
     labels = [torch.empty(tuple(t.shape), dtype=torch.int32, device=dev) for _, t in imgs]
     kdev = torch.zeros(len(imgs), dtype=torch.int32, device=dev)
-    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    nstreams = max(1, args.streams)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(nstreams)]
     sptr = [ctypes.c_void_p(st.cuda_stream) for st in streams]
     px = sum(t.numel() for _, t in imgs)
     lib.ccl_set_global_ctas_per_sm(args.global_ctas_per_sm or 0)
 
-    def step(ns=2):
+    def step(ns=nstreams):
         for i, (_, t) in enumerate(imgs):
             H, W = t.shape
             rc = lib.ccl_label_async(t.data_ptr(), H, W, t.stride(0), args.connectivity, labels[i].data_ptr(),
@@ -635,10 +636,12 @@ def measure_plain(args, name, dev, lib):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 10 if len(imgs) > 1 else 200
     e0.record(main)
-    streams[1].wait_stream(main)
+    for st in streams[1:]:
+        st.wait_stream(main)
     for _ in range(reps):
         step()
-    main.wait_stream(streams[1])
+    for st in streams[1:]:
+        main.wait_stream(st)
     e1.record(main)
     torch.cuda.synchronize()
     status()
@@ -647,7 +650,7 @@ def measure_plain(args, name, dev, lib):
     gbs = PATH_BYTES_PER_PX * px / (ms * 1e-3) / 1e9
     res = {"workload": desc["workload"], "inputs_sha256": desc["inputs_sha256"], "ms_per_step": round(ms, 4),
            "value": round(px / (ms * 1e-3) / 1e9, 2), "unit": UNIT,
-           "path_frac": round(gbs / peak, 4), "how": f"{reps} steps, images alternating over two streams"}
+           "path_frac": round(gbs / peak, 4), "how": f"{reps} steps, images round robin over {nstreams} streams"}
     if len(imgs) == 1:
         ref_k = int(kdev[0])
         lib.ccl_set_global_ctas_per_sm(0)
