@@ -1811,17 +1811,18 @@ template <class C> CCL_HD void tile_local_body(const Img &a, SmemL<C> &s, int ti
 // root count, scan and labels.  Roots are final once the merge is done, so they are
 // counted during the first jump round and labelled while later rounds (deep trees only)
 // keep shortening the other nodes' paths.
-template <class C> CCL_HD void global_body(const Img &a, ScanBuf &sb, int &s_flag, int b, int G, int tid)
+template <class C, int NTG = GNT>
+CCL_HD void global_body(const Img &a, ScanBufT<NTG> &sb, int &s_flag, int b, int G, int tid)
 {
     unsigned epoch = 0;
     GridSync *g = a.gsync;
-    const int64_t stride = (int64_t)G * GNT;
+    const int64_t stride = (int64_t)G * NTG;
     CCL_TICK(1, 0);
 
     // a3: boundary merge (Algorithm 7's boundary loop with Algorithm 8's union)
     const int64_t nh = horizontal_items<C>(a.nTY, a.W);
     const int64_t nv = (int64_t)(a.nTX - 1) * a.H;
-    for (int64_t i = (int64_t)b * GNT + tid; i < nh + nv; i += stride)
+    for (int64_t i = (int64_t)b * NTG + tid; i < nh + nv; i += stride)
         merge_item<C>(a, i, nh);
     grid_sync(g, (unsigned)G, epoch, a.status, tid);
     CCL_TICK(1, 1);
@@ -1829,7 +1830,7 @@ template <class C> CCL_HD void global_body(const Img &a, ScanBuf &sb, int &s_fla
     // a4 + a5: first jump round over this thread's contiguous raster range of segments,
     // counting roots; scan of the counts across the CTA, then across CTAs
     int64_t s0, s1;
-    seg_range(a.nSeg, G, GNT, b, tid, &s0, &s1);
+    seg_range(a.nSeg, G, NTG, b, tid, &s0, &s1);
     int c = 0;
     bool more = false;
     for (int64_t seg = s0; seg < s1; seg++)
@@ -1838,12 +1839,12 @@ template <class C> CCL_HD void global_body(const Img &a, ScanBuf &sb, int &s_fla
         flag_status(&g->round_more[0], 1);
     scan_put(sb, tid, c);
     cta_sync();
-    for (int k = 0; k < GNT_LOG; k++) {
+    for (int k = 0; k < ilog2(NTG); k++) {
         scan_step(sb, tid, k);
         cta_sync();
     }
     const int incl = scan_incl(sb, tid);
-    if (tid == GNT - 1)
+    if (tid == NTG - 1)
         st_g(&a.bsum[b], incl);
     grid_sync(g, (unsigned)G, epoch, a.status, tid);
     CCL_TICK(1, 2);

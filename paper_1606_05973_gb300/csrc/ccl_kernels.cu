@@ -34,12 +34,25 @@ template <class C> __global__ void __launch_bounds__(C::NT, 2048 / C::NT) k_tile
 #ifndef CCL_GLOBAL_MIN_CTAS
 #define CCL_GLOBAL_MIN_CTAS 2
 #endif
-template <class C> __global__ void __launch_bounds__(GNT, CCL_GLOBAL_MIN_CTAS) k_global(Img a)
+// NTG threads per CTA: GNT, or GNT / 2 when the grid is capped at one CTA per SM (images on
+// several streams).  The half-size CTA is held to 32 registers per thread, so that three
+// tile CTAs (512 threads at 32 registers) fit beside it on an SM: on GB300 the 21568^2
+// three-stream step went from 2.41 to 2.33 ms (at 2 CTAs per SM of launch bounds, 56
+// registers and room for two tile CTAs, 2.38 ms)
+#ifndef CCL_GLOBAL_HALF_MIN_CTAS
+#define CCL_GLOBAL_HALF_MIN_CTAS 4
+#endif
+template <class C, int NTG>
+__global__ void __launch_bounds__(NTG, NTG == GNT ? CCL_GLOBAL_MIN_CTAS : CCL_GLOBAL_HALF_MIN_CTAS) k_global(Img a)
 {
-    __shared__ ScanBuf sb;
+    __shared__ ScanBufT<NTG> sb;
     __shared__ int s_flag;
-    global_body<C>(a, sb, s_flag, blockIdx.x, gridDim.x, threadIdx.x);
+    global_body<C, NTG>(a, sb, s_flag, blockIdx.x, gridDim.x, threadIdx.x);
 }
+constexpr int GNT_HALF = GNT / 2;
+#ifndef CCL_GLOBAL_HALF
+#define CCL_GLOBAL_HALF 1
+#endif
 
 // the global phases of a small image in one CTA, in shared memory (small_global_body)
 template <class C> __global__ void __launch_bounds__(GNT, 1) k_global_small(Img a)
@@ -152,6 +165,9 @@ static int current_device()
     return dev;
 }
 
+// the CTAs-per-SM cap of the global kernel in force (0: none)
+static int effective_global_cap(int cap_override) { return cap_override >= 0 ? cap_override : g_global_per_sm.load(); }
+
 // grid of the cooperative global kernel: `need` CTAs, at most `fit` (all resident), and at
 // most the per-SM cap times the SM count when a cap is set (cap_override >= 0: that cap)
 static int global_grid(int64_t need, int fit, int dev, int cap_override = -1)
@@ -165,7 +181,9 @@ static int global_grid(int64_t need, int fit, int dev, int cap_override = -1)
 
 template <class C> struct KernState {
     static int global_ctas[MAX_DEVICES], global_batch_ctas[MAX_DEVICES], tile_ctas[MAX_DEVICES];
+    static int global_half_ctas[MAX_DEVICES];
 };
+template <class C> int KernState<C>::global_half_ctas[MAX_DEVICES] = {};
 template <class C> int KernState<C>::global_ctas[MAX_DEVICES] = {};
 template <class C> int KernState<C>::global_batch_ctas[MAX_DEVICES] = {};
 template <class C> int KernState<C>::tile_ctas[MAX_DEVICES] = {};
@@ -197,13 +215,19 @@ template <class C> static cudaError_t init_cfg(int dev)
     if (err == cudaSuccess)
         KernState<C>::tile_ctas[dev] = g_num_sms[dev] * occt;
     if (err == cudaSuccess)
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_global<C>, GNT, 0);
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_global<C, GNT>, GNT, 0);
+    int occh = 0;
+    if (err == cudaSuccess)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occh, k_global<C, GNT_HALF>, GNT_HALF, 0);
+    if (err == cudaSuccess)
+        KernState<C>::global_half_ctas[dev] = std::min(g_num_sms[dev] * occh, MAX_GLOBAL_CTAS);
     if (err == cudaSuccess)
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, k_global_batch<C>, GNT, 0);
     if (err == cudaSuccess) {
         KernState<C>::global_ctas[dev] = std::min(g_num_sms[dev] * occ, MAX_GLOBAL_CTAS);
         KernState<C>::global_batch_ctas[dev] = std::min(g_num_sms[dev] * occb, MAX_GLOBAL_CTAS);
-        if (KernState<C>::global_ctas[dev] < 1 || KernState<C>::global_batch_ctas[dev] < 1)
+        if (KernState<C>::global_ctas[dev] < 1 || KernState<C>::global_batch_ctas[dev] < 1 ||
+            KernState<C>::global_half_ctas[dev] < 1)
             err = cudaErrorInvalidConfiguration;
     }
     return err;
@@ -319,12 +343,20 @@ static cudaError_t launch_label_t(const Img &a_in, const Layout &L, cudaStream_t
         return cudaSuccess;
     }
     const int64_t work = edge_items<C>(L.nTX, L.nTY, a.H, a.W);
-    const int64_t need = ((work > L.nSeg ? work : L.nSeg) + GNT - 1) / GNT;
     const int dev = current_device();
-    const int grid = global_grid(need, KernState<C>::global_ctas[dev], dev, global_per_sm);
     Img arg = a;
     void *args[] = {&arg};
-    CCL_LAUNCH(KID_GLOBAL, cudaLaunchCooperativeKernel((const void *)k_global<C>, dim3(grid), dim3(GNT), args, 0, s));
+    if (CCL_GLOBAL_HALF && effective_global_cap(global_per_sm) == 1) {
+        const int64_t need = ((work > L.nSeg ? work : L.nSeg) + GNT_HALF - 1) / GNT_HALF;
+        const int grid = global_grid(need, KernState<C>::global_half_ctas[dev], dev, global_per_sm);
+        CCL_LAUNCH(KID_GLOBAL, cudaLaunchCooperativeKernel((const void *)k_global<C, GNT_HALF>, dim3(grid),
+                                                           dim3(GNT_HALF), args, 0, s));
+    } else {
+        const int64_t need = ((work > L.nSeg ? work : L.nSeg) + GNT - 1) / GNT;
+        const int grid = global_grid(need, KernState<C>::global_ctas[dev], dev, global_per_sm);
+        CCL_LAUNCH(KID_GLOBAL,
+                   cudaLaunchCooperativeKernel((const void *)k_global<C, GNT>, dim3(grid), dim3(GNT), args, 0, s));
+    }
     CCL_LAUNCH(KID_FINAL, launch_tiles(k_final<C>, ntiles, C::NT, sizeof(SmemF<C>), s, a));
     return cudaSuccess;
 }

@@ -263,12 +263,12 @@ template <class C> struct Emu {
         g_sched = nullptr;
     }
 
-    // G CTAs of GNT threads, all running at once (cooperative launch)
-    void run_global(const Img &a, int G)
+    // G CTAs of NTG threads, all running at once (cooperative launch)
+    template <int NTG = GNT> void run_global(const Img &a, int G)
     {
-        std::vector<ScanBuf> sbs(G);
+        std::vector<ScanBufT<NTG>> sbs(G);
         std::vector<int> flags(G);
-        Sched sch(G, GNT, rng(), [&](int b, int t) { global_body<C>(a, sbs[b], flags[b], b, G, t); });
+        Sched sch(G, NTG, rng(), [&](int b, int t) { global_body<C, NTG>(a, sbs[b], flags[b], b, G, t); });
         g_sched = &sch;
         sch.run();
         g_sched = nullptr;
@@ -403,6 +403,10 @@ template <class C> struct Emu {
             g_sched = &sch;
             sch.run();
             g_sched = nullptr;
+        } else if ((seed & 3) == 3) {
+            // the half-size global CTAs of the one-CTA-per-SM form
+            const int64_t need2 = ((work > L.nSeg ? work : L.nSeg) + GNT / 2 - 1) / (GNT / 2);
+            run_global<GNT / 2>(a, (int)std::max<int64_t>(1, std::min<int64_t>(4, need2)));
         } else {
             run_global(a, G);
         }
