@@ -199,6 +199,41 @@ def test_global_ctas_per_sm_cap_and_two_streams(ccl):
         lib.ccl_set_global_ctas_per_sm(0)
 
 
+def test_half_size_global_kernel_at_one_cta_per_sm(ccl):
+    """At one CTA per SM the global kernel takes CTAs of 512 threads (each thread then walks
+    twice the items and segments); labels under every mode it serves against the oracle:
+    the three 8-connected tile shapes, 4-connectivity and classes, on a serpentine (one
+    component whose parent chains need several pointer-jumping rounds) and dense noise."""
+    import torch
+
+    lib = ccl.lib()
+    imgs = [synth.serpentine(2000, 2600), synth.bernoulli(2500, 3100, 0.6, 51)]
+    rng = np.random.default_rng(52)
+    cls = rng.integers(0, 3, size=(1500, 2100), dtype=np.uint8)
+    try:
+        assert lib.ccl_set_global_ctas_per_sm(1) == 0
+        for policy in (0, 2, 3):
+            assert lib.ccl_set_tile_policy(policy) == 0
+            for im in imgs:
+                ref, rk = oracle.cclremsp(im)
+                lab, k = ccl.label(torch.from_numpy(im).cuda())
+                assert k == rk and np.array_equal(lab.cpu().numpy(), ref), (policy, im.shape)
+        lib.ccl_set_tile_policy(0)
+        for im in imgs:
+            ref, rk = oracle.cclremsp(im, 4)
+            lab, k = ccl.label(torch.from_numpy(im).cuda(), connectivity=4)
+            assert k == rk and np.array_equal(lab.cpu().numpy(), ref), im.shape
+        for conn in (8, 4):
+            ref, rk = oracle.classes(cls, conn)
+            lab, k = ccl.label(torch.from_numpy(cls).cuda(), connectivity=conn, classes=True)
+            assert k == rk and np.array_equal(lab.cpu().numpy(), ref), conn
+        flags = ctypes.c_int32(0)
+        assert lib.ccl_device_status(stream_handle(), ctypes.byref(flags)) == 0 and flags.value == 0
+    finally:
+        lib.ccl_set_global_ctas_per_sm(0)
+        lib.ccl_set_tile_policy(0)
+
+
 def test_tile_policies_give_identical_labels(ccl):
     """The 8-connected path on 64 x 256 tiles (policy 1), 64 x 128 tiles (policy 2), 64 x 512
     tiles of 512 threads (policy 3) and the size rule (policy 0): single images on both sides
