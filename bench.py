@@ -413,7 +413,9 @@ def run_ours(args, rank, world, local_rank):
     launches = sum(v[0] for v in kt.values())
     check_status("the per-kernel pass")
 
-    # per-image latency: each image labelled alone, one stream, an event pair per call
+    # per-image latency: each image labelled alone, one stream, an event pair per call, with
+    # the library's default global grid (the per-SM cap is for images on several streams)
+    lib.ccl_set_global_ctas_per_sm(0)
     per_image = {}
     for i, (name, t) in enumerate(imgs):
         H, W = t.shape
@@ -433,6 +435,8 @@ def run_ours(args, rank, world, local_rank):
                            "p99_ms": round(ms_i[min(len(ms_i) - 1, int(0.99 * len(ms_i)))], 4),
                            "gpx_s_median": round(H * W / (statistics.median(ms_i) * 1e-3) / 1e9, 2)}
     check_status("the per-image pass", [sptr])
+    if args.global_ctas_per_sm is not None:
+        lib.ccl_set_global_ctas_per_sm(args.global_ctas_per_sm)
 
     # correctness spot check outside the timed region: K must match a fresh labelling
     ks = kdev.cpu().tolist()
@@ -698,7 +702,7 @@ def measure_plain(args, name, dev, lib):
         tms = h0.elapsed_time(h1) / reps
         res["graph_replay_persistent"] = {"us_per_image": round(tms * 1e3, 2),
                                           "value": round(px / (tms * 1e-3) / 1e9, 2)}
-    lib.ccl_set_global_ctas_per_sm(args.global_ctas_per_sm or 0)
+    lib.ccl_set_global_ctas_per_sm(0)  # library default for the single-stream measurements after
     return res
 
 
