@@ -293,7 +293,7 @@ def main():
                 f.write(txt)
         return
     if args.write_table:
-        write_table(args.table_out, args.summary_out or os.path.join(ROOT, "gpurun_out", "tuning_sweep.txt"))
+        write_table(args.table_out, args.summary_out or os.path.join(os.getcwd(), "tuning_sweep.txt"))
         return
     with cf.ThreadPoolExecutor(len(SHAPES)) as ex:
         libs = dict(zip(SHAPES, ex.map(lambda s: build_shape(*s), SHAPES)))
