@@ -306,13 +306,16 @@ int32_t ccl_shutdown(void);
 
 /*
  * ccl_set_global_ctas_per_sm - how many CTAs of the cooperative boundary-merge / flatten
- * kernel (1024 threads each; the merge of Algorithm 7's boundary loop with Algorithm 8's
- * union, and Algorithm 3's flatten) may share one SM.  n = 0 (the default) places as many
- * as fit (2 on GB300, every thread slot).  n = 1 leaves half of each SM's thread slots
- * free, so that when images are labelled on two or more streams, the tile pass of one
- * image (instruction-bound) runs beside the global pass of another (latency-bound); a
- * single stream is then slower, since the global pass has half the threads to hide its
- * latency.  Process-wide; applies to launches enqueued after the call.  Returns
+ * kernel (the merge of Algorithm 7's boundary loop with Algorithm 8's union, and
+ * Algorithm 3's flatten) may share one SM.  n = 0 (the default) places as many as fit (2
+ * CTAs of 1024 threads on GB300, every thread slot).  n = 1 runs one CTA per SM, and for
+ * single images a CTA of 512 threads held to 32 registers, which leaves three quarters of
+ * each SM's thread slots and registers free: when images are labelled on two or more
+ * streams, the tile pass of one image (instruction-bound, three of its CTAs fit beside it)
+ * runs beside the global pass of another (latency-bound).  A single stream is then
+ * slower, since the global pass has fewer threads to hide its latency.  Batches fanned out
+ * over streams (ccl_label_batch) use n = 1 for their images whatever this setting.
+ * Process-wide; applies to launches enqueued after the call.  Returns
  * CCL_ERR_INVALID_ARGUMENT for n < 0; n above what fits is the same as 0.
  */
 int32_t ccl_set_global_ctas_per_sm(int32_t n);
