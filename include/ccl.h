@@ -240,8 +240,10 @@ int32_t ccl_label_static_status(ccl_stream_t stream, int32_t *flags);
  * unchanged underneath).  Requests are admitted while others run: a scheduler thread packs
  * waiting requests, first come first served, into one batched launch per idle lane (a CUDA
  * stream), so launches on different lanes overlap on the device and new requests join the
- * next launch as soon as a lane and memory free up.  Each result is bit-identical to
- * labelling the image alone.
+ * next launch as soon as a lane and memory free up.  The cooperative global kernel of every
+ * launch runs at one CTA per SM whatever ccl_set_global_ctas_per_sm says, so that the other
+ * lanes' kernels fit beside it.  Each result is bit-identical to labelling the image
+ * alone.
  *
  * Memory: one pool of mem_cap_bytes of device workspace, allocated at creation and
  * resident for the server's lifetime, shared by all lanes: each launch reserves one slice

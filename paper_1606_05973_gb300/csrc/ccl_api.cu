@@ -663,7 +663,7 @@ int64_t batch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int c
 // using workspace `w` (at least batch_bytes large).  K of image keep[k] goes to
 // k_dev[keep[k]] when k_dev is not NULL.
 int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
-                      Workspace *w, cudaStream_t s)
+                      Workspace *w, cudaStream_t s, int global_per_sm)
 {
     cudaError_t e = kernels_init();
     if (e != cudaSuccess)
@@ -762,7 +762,7 @@ int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int
     B.bsum = reinterpret_cast<int *>(dev + HDR + desc_bytes + pre_bytes + base_bytes);
     B.gsync = reinterpret_cast<GridSync *>(dev + 16);
     B.status = reinterpret_cast<int *>(dev + 4);
-    return map_cuda(launch_batch(B, tileStart[m], itemStart[m], segStart[m], conn, s));
+    return map_cuda(launch_batch(B, tileStart[m], itemStart[m], segStart[m], conn, s, global_per_sm));
 }
 
 bool batch_persistent(const ccl_image *imgs, const int32_t *keep, int32_t m)
@@ -805,12 +805,12 @@ int64_t launch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int 
 }
 
 int32_t enqueue_launch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
-                       Workspace *w, cudaStream_t s, bool allow_streams)
+                       Workspace *w, cudaStream_t s, bool allow_streams, int global_per_sm)
 {
     switch (batch_form(imgs, keep, m, allow_streams)) {
     case FORM_STREAMS: return enqueue_streams(imgs, keep, m, conn, thr, k_dev, w, s);
     case FORM_PERSISTENT: return enqueue_fused(imgs, keep, m, conn, thr, k_dev, w, s);
-    default: return enqueue_batch(imgs, keep, m, conn, thr, k_dev, w, s);
+    default: return enqueue_batch(imgs, keep, m, conn, thr, k_dev, w, s, global_per_sm);
     }
 }
 

@@ -94,7 +94,9 @@ void bind_workspace(Img &a, const Layout &L, void *ws);
 cudaError_t launch_label(const Img &a, const Layout &L, int conn, cudaStream_t s, int global_per_sm = -1);
 
 // Enqueue the batched path: tiles, boundary items and segments summed over the batch.
-cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, int conn, cudaStream_t s);
+// global_per_sm >= 0 replaces the process-wide CTAs per SM of the global kernel.
+cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, int conn, cudaStream_t s,
+                         int global_per_sm = -1);
 
 // One-time per-device setup of kernel attributes (dynamic shared memory).
 cudaError_t kernels_init();
@@ -171,7 +173,7 @@ int64_t batch_fixed_bytes(int32_t m);
 int batch_conn(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn);
 int batch_conn_px(int64_t px);
 int32_t enqueue_batch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
-                      Workspace *w, cudaStream_t s);
+                      Workspace *w, cudaStream_t s, int global_per_sm = -1);
 // the persistent launch: workspace bytes (fixed part and one image's region) and enqueue
 int64_t fused_fixed_bytes(int32_t m);
 int64_t fused_image_bytes(int32_t H, int32_t W, int conn);
@@ -187,8 +189,9 @@ int batch_form(const ccl_image *imgs, const int32_t *keep, int32_t m, bool allow
 bool batch_persistent(const ccl_image *imgs, const int32_t *keep, int32_t m);
 // workspace bytes of the caller's stream, and the enqueue, for the form batch_form chooses
 int64_t launch_bytes(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, bool allow_streams);
+// (global_per_sm as launch_batch, for the three-launch form)
 int32_t enqueue_launch(const ccl_image *imgs, const int32_t *keep, int32_t m, int conn, int thr, int32_t *k_dev,
-                       Workspace *w, cudaStream_t s, bool allow_streams);
+                       Workspace *w, cudaStream_t s, bool allow_streams, int global_per_sm = -1);
 // the fan-out form: every image on one of FAN_STREAMS library streams (each with its own
 // workspace), joined back to `s`; status bits go to w's header
 constexpr int FAN_STREAMS = 3;

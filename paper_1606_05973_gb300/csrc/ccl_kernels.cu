@@ -362,18 +362,21 @@ static cudaError_t launch_label_t(const Img &a_in, const Layout &L, cudaStream_t
 }
 
 template <class C>
-static cudaError_t launch_batch_t(const Batch &B, int64_t tiles, int64_t items, int64_t segs, cudaStream_t s)
+static cudaError_t launch_batch_t(const Batch &B, int64_t tiles, int64_t items, int64_t segs, cudaStream_t s,
+                                  int global_per_sm)
 {
     if (tiles <= 0)
         return cudaSuccess;
     if (tiles > 0x7FFFFFFF)
         return cudaErrorInvalidValue;
     CCL_LAUNCH(KID_TILE_LOCAL, launch_tiles_b(k_tile_local_batch<C>, (int)tiles, C::NT, sizeof(SmemL<C>), s, B));
-    const int64_t need = ((items > segs ? items : segs) + GNT - 1) / GNT;
     const int dev = current_device();
-    const int grid = global_grid(need, KernState<C>::global_batch_ctas[dev], dev);
     Batch arg = B;
     void *args[] = {&arg};
+    // (at one CTA per SM the batch kernel keeps its 1024-thread CTAs: for the server's
+    // concurrent lanes they gave more capacity than the half-size CTAs of k_global)
+    const int64_t need = ((items > segs ? items : segs) + GNT - 1) / GNT;
+    const int grid = global_grid(need, KernState<C>::global_batch_ctas[dev], dev, global_per_sm);
     CCL_LAUNCH(KID_GLOBAL,
                cudaLaunchCooperativeKernel((const void *)k_global_batch<C>, dim3(grid), dim3(GNT), args, 0, s));
     CCL_LAUNCH(KID_FINAL, launch_tiles_b(k_final_batch<C>, (int)tiles, C::NT, sizeof(SmemF<C>), s, B));
@@ -392,15 +395,16 @@ cudaError_t launch_label(const Img &a, const Layout &L, int conn, cudaStream_t s
     }
 }
 
-cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, int conn, cudaStream_t s)
+cudaError_t launch_batch(const Batch &B, int64_t tiles, int64_t items, int64_t segs, int conn, cudaStream_t s,
+                         int global_per_sm)
 {
     switch (conn) {  // a batch's shape is chosen once for all its images (batch_conn)
-    case 8 | CONN_NARROW: return launch_batch_t<NarrowCfg>(B, tiles, items, segs, s);
-    case 8 | CONN_BIG: return launch_batch_t<BigCfg>(B, tiles, items, segs, s);
-    case 4: return launch_batch_t<MainCfg4>(B, tiles, items, segs, s);
-    case 8 | CONN_CLASSES: return launch_batch_t<MainCfgC8>(B, tiles, items, segs, s);
-    case 4 | CONN_CLASSES: return launch_batch_t<MainCfgC4>(B, tiles, items, segs, s);
-    default: return launch_batch_t<MainCfg>(B, tiles, items, segs, s);
+    case 8 | CONN_NARROW: return launch_batch_t<NarrowCfg>(B, tiles, items, segs, s, global_per_sm);
+    case 8 | CONN_BIG: return launch_batch_t<BigCfg>(B, tiles, items, segs, s, global_per_sm);
+    case 4: return launch_batch_t<MainCfg4>(B, tiles, items, segs, s, global_per_sm);
+    case 8 | CONN_CLASSES: return launch_batch_t<MainCfgC8>(B, tiles, items, segs, s, global_per_sm);
+    case 4 | CONN_CLASSES: return launch_batch_t<MainCfgC4>(B, tiles, items, segs, s, global_per_sm);
+    default: return launch_batch_t<MainCfg>(B, tiles, items, segs, s, global_per_sm);
     }
 }
 

@@ -227,7 +227,9 @@ bool try_launch_locked(ccl_server *s, Lane &L)
         cudaError_t e = cudaMemsetAsync(static_cast<char *>(L.ws.dev) + 4, 0, 4, L.stream);
         rc = map_cuda(e);
         if (rc == CCL_OK)
-            rc = enqueue_launch(L.imgs.data(), L.keep.data(), m, conn, 0, L.k_dev, &L.ws, L.stream, false);
+            // the lanes' batches run side by side: the global kernel takes one CTA per SM,
+            // so that other lanes' tile passes fit beside it
+            rc = enqueue_launch(L.imgs.data(), L.keep.data(), m, conn, 0, L.k_dev, &L.ws, L.stream, false, 1);
         if (rc == CCL_OK) {
             // K values and the status word back to the host
             e = cudaMemcpyAsync(L.k_host, L.k_dev, (size_t)m * 4, cudaMemcpyDeviceToHost, L.stream);
