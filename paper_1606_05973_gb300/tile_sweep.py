@@ -87,6 +87,19 @@ DENSITIES = (0.1, 0.5, 0.9)  # one Bernoulli density inside each class of densit
 CTAS = (4, 6, 8)
 SINGLE_SIDES = (256, 512, 1024, 1536, 2048, 3072, 4096, 8192)
 STREAM_SIDES = (4096, 6144, 8192, 12288, 16384)
+FAN_MARGIN = 0.95
+
+
+def fanout_threshold(sides, fan_ms, three_ms, margin=FAN_MARGIN):
+    """The fan-out threshold from per-side timings (sides ascending): the pixel count of the
+    smallest side from which the fan-out takes at most `margin` of the three-launch time at
+    that side and at every larger one; -1 if it does not at the largest side."""
+    best = -1
+    for side, f, t in reversed(list(zip(sides, fan_ms, three_ms))):
+        if not f < margin * t:
+            break
+        best = side * side
+    return best
 
 
 def streams_threshold(lines):
@@ -103,7 +116,7 @@ def streams_threshold(lines):
     lib = ccl.lib()
     dev = torch.device("cuda:0")
     sync = torch.cuda.synchronize
-    wins = {}
+    fan, three = [], []
     lines.append("batches of six images, ms per call: fanned out over streams / three launches")
     for side in STREAM_SIDES:
         imgs = []
@@ -122,15 +135,12 @@ def streams_threshold(lines):
         lib.ccl_set_launch_mode(0)
         if ks[3] != ks[1]:
             raise RuntimeError(f"K differs between the batch forms at {side}^2")
-        wins[side] = ms[3] < 0.95 * ms[1]
+        fan.append(ms[3])
+        three.append(ms[1])
         lines.append(f"  {side}^2: {ms[3]:.4f} / {ms[1]:.4f}")
         del imgs, outs
         torch.cuda.empty_cache()
-    best = -1
-    for side in reversed(STREAM_SIDES):
-        if not wins[side]:
-            break
-        best = side * side
+    best = fanout_threshold(STREAM_SIDES, fan, three)
     lines.append(f"batches whose smallest image has at least {best} px are fanned out over streams")
     return best
 
