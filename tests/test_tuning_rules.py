@@ -15,13 +15,15 @@ SIDES = tile_sweep.STREAM_SIDES  # 4096, 6144, 8192, 12288, 16384
 
 
 def test_fanout_threshold_from_recorded_sweeps():
-    """The two GB300 sweeps recorded in profiles/tuning_sweep.txt (ms per call, fanned out /
-    three launches): the later one clears the 5% margin from 4096^2, the earlier one only
-    from 8192^2 (6144^2 was 1.4% faster, under the margin)."""
+    """The GB300 sweeps recorded in profiles/tuning_sweep.txt (ms per call, fanned out / three
+    launches): one clears the 5% margin from 4096^2, the earliest only from 8192^2 (6144^2
+    was 1.4% faster, under the margin), the latest from 6144^2 (it lost at 4096^2)."""
     later = ([0.2430, 0.4542, 0.7153, 1.5433, 2.6444], [0.2572, 0.5316, 0.8890, 1.9557, 3.4222])
     earlier = ([0.2510, 0.5256, 0.8032, 1.6725, 2.7880], [0.2568, 0.5331, 0.8986, 1.9608, 3.4332])
+    latest = ([0.2658, 0.4547, 0.7132, 1.5380, 2.6623], [0.2495, 0.5299, 0.8971, 1.9536, 3.4111])
     assert tile_sweep.fanout_threshold(SIDES, *later) == 4096 * 4096
     assert tile_sweep.fanout_threshold(SIDES, *earlier) == 8192 * 8192
+    assert tile_sweep.fanout_threshold(SIDES, *latest) == 6144 * 6144
 
 
 def test_fanout_threshold_needs_every_larger_side():
